@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark of the protected convolution (numerical entanglement) on GB300.
+
+Default workload: M = 4 integer streams of N = 2^22 samples, K = 64 taps,
+data and taps uniform in [-2^15, 2^15), 64-bit entangled words; each step is
+one pass of the whole protected path over the job (entangle-on-load,
+convolution of every entangled stream, fail-stop of stream r = step mod M,
+recovery of all M outputs from the other M-1) in the fused launch.
+
+Prints ONE JSON line (rank 0).  `value` is protected GOPS (2*M*N*K integer
+ops per job) over all ranks; beside it: the unprotected and checksum-ABFT
+GPU baselines on the same data, the roofline of the dominant kernel, the
+end-to-end figure through host buffers, the clocks seen, and the CPU oracle
+timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ne|reference]
+Under torchrun (N > 1) each rank runs its own independent job (weak
+scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("protected conv GOPS + % overhead vs unprotected GB300 conv; "
+          "p99 ms served")
+WORKLOAD = ("M=4 streams x N=2^22 samples, K=64 taps, data and taps uniform "
+            "in [-2^15,2^15), 64-bit entangled words with exact int64 "
+            "accumulation, one stream fail-stopped per step (r = step mod 4, "
+            "its result dropped) and recovered")
+L2_NOTE = ("inputs larger than L2: c 134 MB + d 134 MB per step vs 129 MB L2 "
+           "(no flush)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ne", "reference"], default="ne")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target wall time of the CPU oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks: nvidia-smi sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}",
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()  # the exact process started above
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append((ts, parts))
+        inside = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15]
+        use = inside or rows[-3:]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0, "note": "nvidia-smi unavailable"}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(p[2]) for _, p in use if num(p[2]) is not None]
+        smax = [num(p[3]) for _, p in use if num(p[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = set()
+        for _, p in use:
+            for i, nm in enumerate(names):
+                if p[6 + i].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(use),
+                "samples_inside_timed_region": len(inside)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (the oracle as it stands, on the host cores)
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_sample(target_s: float, n_sample: int = 1 << 14):
+    """Time the oracle's protected convolution (entangle -> convolve every
+    stream -> recover) on independent slices of the workload, one thread per
+    host core (the oracle releases the GIL inside its C calls)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import oracle as orc
+    from paper_1509_03838_gb300 import synth
+
+    orc.build()
+    M, K, w = 4, 64, 64
+    l = orc.params(M, w)[0]
+
+    def one(seed):
+        j = synth.stream_job(seed, M=M, N=n_sample, K=K, data_bits=15,
+                             tap_bits=15, w=w)
+        orc.protected_conv(j.c, j.g, w, l, j.failed)
+        return M * n_sample * K
+
+    t = time.perf_counter()
+    one(0)
+    t_one = time.perf_counter() - t
+    cores = os.cpu_count() or 1
+    per_thread = max(1, int(target_s / max(t_one, 1e-6)))
+    jobs = cores * per_thread
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        macs = sum(ex.map(one, range(1, jobs + 1)))
+    el = time.perf_counter() - t0
+    gops = 2.0 * macs / el / 1e9
+    return {"value": gops, "unit": "GOPS", "cores": cores, "kind": "oracle",
+            "sample": (f"{jobs} slices of M=4 x N={n_sample} samples, K=64 "
+                       f"(the workload's shape, {jobs * n_sample} of its "
+                       f"2^22 samples per stream), entangle + convolve all "
+                       f"streams + recover one failed stream, {el:.1f} s wall"),
+            "seconds": el}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    steps, warm = args.steps, args.warmup
+    # each step is a bounded sample of the workload timed on the host cores
+    per_step = max(0.5, min(5.0, 120.0 / max(steps + warm, 1)))
+    for _ in range(warm):
+        cpu_oracle_sample(per_step * 0.2)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(steps):
+        last = cpu_oracle_sample(per_step)
+        vals.append(last["value"])
+    el = time.perf_counter() - t0
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GOPS",
+            "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+            "ms_per_step": el * 1e3 / max(steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": WORKLOAD,
+                                            "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": "GOPS",
+                             "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "GOPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def timed(fn, steps, world, stream, per_launch=False):
+    """Run fn(i) `steps` times between barriers and synchronisations; return
+    (total ms max over ranks, per-launch ms list)."""
+    import torch
+    ev = []
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        if per_launch:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(i)
+            b.record(stream)
+            ev.append((a, b))
+        else:
+            fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    total = e0.elapsed_time(e1)
+    launches = [a.elapsed_time(b) for a, b in ev]
+    return total, launches
+
+
+def run_ne(args):
+    import torch
+
+    world, rank, local = dist_env()
+    init_dist(world, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1509_03838_gb300 import build, ne, synth
+    if rank == 0:
+        build.build()
+    barrier(world)
+    build.build()
+
+    j = synth.large_job(seed=2 + rank)
+    M, N, K = j.M, j.N, j.K
+    Nout = N + K - 1
+    p = ne.ne_params(M, 64)
+    stream = torch.cuda.current_stream()
+    c = torch.from_numpy(j.c).to(dev)
+    g = torch.from_numpy(j.g.astype(np.int32)).to(dev)
+    d = torch.empty((M, Nout), dtype=torch.int64, device=dev)
+    ws = torch.empty(ne.ne_protected_conv_ws_bytes(M, N, K), dtype=torch.uint8,
+                     device=dev)
+
+    def protected(i):
+        ne.ne_protected_conv(c, g, d, l=p.l, max_abs_c=j.bound_c,
+                             max_abs_g=j.bound_g, failed=i % M,
+                             fail_mode=ne.NE_FAIL_DROP, ws=ws)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.warmup):
+        protected(i)
+    torch.cuda.synchronize()
+    t_start = time.time()
+    total_ms, _ = timed(protected, args.steps, world, stream)
+    t_end = time.time()
+    clocks.stop()
+    total_ms = max_over_ranks(total_ms, world, dev)
+    ms_step = total_ms / args.steps
+    ops_job = 2.0 * M * N * K
+    gops = world * ops_job * args.steps / (total_ms * 1e-3) / 1e9
+
+    # per-launch duration of the dominant (fused) kernel
+    _, launches = timed(protected, max(args.steps, 10), world, stream,
+                        per_launch=True)
+    prot_ms = statistics.mean(launches)
+
+    # ---- baselines on the same data (same number of steps) ---------------
+    def unprot_same(i):   # same kernel template and word arithmetic
+        ne.ne_conv(c, g, d, max_abs_x=0)
+
+    def unprot_best(i):   # narrowest exact arithmetic for the raw data
+        ne.ne_conv(c, g, d, max_abs_x=j.bound_c)
+
+    cs = torch.empty((M + 1, N), dtype=torch.int64, device=dev)
+    cs[:M] = c
+    cso = torch.empty((M + 1, Nout), dtype=torch.int64, device=dev)
+
+    def checksum(i):      # Eq. 3-5: checksum stream, M+1 convs, recovery
+        f = i % M
+        ne.ne_checksum(cs[:M], cs[M])
+        ne.ne_conv(cs, g, cso, max_abs_x=M * j.bound_c)
+        ne.ne_checksum_recover(cso[:M], cso[M], cso[f], f=f)
+
+    eps = torch.empty_like(c)
+    delta = torch.empty_like(d)
+
+    def unfused(i):       # entangle -> conv (r not run) -> recover
+        r = i % M
+        ne.ne_entangle(c, eps, l=p.l)
+        ne.ne_conv(eps, g, delta, max_abs_x=0,
+                   live_mask=((1 << M) - 1) & ~(1 << r))
+        ne.ne_recover(delta, d, l=p.l, failed=r)
+
+    res = {}
+    for name, fn in [("unprotected_same_arith", unprot_same),
+                     ("unprotected_best_arith", unprot_best),
+                     ("checksum_abft", checksum),
+                     ("protected_unfused", unfused)]:
+        for i in range(3):
+            fn(i)
+        t, _ = timed(fn, args.steps, world, stream)
+        res[name] = max_over_ranks(t, world, dev) / args.steps
+    del eps, delta, cs, cso
+
+    def pct(a, b):
+        return 100.0 * (a - b) / b
+
+    overhead = {
+        "protected_vs_unprotected_same_arith": pct(ms_step, res["unprotected_same_arith"]),
+        "protected_vs_unprotected_best_arith": pct(ms_step, res["unprotected_best_arith"]),
+        "checksum_vs_unprotected_best_arith": pct(res["checksum_abft"], res["unprotected_best_arith"]),
+        "unfused_protected_vs_unprotected_same_arith": pct(res["protected_unfused"], res["unprotected_same_arith"]),
+        "ms_per_job": {"protected_fused": ms_step, **res},
+    }
+
+    # ---- roofline of the dominant kernel (integer multiply-add pipe) -------
+    probe = {}
+    for kind, nm in [(0, "imad32"), (1, "imad_wide"), (2, "split_pair")]:
+        rate, _ = ne.ne_probe_imad_rate(kind, 2048)
+        probe[nm] = rate
+    # split 64-bit arithmetic: one 32x32->64 and one 32-bit multiply-add per
+    # tap; the stream r conv of the dropped stream also runs (M streams).
+    instr = 2.0 * M * N * K
+    achieved = instr / (prot_ms * 1e-3) / 1e12
+    peak = probe["split_pair"] / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "T multiply-add instr/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "conv_kernel<int64_t, MODE_SPLIT, VEC, PROT> (fused)",
+                "peak_source": "measured: ne_probe_imad_rate kind 2 (paired "
+                               "mad.wide.s32 + mad.lo.u32 chains), this GPU",
+                "launch_ms": prot_ms,
+                "probe_instr_per_s": probe}
+
+    # ---- end to end through host buffers ----------------------------------
+    c_h = torch.from_numpy(j.c).pin_memory()
+    d_h = torch.empty((M, Nout), dtype=torch.int64).pin_memory()
+    g_h = torch.from_numpy(j.g.astype(np.int32)).pin_memory()
+
+    def e2e(i):
+        c.copy_(c_h, non_blocking=True)
+        g.copy_(g_h, non_blocking=True)
+        protected(i)
+        d_h.copy_(d, non_blocking=True)
+
+    for i in range(2):
+        e2e(i)
+    t_e2e, _ = timed(e2e, args.steps, world, stream)
+    t_e2e = max_over_ranks(t_e2e, world, dev)
+    e2e_val = world * ops_job * args.steps / (t_e2e * 1e-3) / 1e9
+
+    clk = clocks.summary(t_start, t_end)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(args.cpu_seconds)
+        cpu.pop("seconds", None)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": gops, "unit": "GOPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded uniform integers; the paper names no "
+                    "dataset)",
+            "config": {"workload": WORKLOAD, "l2": L2_NOTE, "M": M, "N": N,
+                       "K": K, "w": 64, "l": p.l, "k": p.k,
+                       "parallelism": "one independent job per GPU"},
+            "samples_per_s": world * M * Nout * args.steps / (total_ms * 1e-3),
+            "overhead_pct": overhead,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "GOPS",
+                    "h2d_bytes_per_step": c.numel() * 8 + g.numel() * 4,
+                    "d2h_bytes_per_step": d.numel() * 8},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "p99_ms_served": None,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ne(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,227 @@
+/*
+ * ne.h -- C ABI of the numerical-entanglement library (libne.so), GB300.
+ *
+ * Numerical entanglement (Anam & Andreopoulos, arXiv 1509.03838) protects an
+ * LSB operation (linear, sesquilinear or bijective: scaling, addition,
+ * convolution, permutation ...) applied to M >= 3 integer streams against the
+ * fail-stop loss of any one stream computation (Sec. II-B):
+ *   1. the M input streams c_m are superimposed in pairs,
+ *        eps_m = c_m + S_l{c_{(m-1) mod M}}             (Eq. 6, Eq. 14-15)
+ *   2. the LSB operation runs on each entangled stream independently,
+ *        delta_m = eps_m op g                           (Eq. 9)
+ *   3. all M true outputs d_m are extracted from ANY M-1 of the delta_m by
+ *      additions and arithmetic shifts                  (Eq. 10, Eq. 16-19).
+ *
+ * Conventions shared by every call
+ *   - Streams are stored stream-major: M rows of `ld` words; row m starts at
+ *     base + m*ld words.  A word is int32_t when w == 32 and int64_t when
+ *     w == 64.  N is the number of samples in a row (N <= ld).
+ *   - Every pointer to stream data or taps is a DEVICE pointer owned by the
+ *     caller; the library never frees or retains caller memory.  Rows whose
+ *     start is 16-byte aligned take a 128-bit vector path; any other layout
+ *     takes a scalar path with the same results.
+ *   - Every compute call is asynchronous on the caller's CUDA stream
+ *     (`stream` is a cudaStream_t passed as void*, NULL = legacy default
+ *     stream).  Argument and range checks run on the host before any launch
+ *     and return an error without touching device memory.  A launch failure
+ *     returns NE_ERR_CUDA; an asynchronous kernel fault surfaces as
+ *     NE_ERR_CUDA from a later call or from the caller's own synchronisation.
+ *   - Arithmetic is modulo 2^w (two's complement).  Results equal the exact
+ *     integers whenever every true output d satisfies |d| <= d_max_exact of
+ *     ne_params(); beyond that the outputs are defined (no fault) but wrong.
+ *   - No call blocks the host, allocates device memory, or spins on the
+ *     device.
+ */
+#ifndef NE_H_
+#define NE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NE_OK = 0,
+  NE_ERR_INVALID_ARG = 1,   /* bad pointer, size, stride, M, w, l or index   */
+  NE_ERR_RANGE = 2,         /* declared data bounds exceed the exact range   */
+  NE_ERR_UNRECOVERABLE = 3, /* more than one stream failed (only single      */
+                            /* fail-stop failures are recoverable, Sec. I-B)  */
+  NE_ERR_NOMEM = 4,         /* a caller-provided workspace is too small      */
+  NE_ERR_TIMEOUT = 5,       /* a bounded wait expired                        */
+  NE_ERR_CUDA = 6,          /* a CUDA runtime call or kernel launch failed   */
+  NE_ERR_UNSUPPORTED = 7    /* valid request outside this build's limits     */
+} ne_status;
+
+/* Failure injection for the protected convolution (fail-stop model of
+ * Sec. I: a core is unresponsive or misses its deadline). */
+typedef enum {
+  NE_FAIL_NONE = 0, /* every stream delivers                                 */
+  NE_FAIL_SKIP = 1, /* stream `failed` never runs (core dead from the start)  */
+  NE_FAIL_DROP = 2  /* stream `failed` computes but its result is lost        */
+} ne_fail_mode;
+
+typedef struct {
+  int M;               /* number of streams, >= 3                          */
+  int w;               /* word width in bits: 32 or 64                     */
+  int l;               /* entanglement shift (Eq. 6)                       */
+  int k;               /* Eq. 8 / Eq. 12: (M-1)l + k <= w                  */
+  int64_t d_max_paper; /* Eq. 13: 2^{(M-3)l+k} (2^{l-1} - 1)               */
+  int64_t d_max_exact; /* exact limit: min(floor((2^{w-1}-1)/(2^l+1)),     */
+                       /*                  2^{(M-1)l-1} - 1)               */
+} ne_params_t;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *ne_status_str(int status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int ne_version(void);
+
+/*
+ * ne_params -- entanglement parameters for M streams in w-bit words
+ * (Sec. III-A after Eq. 8; Eq. 12, Eq. 13; Table I).  l and k maximise the
+ * supported output bitwidth (M-2)l + k subject to (M-1)l + k <= w and
+ * 0 <= k <= l, ties to the larger l; this reproduces every row of Table I.
+ * Host-only; no CUDA call.  w must be 32 or 64; 3 <= M <= 32.
+ * Returns NE_OK or NE_ERR_INVALID_ARG.
+ */
+int ne_params(int M, int w, ne_params_t *out);
+
+/*
+ * ne_choose_width -- pick the narrowest word (32, else 64 bits) for which a
+ * convolution of K taps with |c| <= max_abs_c and |g| <= max_abs_g stays
+ * within the exact range: K * max_abs_c * max_abs_g <= d_max_exact (the
+ * dynamic-range bound of Eq. 11 / Eq. 13 decides the accumulator width).
+ * Host-only.  Returns NE_OK and fills *out, or NE_ERR_RANGE if even 64-bit
+ * words cannot hold the outputs, or NE_ERR_INVALID_ARG.
+ */
+int ne_choose_width(int M, int K, int64_t max_abs_c, int64_t max_abs_g,
+                    ne_params_t *out);
+
+/*
+ * ne_entangle -- eps = E{c} (Eq. 15; Eq. 6 for M = 3):
+ *     eps_m[n] = c_m[n] + (c_{(m-1) mod M}[n] << l)   (mod 2^w)
+ * for 0 <= m < M, 0 <= n < N.  c: M rows of N words, leading dim ldc; eps:
+ * M rows, leading dim lde.  In place is allowed (eps == c and lde == ldc),
+ * as the paper stores the entangled streams in place of the inputs; any
+ * other overlap is invalid.  Bandwidth-bound: reads and writes every word
+ * once.  Requires 0 < l < w.
+ */
+int ne_entangle(const void *c, int64_t ldc, void *eps, int64_t lde, int M,
+                int64_t N, int w, int l, void *stream);
+
+/*
+ * ne_conv -- the LSB operation of Eq. 9 for op = full linear convolution:
+ *     y_m[n] = sum_{t=0}^{K-1} x_m[n-t] * g[t]   (mod 2^w),
+ *     0 <= n < N + K - 1, x_m[j] = 0 outside [0, N),
+ * for every stream m whose bit is set in live_mask (bit m = stream m; other
+ * rows of y are not written: a fail-stopped stream).  x: M rows of N words
+ * (ldx); y: M rows of N+K-1 words (ldy >= N+K-1); g: K int32 taps on the
+ * device.  max_abs_x is the caller's bound on |x| (0 = unknown); for w = 64
+ * a bound below 2^31 lets the kernel use a single 32x32->64 multiply-add per
+ * tap instead of two.  The result is exact modulo 2^w either way.
+ * Requires 1 <= K <= 8192, 1 <= M <= 32.  Works on raw streams (the
+ * unprotected baseline) and on entangled streams alike.
+ */
+int ne_conv(const void *x, int64_t ldx, int M, int64_t N, const int32_t *g,
+            int K, void *y, int64_t ldy, int w, int64_t max_abs_x,
+            uint32_t live_mask, void *stream);
+
+/*
+ * ne_recover -- recover all M outputs from the M-1 entangled outputs that
+ * remain after stream `failed` fail-stopped (Eq. 16-19; Eq. 10 for M = 3;
+ * Remark 2).  Row `failed` of delta is never read.  delta: M rows of Nout
+ * words (ldd); d: M rows (ld_out), written for every m.  d must not overlap
+ * delta except d == delta with ld_out == ldd (in place).  Uses only w-bit
+ * operations (Remark 1): the low (M-1)l bits of d_temp give
+ * d_{(failed-1) mod M}, and a backward chain of subtract-and-shift steps
+ * gives the others.  failed in [0, M).  Bandwidth-bound.
+ */
+int ne_recover(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
+               int l, int failed, void *d, int64_t ld_out, void *stream);
+
+/*
+ * ne_extract -- extraction with all M entangled outputs present.  The
+ * result is unique, so this is ne_recover with one stream left unread
+ * (stream 0, as Eq. 10 leaves delta_0 unused).
+ */
+int ne_extract(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
+               int l, void *d, int64_t ld_out, void *stream);
+
+/*
+ * ne_protected_conv -- the whole protected path in one launch:
+ * entangle-on-load (Sec. II-B: entanglement applied as each input stream is
+ * read) -> convolution of each entangled stream as independent units of
+ * work (Eq. 9) -> per output tile, the (M-1)-th stream to deliver extracts
+ * all M outputs from the M-1 delivered entangled tiles (Eq. 16-19; results
+ * are disentangled as soon as any M-1 output streams are available, Sec. V).
+ *   c: M raw input rows of N words (ldc); g: K int32 taps;
+ *   d: M output rows (ldd >= N+K-1), receives the true outputs d_m = c_m * g.
+ *      It also serves as the landing buffer of the entangled tiles.
+ *   max_abs_c, max_abs_g: caller's bounds on |c| and |g|; the call returns
+ *      NE_ERR_RANGE if K*max_abs_c*max_abs_g > d_max_exact for (M, w).
+ *   failed, fail_mode: failure injection (failed in [0, M) or -1 with
+ *      NE_FAIL_NONE).
+ *   ws: device workspace of ne_protected_conv_ws_bytes() bytes (per-tile
+ *      arrival words; zeroed by this call on `stream`); ws_bytes its size.
+ * No device-side waiting: the tile extractor is whichever stream arrives
+ * (M-1)-th; a late M-th stream discards its result.
+ */
+int ne_protected_conv(const void *c, int64_t ldc, int M, int64_t N,
+                      const int32_t *g, int K, int w, int l,
+                      int64_t max_abs_c, int64_t max_abs_g, int failed,
+                      int fail_mode, void *d, int64_t ldd, void *ws,
+                      size_t ws_bytes, void *stream);
+
+/* Workspace bytes ne_protected_conv needs for (M, N, K). Host-only. */
+size_t ne_protected_conv_ws_bytes(int M, int64_t N, int K);
+
+/*
+ * ne_checksum -- checksum stream of the ABFT baseline (Eq. 3-4):
+ *     r[n] = sum_m c_m[n]  (mod 2^w),  0 <= n < N.
+ * c: M rows (ldc); r: N words (may be row M of the same [M+1][ldc] buffer,
+ * so that one ne_conv launch then processes all M+1 streams, Eq. 5).
+ */
+int ne_checksum(const void *c, int64_t ldc, int M, int64_t N, int w, void *r,
+                void *stream);
+
+/*
+ * ne_checksum_recover -- recover the output of failed stream f from the
+ * checksum output e and the other M outputs (Eq. 5 and the text after it):
+ *     out[n] = e[n] - sum_{m != f} d_m[n]   (mod 2^w).
+ * d: M rows (ldd), row f not read; e, out: Nout words (out may be row f).
+ */
+int ne_checksum_recover(const void *d, int64_t ldd, const void *e, int M,
+                        int64_t Nout, int w, int f, void *out, void *stream);
+
+/*
+ * Element-wise LSB operations of Eq. 2 applied to M rows of N words
+ * (each may run in place: y == x with equal leading dims):
+ *   ne_scale:  y_m[n] = s * x_m[n]            (op = x, scalar kernel)
+ *   ne_add:    y_m[n] = x_m[n] + z_m[n]       (op = +, both entangled with
+ *                                              the same l)
+ *   ne_self_entangle: out[n] = (g[n] << l) + g[n] for one row of N words
+ *              (footnote to Eq. 9: a plain kernel added to or subtracted
+ *              from entangled streams must first be entangled with itself)
+ *   ne_permute: y_m[n] = x_m[perm[n]]        (a fixed, data-independent
+ *              bijection; perm: N int64 device indices in [0, N); y must
+ *              not overlap x).  Indices outside [0, N) write 0 and are
+ *              counted in *bad_count if bad_count != NULL (a device int
+ *              that the caller zeroes).
+ */
+int ne_scale(const void *x, int64_t ldx, int M, int64_t N, int64_t s, int w,
+             void *y, int64_t ldy, void *stream);
+int ne_add(const void *x, int64_t ldx, const void *z, int64_t ldz, int M,
+           int64_t N, int w, void *y, int64_t ldy, void *stream);
+int ne_self_entangle(const void *g, int64_t N, int w, int l, void *out,
+                     void *stream);
+int ne_permute(const void *x, int64_t ldx, int M, int64_t N,
+               const int64_t *perm, int w, void *y, int64_t ldy,
+               int32_t *bad_count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NE_H_ */

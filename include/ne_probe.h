@@ -1,0 +1,33 @@
+/*
+ * ne_probe.h -- measurement utility of libne.so (not an operation of the
+ * paper): the integer multiply-add throughput of the current GPU, which is
+ * the denominator of the convolution's roofline.
+ */
+#ifndef NE_PROBE_H_
+#define NE_PROBE_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * ne_probe_imad_rate -- launch 8 blocks of 256 threads per SM, each thread
+ * running eight independent chains of `iters` multiply-adds of one kind:
+ *   kind 0: 32-bit multiply-add (mad.lo.u32)
+ *   kind 1: 32x32->64 multiply-add (mad.wide.s32)
+ *   kind 2: one of each per round (two instructions)
+ * and return the best of three timed launches (after one warm-up) as
+ * multiply-add instructions per second in *instr_per_s (and the launch time
+ * in *elapsed_ms if non-NULL).  Unlike the compute calls of ne.h this call
+ * allocates 8 bytes of device memory, uses the legacy default stream and
+ * blocks until the launches finish.  Returns NE_OK, NE_ERR_INVALID_ARG or
+ * NE_ERR_CUDA.
+ */
+int ne_probe_imad_rate(int kind, int iters, double *instr_per_s,
+                       double *elapsed_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NE_PROBE_H_ */

@@ -1,0 +1,133 @@
+// Per-column recovery of all M outputs from the M-1 entangled outputs that
+// remain after stream r fail-stops, using w-bit operations only (Remark 1).
+//
+// With delta_m = d_m + 2^l d_{m-1} (mod 2^w), the Horner evaluation
+//     t = delta_{r+1};  t = (t << l) -/+ delta_{r+1+q},  q = 1 .. M-2
+// (sign (-1)^q) gives sum_q (-1)^q 2^{(M-2-q)l} delta_{(r+1+q) mod M}, the
+// sum of Eq. 16; times (-1)^M it telescopes to d_{r-1} + (-1)^M 2^{(M-1)l} d_r,
+// so its low (M-1)l bits, sign-extended, are d_{(r-1) mod M} (Eq. 17).  The
+// high part that Eq. 18 would shift down is not needed: a backward chain
+//     d_{j-1} = (delta_j - d_j) >> l,   j = r-1, r-2, ..., r+1  (mod M)
+// recovers the rest; each step is an exact division by 2^l of a w-bit value
+// (delta_j - d_j = 2^l d_{j-1}), so nothing ever needs 2w bits.  This is the
+// same result as Eq. 18-19, reached in the opposite direction around the
+// cycle.
+#pragma once
+
+#include "ne_common.cuh"
+
+namespace ne {
+
+template <typename W, int V, bool CG>
+__device__ __forceinline__ void load_words(const W* p, W (&out)[V]) {
+  if constexpr (V == 1) {
+    out[0] = CG ? __ldcg(p) : *p;
+  } else {
+    using VT = typename Vec<W>::T;
+    VT v = CG ? __ldcg(reinterpret_cast<const VT*>(p))
+              : *reinterpret_cast<const VT*>(p);
+    const W* pv = reinterpret_cast<const W*>(&v);
+#pragma unroll
+    for (int i = 0; i < V; ++i) out[i] = pv[i];
+  }
+}
+
+template <typename W, int V>
+__device__ __forceinline__ void store_words(W* p, const W (&in)[V]) {
+  if constexpr (V == 1) {
+    *p = in[0];
+  } else {
+    using VT = typename Vec<W>::T;
+    VT v;
+    W* pv = reinterpret_cast<W*>(&v);
+#pragma unroll
+    for (int i = 0; i < V; ++i) pv[i] = in[i];
+    *reinterpret_cast<VT*>(p) = v;
+  }
+}
+
+// Recover V consecutive columns [n, n+V).  MM = M when M is a compile-time
+// constant (all delta rows kept in registers), 0 for any M (rows re-read in
+// the backward pass).  CG: read delta through L2 only (data written by other
+// thread blocks of the same launch).  d may equal delta (in place): every
+// delta row is read before the same row of d is written.
+template <typename W, int MM, int V, bool CG>
+__device__ __forceinline__ void recover_columns(const W* delta, int64_t ldd,
+                                                int M_rt, int64_t n, int l,
+                                                int r, W* d, int64_t ldo) {
+  const int M = MM ? MM : M_rt;
+  constexpr int CACHE = MM ? MM : 1;
+  W cache[CACHE][V];
+  W t[V];
+  int row = r + 1 == M ? 0 : r + 1;
+  {
+    W v[V];
+    load_words<W, V, CG>(delta + (int64_t)row * ldd + n, v);
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      t[i] = v[i];
+      if (MM) cache[0][i] = v[i];
+    }
+  }
+#pragma unroll
+  for (int q = 1; q < (MM ? MM - 1 : 1); ++q) {  // unrolled path (MM > 0)
+    row = row + 1 == M ? 0 : row + 1;
+    W v[V];
+    load_words<W, V, CG>(delta + (int64_t)row * ldd + n, v);
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      cache[q][i] = v[i];
+      t[i] = (q & 1) ? wsub<W>(shl<W>(t[i], l), v[i])
+                     : wadd<W>(shl<W>(t[i], l), v[i]);
+    }
+  }
+  if (!MM) {
+    for (int q = 1; q < M - 1; ++q) {
+      row = row + 1 == M ? 0 : row + 1;
+      W v[V];
+      load_words<W, V, CG>(delta + (int64_t)row * ldd + n, v);
+#pragma unroll
+      for (int i = 0; i < V; ++i)
+        t[i] = (q & 1) ? wsub<W>(shl<W>(t[i], l), v[i])
+                       : wadd<W>(shl<W>(t[i], l), v[i]);
+    }
+  }
+  // d_{r-1}: low (M-1)l bits of (-1)^M t, sign-extended
+  const int win = (M - 1) * l;
+  W dcur[V];
+#pragma unroll
+  for (int i = 0; i < V; ++i) {
+    const W dt = (M & 1) ? wsub<W>((W)0, t[i]) : t[i];
+    dcur[i] = sext_low<W>(dt, win);
+  }
+  // backward chain: rows r-1, r-2, ..., r+1
+  int j = r == 0 ? M - 1 : r - 1;
+#pragma unroll
+  for (int q = (MM ? MM - 2 : 0); q >= 0; --q) {  // unrolled path (MM > 0)
+    if (!MM) break;
+    W nxt[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) nxt[i] = wsub<W>(cache[q][i], dcur[i]) >> l;
+    store_words<W, V>(d + (int64_t)j * ldo + n, dcur);
+#pragma unroll
+    for (int i = 0; i < V; ++i) dcur[i] = nxt[i];
+    j = j == 0 ? M - 1 : j - 1;
+  }
+  if (!MM) {
+    for (int q = M - 2; q >= 0; --q) {
+      W v[V];
+      load_words<W, V, CG>(delta + (int64_t)j * ldd + n, v);
+      W nxt[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) nxt[i] = wsub<W>(v[i], dcur[i]) >> l;
+      store_words<W, V>(d + (int64_t)j * ldo + n, dcur);
+#pragma unroll
+      for (int i = 0; i < V; ++i) dcur[i] = nxt[i];
+      j = j == 0 ? M - 1 : j - 1;
+    }
+  }
+  // j == r now; dcur == d_r
+  store_words<W, V>(d + (int64_t)r * ldo + n, dcur);
+}
+
+}  // namespace ne

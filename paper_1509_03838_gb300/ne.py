@@ -1,0 +1,326 @@
+"""Thin ctypes binding of libne.so (C ABI in include/ne.h).
+
+Argument marshalling only: every function takes torch CUDA tensors, passes
+their device pointers, leading dimensions and the current CUDA stream to the
+C entry point of the same name, and raises :class:`NEError` on a non-OK
+status.  There is no CPU fallback: if libne.so is missing the first call
+raises, naming how to build it.
+
+Layout: stream data are 2-D tensors [rows, >= samples] with unit stride
+along samples (row stride = leading dimension); int32 tensors are w = 32
+words and int64 tensors are w = 64 words.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libne.so")
+
+NE_OK = 0
+NE_ERR_INVALID_ARG = 1
+NE_ERR_RANGE = 2
+NE_ERR_UNRECOVERABLE = 3
+NE_ERR_NOMEM = 4
+NE_ERR_TIMEOUT = 5
+NE_ERR_CUDA = 6
+NE_ERR_UNSUPPORTED = 7
+
+NE_FAIL_NONE = 0
+NE_FAIL_SKIP = 1
+NE_FAIL_DROP = 2
+
+_lib = None
+_lock = threading.Lock()
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int
+_i64 = ctypes.c_int64
+_u32 = ctypes.c_uint32
+_sz = ctypes.c_size_t
+
+
+class NEError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("M", _i32), ("w", _i32), ("l", _i32), ("k", _i32),
+                ("d_max_paper", _i64), ("d_max_exact", _i64)]
+
+
+@dataclass(frozen=True)
+class Params:
+    M: int
+    w: int
+    l: int
+    k: int
+    d_max_paper: int
+    d_max_exact: int
+
+
+# name -> (argtypes, restype)
+_SIGS = {
+    "ne_status_str": ([_i32], ctypes.c_char_p),
+    "ne_version": ([], _i32),
+    "ne_params": ([_i32, _i32, ctypes.POINTER(_Params)], _i32),
+    "ne_choose_width": ([_i32, _i32, _i64, _i64, ctypes.POINTER(_Params)], _i32),
+    "ne_entangle": ([_vp, _i64, _vp, _i64, _i32, _i64, _i32, _i32, _vp], _i32),
+    "ne_conv": ([_vp, _i64, _i32, _i64, _vp, _i32, _vp, _i64, _i32, _i64,
+                 _u32, _vp], _i32),
+    "ne_recover": ([_vp, _i64, _i32, _i64, _i32, _i32, _i32, _vp, _i64, _vp],
+                   _i32),
+    "ne_extract": ([_vp, _i64, _i32, _i64, _i32, _i32, _vp, _i64, _vp], _i32),
+    "ne_protected_conv": ([_vp, _i64, _i32, _i64, _vp, _i32, _i32, _i32, _i64,
+                           _i64, _i32, _i32, _vp, _i64, _vp, _sz, _vp], _i32),
+    "ne_protected_conv_ws_bytes": ([_i32, _i64, _i32], _sz),
+    "ne_checksum": ([_vp, _i64, _i32, _i64, _i32, _vp, _vp], _i32),
+    "ne_checksum_recover": ([_vp, _i64, _vp, _i32, _i64, _i32, _i32, _vp, _vp],
+                            _i32),
+    "ne_scale": ([_vp, _i64, _i32, _i64, _i64, _i32, _vp, _i64, _vp], _i32),
+    "ne_add": ([_vp, _i64, _vp, _i64, _i32, _i64, _i32, _vp, _i64, _vp], _i32),
+    "ne_self_entangle": ([_vp, _i64, _i32, _i32, _vp, _vp], _i32),
+    "ne_permute": ([_vp, _i64, _i32, _i64, _vp, _i32, _vp, _i64, _vp, _vp],
+                   _i32),
+    "ne_probe_imad_rate": ([_i32, _i32, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double)], _i32),
+}
+# optional entry points added by later modules register here
+EXTRA_SIGS: dict = {}
+
+
+def lib():
+    """The loaded libne.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -m paper_1509_03838_gb300.build` (nvcc, sm_103a); "
+                    "there is no CPU fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in {**_SIGS, **EXTRA_SIGS}.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return lib().ne_status_str(status).decode()
+
+
+def _check(status: int, where: str) -> None:
+    if status != NE_OK:
+        raise NEError(status, where)
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _word_bits(t: torch.Tensor) -> int:
+    if t.dtype == torch.int32:
+        return 32
+    if t.dtype == torch.int64:
+        return 64
+    raise TypeError(f"stream words must be int32 or int64, got {t.dtype}")
+
+
+def _rows(t: torch.Tensor, name: str):
+    """(ptr, rows, samples, ld) of a 2-D CUDA tensor with unit inner stride."""
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dim() == 1:
+        t2 = t.unsqueeze(0)
+    elif t.dim() == 2:
+        t2 = t
+    else:
+        raise ValueError(f"{name} must be 1-D or 2-D")
+    if t2.size(1) > 1 and t2.stride(1) != 1:
+        raise ValueError(f"{name} must have unit stride along samples")
+    ld = t2.stride(0) if t2.size(0) > 1 else max(t2.size(1), 1)
+    return ctypes.c_void_p(t2.data_ptr()), t2.size(0), t2.size(1), ld
+
+
+# ---------------------------------------------------------------------------
+# host-only calls
+# ---------------------------------------------------------------------------
+
+def ne_params(M: int, w: int) -> Params:
+    p = _Params()
+    _check(lib().ne_params(M, w, ctypes.byref(p)), "ne_params")
+    return Params(p.M, p.w, p.l, p.k, p.d_max_paper, p.d_max_exact)
+
+
+def ne_choose_width(M: int, K: int, max_abs_c: int, max_abs_g: int) -> Params:
+    p = _Params()
+    _check(lib().ne_choose_width(M, K, max_abs_c, max_abs_g, ctypes.byref(p)),
+           "ne_choose_width")
+    return Params(p.M, p.w, p.l, p.k, p.d_max_paper, p.d_max_exact)
+
+
+def ne_protected_conv_ws_bytes(M: int, N: int, K: int) -> int:
+    return int(lib().ne_protected_conv_ws_bytes(M, N, K))
+
+
+# ---------------------------------------------------------------------------
+# device calls (asynchronous on the current torch stream unless given)
+# ---------------------------------------------------------------------------
+
+def ne_entangle(c: torch.Tensor, eps: torch.Tensor | None = None, *, l: int,
+                N: int | None = None, stream=None) -> torch.Tensor:
+    """eps = E{c} (Eq. 15).  In place when eps is None or eps is c."""
+    eps = c if eps is None else eps
+    pc, M, n, ldc = _rows(c, "c")
+    pe, _, _, lde = _rows(eps, "eps")
+    w = _word_bits(c)
+    assert _word_bits(eps) == w
+    _check(lib().ne_entangle(pc, ldc, pe, lde, M, n if N is None else N, w, l,
+                             _stream(stream)), "ne_entangle")
+    return eps
+
+
+def ne_conv(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
+            max_abs_x: int = 0, live_mask: int = 0xFFFFFFFF,
+            N: int | None = None, stream=None) -> torch.Tensor:
+    """y_m = x_m * g (full linear convolution, Eq. 9) for live streams."""
+    px, M, n, ldx = _rows(x, "x")
+    py, _, _, ldy = _rows(y, "y")
+    if g.dtype != torch.int32 or not g.is_cuda:
+        raise ValueError("taps g must be an int32 CUDA tensor")
+    w = _word_bits(x)
+    assert _word_bits(y) == w
+    _check(lib().ne_conv(px, ldx, M, n if N is None else N,
+                         ctypes.c_void_p(g.data_ptr()), g.numel(), py, ldy, w,
+                         max_abs_x, live_mask & 0xFFFFFFFF, _stream(stream)),
+           "ne_conv")
+    return y
+
+
+def ne_recover(delta: torch.Tensor, d: torch.Tensor, *, l: int, failed: int,
+               Nout: int | None = None, stream=None) -> torch.Tensor:
+    pdl, M, n, ldd = _rows(delta, "delta")
+    pd, _, _, ldo = _rows(d, "d")
+    w = _word_bits(delta)
+    _check(lib().ne_recover(pdl, ldd, M, n if Nout is None else Nout, w, l,
+                            failed, pd, ldo, _stream(stream)), "ne_recover")
+    return d
+
+
+def ne_extract(delta: torch.Tensor, d: torch.Tensor, *, l: int,
+               Nout: int | None = None, stream=None) -> torch.Tensor:
+    pdl, M, n, ldd = _rows(delta, "delta")
+    pd, _, _, ldo = _rows(d, "d")
+    w = _word_bits(delta)
+    _check(lib().ne_extract(pdl, ldd, M, n if Nout is None else Nout, w, l, pd,
+                            ldo, _stream(stream)), "ne_extract")
+    return d
+
+
+def ne_protected_conv(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
+                      l: int, max_abs_c: int, max_abs_g: int,
+                      failed: int = -1, fail_mode: int = NE_FAIL_NONE,
+                      ws: torch.Tensor | None = None, N: int | None = None,
+                      stream=None) -> torch.Tensor:
+    """Entangle-on-load -> conv -> extract/recover, one launch (d = c * g)."""
+    pc, M, n, ldc = _rows(c, "c")
+    pd, _, _, ldd = _rows(d, "d")
+    n = n if N is None else N
+    w = _word_bits(c)
+    K = g.numel()
+    need = ne_protected_conv_ws_bytes(M, n, K)
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=c.device)
+    _check(lib().ne_protected_conv(pc, ldc, M, n, ctypes.c_void_p(g.data_ptr()),
+                                   K, w, l, max_abs_c, max_abs_g, failed,
+                                   fail_mode, pd, ldd,
+                                   ctypes.c_void_p(ws.data_ptr()),
+                                   ws.numel() * ws.element_size(),
+                                   _stream(stream)), "ne_protected_conv")
+    return d
+
+
+def ne_checksum(c: torch.Tensor, r: torch.Tensor, *, N: int | None = None,
+                stream=None) -> torch.Tensor:
+    pc, M, n, ldc = _rows(c, "c")
+    w = _word_bits(c)
+    _check(lib().ne_checksum(pc, ldc, M, n if N is None else N, w,
+                             ctypes.c_void_p(r.data_ptr()), _stream(stream)),
+           "ne_checksum")
+    return r
+
+
+def ne_checksum_recover(d: torch.Tensor, e: torch.Tensor, out: torch.Tensor, *,
+                        f: int, Nout: int | None = None,
+                        stream=None) -> torch.Tensor:
+    pd, M, n, ldd = _rows(d, "d")
+    w = _word_bits(d)
+    _check(lib().ne_checksum_recover(pd, ldd, ctypes.c_void_p(e.data_ptr()), M,
+                                     n if Nout is None else Nout, w, f,
+                                     ctypes.c_void_p(out.data_ptr()),
+                                     _stream(stream)), "ne_checksum_recover")
+    return out
+
+
+def ne_scale(x: torch.Tensor, s: int, y: torch.Tensor | None = None, *,
+             stream=None) -> torch.Tensor:
+    y = x if y is None else y
+    px, M, n, ldx = _rows(x, "x")
+    py, _, _, ldy = _rows(y, "y")
+    _check(lib().ne_scale(px, ldx, M, n, int(s), _word_bits(x), py, ldy,
+                          _stream(stream)), "ne_scale")
+    return y
+
+
+def ne_add(x: torch.Tensor, z: torch.Tensor, y: torch.Tensor | None = None, *,
+           stream=None) -> torch.Tensor:
+    y = x if y is None else y
+    px, M, n, ldx = _rows(x, "x")
+    pz, _, _, ldz = _rows(z, "z")
+    py, _, _, ldy = _rows(y, "y")
+    _check(lib().ne_add(px, ldx, pz, ldz, M, n, _word_bits(x), py, ldy,
+                        _stream(stream)), "ne_add")
+    return y
+
+
+def ne_self_entangle(g: torch.Tensor, out: torch.Tensor, *, l: int,
+                     stream=None) -> torch.Tensor:
+    _check(lib().ne_self_entangle(ctypes.c_void_p(g.data_ptr()), g.numel(),
+                                  _word_bits(g), l,
+                                  ctypes.c_void_p(out.data_ptr()),
+                                  _stream(stream)), "ne_self_entangle")
+    return out
+
+
+def ne_permute(x: torch.Tensor, perm: torch.Tensor, y: torch.Tensor, *,
+               bad: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    px, M, n, ldx = _rows(x, "x")
+    py, _, _, ldy = _rows(y, "y")
+    if perm.dtype != torch.int64:
+        raise ValueError("perm must be int64")
+    _check(lib().ne_permute(px, ldx, M, n, ctypes.c_void_p(perm.data_ptr()),
+                            _word_bits(x), py, ldy,
+                            ctypes.c_void_p(bad.data_ptr() if bad is not None else 0),
+                            _stream(stream)), "ne_permute")
+    return y
+
+
+def ne_probe_imad_rate(kind: int, iters: int = 4096):
+    """(multiply-add instructions per second, launch ms) of probe `kind`."""
+    rate = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(lib().ne_probe_imad_rate(kind, iters, ctypes.byref(rate),
+                                    ctypes.byref(ms)), "ne_probe_imad_rate")
+    return rate.value, ms.value

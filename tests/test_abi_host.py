@@ -1,0 +1,165 @@
+"""libne.so loads, exports every symbol include/ne.h declares, and its
+host-only logic (parameter rule, range checks, argument validation) behaves
+as the paper fixes.  No call here launches a kernel: argument errors are
+returned on the host before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f)
+           for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def ne():
+    from paper_1509_03838_gb300 import build, ne as nemod
+    build.build()
+    return nemod
+
+
+def declared_symbols():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(ne_\w+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_hot_path_calls():
+    names = declared_symbols()
+    for required in ["ne_params", "ne_entangle", "ne_conv", "ne_extract",
+                     "ne_recover", "ne_protected_conv", "ne_checksum",
+                     "ne_checksum_recover"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(ne):
+    L = ctypes.CDLL(ne.LIB_PATH)
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header(ne):
+    ne.lib()
+    bound = set(ne._SIGS) | set(ne.EXTRA_SIGS)
+    assert set(declared_symbols()) <= bound
+
+
+def test_status_strings(ne):
+    assert ne.status_str(0) == "NE_OK"
+    assert ne.status_str(2) == "NE_ERR_RANGE"
+    assert ne.status_str(99) == "NE_ERR_UNKNOWN"
+
+
+def _table1():
+    rows = []
+    for line in open(os.path.join(ROOT, "tests", "golden", "table1_w32.txt")):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(tuple(int(v) for v in line.split()))
+    return rows
+
+
+@pytest.mark.parametrize("row", _table1())
+def test_library_params_reproduce_table1(ne, row):
+    M, l, k, proposed, _ = row
+    p = ne.ne_params(M, 32)
+    assert (p.l, p.k) == (l, k)
+    assert (M - 2) * p.l + p.k == proposed
+
+
+@pytest.mark.parametrize("w", [32, 64])
+@pytest.mark.parametrize("M", list(range(3, 17)) + [32])
+def test_library_params_agree_with_oracle(ne, orc, M, w):
+    """The library's closed-form rule and the oracle's exhaustive search are
+    independent implementations of the same rule."""
+    try:
+        ol, ok, odp, ode = orc.params(M, w)
+    except ValueError:
+        with pytest.raises(ne.NEError):
+            ne.ne_params(M, w)
+        return
+    p = ne.ne_params(M, w)
+    assert (p.l, p.k, p.d_max_paper, p.d_max_exact) == (ol, ok, odp, ode)
+
+
+def test_choose_width(ne):
+    # |d| <= K * 2^7 * 2^7 = 2^18 for K = 16: 32-bit words suffice (Eq. 13)
+    assert ne.ne_choose_width(3, 16, 1 << 7, 1 << 7).w == 32
+    # 16-bit data and taps, K = 64: 2^36 needs 64-bit words
+    assert ne.ne_choose_width(4, 64, 1 << 15, 1 << 15).w == 64
+    with pytest.raises(ne.NEError) as ei:
+        ne.ne_choose_width(4, 1 << 20, 1 << 31, 1 << 31)
+    assert ei.value.status == ne.NE_ERR_RANGE
+
+
+def test_bad_params(ne):
+    for M, w in [(2, 32), (33, 32), (4, 16), (4, 0)]:
+        with pytest.raises(ne.NEError) as ei:
+            ne.ne_params(M, w)
+        assert ei.value.status == ne.NE_ERR_INVALID_ARG
+
+
+DUMMY = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails first
+
+
+def test_argument_errors_return_before_launch(ne):
+    L = ne.lib()
+    s = ctypes.c_void_p(0)
+    # M < 3
+    assert L.ne_entangle(DUMMY, 8, DUMMY, 8, 2, 8, 64, 16, s) == ne.NE_ERR_INVALID_ARG
+    # l out of range
+    assert L.ne_entangle(DUMMY, 8, DUMMY, 8, 3, 8, 32, 32, s) == ne.NE_ERR_INVALID_ARG
+    # K = 0, K too large
+    assert L.ne_conv(DUMMY, 8, 3, 8, DUMMY, 0, DUMMY, 8, 64, 0, 7, s) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_conv(DUMMY, 8, 3, 8, DUMMY, 9000, DUMMY, 9100, 64, 0, 7, s) == ne.NE_ERR_INVALID_ARG
+    # output leading dimension shorter than N + K - 1
+    assert L.ne_conv(DUMMY, 8, 3, 8, DUMMY, 4, DUMMY, 10, 64, 0, 7, s) == ne.NE_ERR_INVALID_ARG
+    # failed index out of range
+    assert L.ne_recover(DUMMY, 8, 4, 8, 64, 16, 4, DUMMY, 8, s) == ne.NE_ERR_INVALID_ARG
+    # (M-1) l > w
+    assert L.ne_recover(DUMMY, 8, 4, 8, 32, 11, 0, DUMMY, 8, s) == ne.NE_ERR_INVALID_ARG
+
+
+def test_protected_conv_range_and_failure_checks(ne):
+    L = ne.lib()
+    s = ctypes.c_void_p(0)
+    p = ne.ne_params(4, 64)
+    # K * max|c| * max|g| beyond the exact limit -> NE_ERR_RANGE
+    st = L.ne_protected_conv(DUMMY, 1 << 20, 4, 1 << 20, DUMMY, 64, 64, p.l,
+                             1 << 30, 1 << 30, -1, ne.NE_FAIL_NONE, DUMMY,
+                             (1 << 20) + 63, DUMMY, 1 << 20, s)
+    assert st == ne.NE_ERR_RANGE
+    # failure mode without a stream, and a stream without a mode
+    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, 100, 100,
+                             -1, ne.NE_FAIL_SKIP, DUMMY, 71, DUMMY, 1 << 20, s)
+    assert st == ne.NE_ERR_INVALID_ARG
+    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, 100, 100,
+                             2, ne.NE_FAIL_NONE, DUMMY, 71, DUMMY, 1 << 20, s)
+    assert st == ne.NE_ERR_INVALID_ARG
+    # workspace too small
+    need = ne.ne_protected_conv_ws_bytes(4, 64, 8)
+    assert need > 0
+    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, 100, 100,
+                             -1, ne.NE_FAIL_NONE, ctypes.c_void_p(0x100000), 71,
+                             DUMMY, need - 1, s)
+    assert st == ne.NE_ERR_NOMEM
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    """With libne.so absent, the binding raises instead of computing on the
+    CPU."""
+    import importlib
+    from paper_1509_03838_gb300 import ne as nemod
+    fresh = importlib.reload(nemod)
+    monkeypatch.setattr(fresh, "LIB_PATH", str(tmp_path / "libne.so"))
+    monkeypatch.setattr(fresh, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        fresh.ne_params(3, 32)
+    importlib.reload(nemod)

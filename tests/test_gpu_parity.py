@@ -1,0 +1,431 @@
+"""GPU parity: every kernel of the hot path against the CPU oracle, bit-exact.
+
+Sizes span several 3072-sample output tiles with ragged tails; edge cases
+cover N = 0, N < K, K = 1, the maximum K, unaligned rows (scalar paths),
+in-place operation and every failed-stream index under every failure mode.
+"""
+import numpy as np
+import pytest
+
+from paper_1509_03838_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TILE = 3072
+
+
+@pytest.fixture(scope="module")
+def ne():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_03838_gb300 import build, ne as nemod
+    build.build()
+    return nemod
+
+
+def dt(w):
+    return torch.int32 if w == 32 else torch.int64
+
+
+def dev(a, w, ld=None):
+    """numpy [rows, n] -> CUDA tensor of w-bit words, optional padded ld."""
+    a = np.asarray(a, dtype=np.int64)
+    if a.ndim == 1:
+        a = a[None, :]
+    rows, n = a.shape
+    if ld is None:
+        ld = n
+    buf = torch.zeros((rows, ld), dtype=dt(w))
+    buf[:, :n] = torch.from_numpy(a.astype(np.int32 if w == 32 else np.int64))
+    return buf.cuda()[:, :n]
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.int64)
+
+
+def taps(g):
+    return torch.from_numpy(np.asarray(g, dtype=np.int32)).cuda()
+
+
+def job(seed, M, N, K, w, bits=None):
+    p = None
+    if bits is None:
+        import math
+        from oracle import oracle as o
+        l, k, dp, de = o.params(M, w)
+        bits = max(1, (int(math.log2(max(dp, 2))) - max(1, int(math.log2(K)))) // 2 - 1)
+    gen = synth.rng(seed)
+    c = synth.uniform_int(gen, (M, N), -(1 << bits), 1 << bits)
+    g = synth.uniform_int(gen, (K,), -(1 << bits), 1 << bits)
+    return c, g, 1 << bits
+
+
+# ---------------------------------------------------------------------------
+# entanglement
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("w,M", [(32, 3), (32, 4), (32, 5), (32, 8), (32, 16),
+                                 (64, 3), (64, 4), (64, 6), (64, 8)])
+@pytest.mark.parametrize("N,pad", [(1, 0), (7, 0), (2 * TILE + 5, 0),
+                                   (1000, 3)])
+def test_entangle(ne, orc, w, M, N, pad):
+    l = ne.ne_params(M, w).l
+    c, _, _ = job(w + M + N, M, N, 1, w)
+    expect = orc.entangle(c, w, l)
+    x = dev(c, w, ld=N + pad)
+    out = torch.empty_like(x)
+    ne.ne_entangle(x, out, l=l)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(out), expect)
+    ne.ne_entangle(x, l=l)  # in place
+    torch.cuda.synchronize()
+    assert np.array_equal(host(x), expect)
+
+
+# ---------------------------------------------------------------------------
+# convolution (all three arithmetic modes)
+# ---------------------------------------------------------------------------
+
+CONV_CASES = [
+    # w, M, N, K, input bits, declared bound (0 = unknown)
+    (32, 3, 2 * TILE + 77, 16, 7, 1 << 7),          # int32 words
+    (32, 4, 5000, 1, 12, 1 << 12),                  # K = 1
+    (64, 4, 3 * TILE + 1, 64, 15, 1 << 15),         # 64-bit, |x| < 2^31
+    (64, 4, 3 * TILE + 1, 64, 15, 0),               # 64-bit, split operands
+    (64, 3, 4000, 17, 40, 0),                       # wide entangled-size words
+    (64, 5, 513, 300, 20, 0),                       # N < K + tile
+    (64, 3, 9, 200, 20, 0),                         # N < K
+    (32, 3, 100, 8192, 5, 1 << 5),                  # maximum K
+]
+
+
+@pytest.mark.parametrize("case", CONV_CASES)
+def test_conv(ne, orc, case):
+    w, M, N, K, bits, bound = case
+    gen = synth.rng(N * 7 + K)
+    x = synth.uniform_int(gen, (M, N), -(1 << bits), 1 << bits)
+    g = synth.uniform_int(gen, (K,), -(1 << 15), 1 << 15)
+    expect = orc.conv(x, g, w, strict=False)
+    y = torch.zeros((M, N + K - 1), dtype=dt(w), device="cuda")
+    ne.ne_conv(dev(x, w), taps(g), y, max_abs_x=bound)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), expect)
+
+
+def test_conv_wraps_like_the_oracle(ne, orc):
+    """Full-range 64-bit words: products overflow, results agree mod 2^64."""
+    gen = synth.rng(99)
+    M, N, K, w = 3, 2000, 40, 64
+    x = synth.uniform_int(gen, (M, N), -(1 << 62), 1 << 62)
+    g = synth.uniform_int(gen, (K,), -(1 << 31), 1 << 31)
+    expect = orc.conv(x, g, w, strict=False)
+    y = torch.zeros((M, N + K - 1), dtype=torch.int64, device="cuda")
+    ne.ne_conv(dev(x, w), taps(g), y)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), expect)
+
+
+def test_conv_live_mask_and_unaligned(ne, orc):
+    gen = synth.rng(5)
+    M, N, K, w = 5, 3 * TILE - 3, 33, 64
+    x = synth.uniform_int(gen, (M, N), -(1 << 20), 1 << 20)
+    g = synth.uniform_int(gen, (K,), -(1 << 15), 1 << 15)
+    expect = orc.conv(x, g, w)
+    xd = dev(x, w, ld=N + 1)  # odd leading dimension: scalar path
+    y = torch.full((M, N + K), -7, dtype=torch.int64, device="cuda")[:, :N + K - 1]
+    ne.ne_conv(xd, taps(g), y, live_mask=0b10110)
+    torch.cuda.synchronize()
+    got = host(y)
+    for m in range(M):
+        if (0b10110 >> m) & 1:
+            assert np.array_equal(got[m], expect[m])
+        else:
+            assert np.all(got[m] == -7)  # a stream that was not run
+
+
+def test_conv_empty(ne):
+    x = torch.zeros((3, 0), dtype=torch.int64, device="cuda")
+    y = torch.zeros((3, 15), dtype=torch.int64, device="cuda")
+    g = taps(np.ones(16))
+    ne.ne_conv(x, g, y)
+    torch.cuda.synchronize()
+
+
+# ---------------------------------------------------------------------------
+# recovery / extraction
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("w,M", [(32, 3), (32, 4), (32, 8), (32, 11),
+                                 (64, 3), (64, 4), (64, 5), (64, 6), (64, 7),
+                                 (64, 8), (64, 10)])
+def test_recover_every_r(ne, orc, w, M):
+    p = ne.ne_params(M, w)
+    gen = synth.rng(w * M)
+    N = 2 * TILE + 3
+    d = synth.uniform_int(gen, (M, N), -p.d_max_exact, p.d_max_exact + 1)
+    d[:, 0] = p.d_max_exact
+    d[:, 1] = -p.d_max_exact
+    delta = orc.entangle(d, w, p.l)  # entangled outputs of an identity op
+    dd = dev(delta, w)
+    for r in range(M):
+        expect = orc.recover(delta, w, p.l, r)
+        assert np.array_equal(expect, d)
+        out = torch.empty_like(dd)
+        ne.ne_recover(dd, out, l=p.l, failed=r)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(out), expect), r
+    # the failed row is never read: poison it
+    poisoned = dd.clone()
+    poisoned[1] = 12345
+    out = torch.empty_like(dd)
+    ne.ne_recover(poisoned, out, l=p.l, failed=1)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(out), d)
+    # extraction (no failure) and in-place recovery
+    ne.ne_extract(dd, out, l=p.l)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(out), d)
+    ne.ne_recover(dd, dd, l=p.l, failed=M - 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(dd), d)
+
+
+def test_recover_unaligned_rows(ne, orc):
+    w, M = 64, 4
+    p = ne.ne_params(M, w)
+    gen = synth.rng(3)
+    d = synth.uniform_int(gen, (M, 1001), -p.d_max_paper, p.d_max_paper + 1)
+    delta = orc.entangle(d, w, p.l)
+    dd = dev(delta, w, ld=1003)
+    out = dev(np.zeros_like(d), w, ld=1005)
+    ne.ne_recover(dd, out, l=p.l, failed=2)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(out), d)
+
+
+# ---------------------------------------------------------------------------
+# fused protected convolution
+# ---------------------------------------------------------------------------
+
+PROT_CASES = [
+    # w, M, N, K, data bits, tap bits
+    (32, 3, 4096, 16, 7, 7),          # the small int32 workload shape
+    (64, 4, 3 * TILE + 11, 64, 15, 15),  # 16-bit data, 64-bit words (split)
+    (64, 8, 2 * TILE + 1, 37, 15, 15),   # M = 8: |eps| < 2^31 (wide)
+    (64, 5, TILE - 1, 1024, 12, 12),     # long kernel, one tile
+    (32, 4, 777, 5, 6, 6),
+    (64, 3, 50, 100, 15, 15),            # N < K
+]
+
+
+@pytest.mark.parametrize("case", PROT_CASES)
+def test_protected_conv_all_failures(ne, orc, case):
+    w, M, N, K, bc, bg = case
+    p = ne.ne_params(M, w)
+    gen = synth.rng(N + K + M)
+    c = synth.uniform_int(gen, (M, N), -(1 << bc), 1 << bc)
+    g = synth.uniform_int(gen, (K,), -(1 << bg), 1 << bg)
+    plain = orc.conv(c, g, w)
+    cd, gd = dev(c, w), taps(g)
+    modes = [(ne.NE_FAIL_NONE, -1)] + [(fm, r) for fm in (ne.NE_FAIL_SKIP,
+                                                          ne.NE_FAIL_DROP)
+                                       for r in range(M)]
+    for fm, r in modes:
+        # the oracle's step-by-step method gives the same result
+        if r >= 0:
+            _, _, d_or = orc.protected_conv(c, g, w, p.l, r)
+            assert np.array_equal(d_or, plain)
+        d = torch.full((M, N + K - 1), 99, dtype=dt(w), device="cuda")
+        ne.ne_protected_conv(cd, gd, d, l=p.l, max_abs_c=1 << bc,
+                             max_abs_g=1 << bg, failed=r, fail_mode=fm)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), plain), (fm, r)
+
+
+def test_protected_conv_repeat_reuses_workspace(ne, orc):
+    w, M, N, K = 64, 4, 2 * TILE, 64
+    p = ne.ne_params(M, w)
+    c, g, b = job(17, M, N, K, w, bits=15)
+    plain = orc.conv(c, g, w)
+    ws = torch.empty(ne.ne_protected_conv_ws_bytes(M, N, K), dtype=torch.uint8,
+                     device="cuda")
+    cd, gd = dev(c, w), taps(g)
+    for it in range(3):
+        d = torch.zeros((M, N + K - 1), dtype=torch.int64, device="cuda")
+        ne.ne_protected_conv(cd, gd, d, l=p.l, max_abs_c=b, max_abs_g=b,
+                             failed=it % M, fail_mode=ne.NE_FAIL_DROP, ws=ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), plain)
+
+
+def test_protected_conv_range_error(ne):
+    w, M = 32, 3
+    p = ne.ne_params(M, w)
+    c = torch.zeros((M, 64), dtype=torch.int32, device="cuda")
+    g = taps(np.ones(16))
+    d = torch.zeros((M, 79), dtype=torch.int32, device="cuda")
+    with pytest.raises(ne.NEError) as ei:
+        ne.ne_protected_conv(c, g, d, l=p.l, max_abs_c=1 << 10,
+                             max_abs_g=1 << 10)
+    assert ei.value.status == ne.NE_ERR_RANGE
+
+
+# ---------------------------------------------------------------------------
+# checksum ABFT baseline
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("w,M", [(32, 3), (64, 4), (64, 8)])
+def test_checksum_path(ne, orc, w, M):
+    gen = synth.rng(M)
+    N, K = 2 * TILE + 9, 48
+    c = synth.uniform_int(gen, (M, N), -(1 << 12), 1 << 12)
+    g = synth.uniform_int(gen, (K,), -(1 << 12), 1 << 12)
+    buf = torch.zeros((M + 1, N), dtype=dt(w), device="cuda")
+    buf[:M] = dev(c, w)
+    ne.ne_checksum(buf[:M], buf[M])
+    torch.cuda.synchronize()
+    assert np.array_equal(host(buf[M]), orc.checksum(c, w))
+    out = torch.zeros((M + 1, N + K - 1), dtype=dt(w), device="cuda")
+    ne.ne_conv(buf, taps(g), out, max_abs_x=M << 12)
+    plain = orc.conv(c, g, w)
+    e = out[M].clone()
+    for f in range(M):
+        rec = torch.zeros(N + K - 1, dtype=dt(w), device="cuda")
+        ne.ne_checksum_recover(out[:M], e, rec, f=f)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(rec), plain[f])
+
+
+# ---------------------------------------------------------------------------
+# element-wise LSB ops (Eq. 2) on entangled streams
+# ---------------------------------------------------------------------------
+
+def test_elementwise_ops(ne, orc):
+    w, M = 64, 5
+    p = ne.ne_params(M, w)
+    gen = synth.rng(8)
+    N = TILE + 13
+    c = synth.uniform_int(gen, (M, N), -(1 << 12), 1 << 12)
+    c2 = synth.uniform_int(gen, (M, N), -(1 << 12), 1 << 12)
+    e = orc.entangle(c, w, p.l)
+    e2 = orc.entangle(c2, w, p.l)
+    ed, e2d = dev(e, w), dev(e2, w)
+    y = torch.empty_like(ed)
+    ne.ne_scale(ed, -93, y)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), orc.scale(e, -93, w))
+    z = torch.empty_like(ed)
+    ne.ne_add(y, e2d, z)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(z), orc.add(orc.scale(e, -93, w), e2, w))
+    perm = gen.permutation(N).astype(np.int64)
+    out = torch.empty_like(ed)
+    bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ne.ne_permute(z, torch.from_numpy(perm).cuda(), out, bad=bad)
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 0
+    assert np.array_equal(host(out), orc.permute(host(z), perm))
+    g = synth.uniform_int(gen, (N,), -(1 << 10), 1 << 10)
+    ge = torch.empty(N, dtype=torch.int64, device="cuda")
+    ne.ne_self_entangle(torch.from_numpy(g).cuda(), ge, l=p.l)
+    torch.cuda.synchronize()
+    assert np.array_equal(ge.cpu().numpy(), orc.self_entangle(g, w, p.l))
+
+
+def test_permute_bad_index_is_counted(ne):
+    x = torch.arange(10, dtype=torch.int64, device="cuda").reshape(1, 10)
+    perm = torch.tensor([0, 1, 2, 3, 4, 5, 6, 7, 8, 10], dtype=torch.int64,
+                        device="cuda")
+    y = torch.empty_like(x)
+    bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ne.ne_permute(x, perm, y, bad=bad)
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 1 and int(y[0, 9].item()) == 0
+
+
+# ---------------------------------------------------------------------------
+# the two stream workloads end to end
+# ---------------------------------------------------------------------------
+
+def test_small_workload_every_failure(ne, orc):
+    """M=3 int32 streams, N=4096, K=16, data and taps in [-2^7, 2^7)."""
+    j = synth.small_job(seed=1)
+    p = ne.ne_choose_width(j.M, j.K, j.bound_c, j.bound_g)
+    assert p.w == 32 and (p.l, p.k) == (11, 10)
+    plain = orc.conv(j.c, j.g, 32)
+    # separate kernels: entangle -> conv (failed stream not run) -> recover
+    cd = dev(j.c, 32)
+    eps = torch.empty_like(cd)
+    ne.ne_entangle(cd, eps, l=p.l)
+    for r in range(j.M):
+        delta = torch.full((j.M, j.N + j.K - 1), 5, dtype=torch.int32,
+                           device="cuda")
+        ne.ne_conv(eps, taps(j.g), delta, max_abs_x=j.bound_c * (1 + 2 ** p.l),
+                   live_mask=0b111 & ~(1 << r))
+        d = torch.empty_like(delta)
+        ne.ne_recover(delta, d, l=p.l, failed=r)
+        torch.cuda.synchronize()
+        eps_o, delta_o, d_o = orc.protected_conv(j.c, j.g, 32, p.l, r)
+        assert np.array_equal(host(eps), eps_o)
+        got_delta = host(delta)
+        for m in range(j.M):
+            if m != r:
+                assert np.array_equal(got_delta[m], delta_o[m])
+        assert np.array_equal(host(d), d_o)
+        assert np.array_equal(d_o, plain)
+
+
+def test_large_workload_full_size(ne, orc):
+    """M=4 streams of N=2^22, K=64, 16-bit data and taps, 64-bit words, every
+    stream failed in turn through the fused launch.  Entanglement and
+    recovery are checked on every sample; the convolution at seeded sample
+    positions (plus the ends) against the oracle's per-output sum."""
+    j = synth.large_job(seed=2)
+    M, N, K = j.M, j.N, j.K
+    p = ne.ne_params(M, 64)
+    cd, gd = dev(j.c, 64), taps(j.g)
+    gen = synth.rng(12345)
+    pos = np.unique(np.concatenate([
+        gen.integers(0, N + K - 1, size=200), [0, 1, K - 2, K - 1, N - 1,
+                                               N, N + K - 3, N + K - 2]]))
+    expect = np.stack([orc.conv_at(j.c[m], j.g, 64, pos) for m in range(M)])
+    # entanglement on every sample
+    eps = torch.empty_like(cd)
+    ne.ne_entangle(cd, eps, l=p.l)
+    torch.cuda.synchronize()
+    eps_h = host(eps)
+    assert np.array_equal(eps_h, orc.entangle(j.c, 64, p.l))
+    # convolution of the entangled streams at sampled outputs
+    delta = torch.empty((M, N + K - 1), dtype=torch.int64, device="cuda")
+    ne.ne_conv(eps, gd, delta)
+    torch.cuda.synchronize()
+    dh = host(delta)
+    for m in range(M):
+        assert np.array_equal(dh[m, pos], orc.conv_at(eps_h[m], j.g, 64, pos))
+    # recovery on every sample, against the oracle's recovery of the same delta
+    for r in range(M):
+        d = torch.empty_like(delta)
+        ne.ne_recover(delta, d, l=p.l, failed=r)
+        torch.cuda.synchronize()
+        dh_r = host(d)
+        assert np.array_equal(dh_r[:, pos], expect)
+        if r == 0:
+            assert np.array_equal(dh_r, orc.recover(dh, 64, p.l, r))
+    del delta
+    # the fused launch, every stream failed in turn (late result dropped)
+    ws = torch.empty(ne.ne_protected_conv_ws_bytes(M, N, K), dtype=torch.uint8,
+                     device="cuda")
+    ref = None
+    for r in range(M):
+        d = torch.empty((M, N + K - 1), dtype=torch.int64, device="cuda")
+        ne.ne_protected_conv(cd, gd, d, l=p.l, max_abs_c=j.bound_c,
+                             max_abs_g=j.bound_g, failed=r,
+                             fail_mode=ne.NE_FAIL_DROP, ws=ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d[:, pos]), expect)
+        if ref is None:
+            ref = d
+        else:
+            assert torch.equal(d, ref)  # the unique result, whatever failed
