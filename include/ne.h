@@ -29,6 +29,8 @@
  *   - Arithmetic is modulo 2^w (two's complement).  Results equal the exact
  *     integers whenever every true output d satisfies |d| <= d_max_exact of
  *     ne_params(); beyond that the outputs are defined (no fault) but wrong.
+ *   - N = 0 (or Nout = 0) is a valid no-op: nothing is read or written and
+ *     data pointers may be NULL.
  *   - No call blocks the host, allocates device memory, or spins on the
  *     device.
  */

@@ -16,10 +16,13 @@ extern "C" {
  *   kind 0: 32-bit multiply-add (mad.lo.u32)
  *   kind 1: 32x32->64 multiply-add (mad.wide.s32)
  *   kind 2: one of each per round (two instructions)
+ *   kind 3: mad.lo.cc.u32 + madc.hi.s32 per round, a 64-bit accumulation
+ *           by carry chain (two instructions)
+ *   kind 4: mad.wide.s32 + fma.rn.f32 per round (two instructions)
  * and return the best of three timed launches (after one warm-up) as
  * multiply-add instructions per second in *instr_per_s (and the launch time
  * in *elapsed_ms if non-NULL).  Unlike the compute calls of ne.h this call
- * allocates 8 bytes of device memory, uses the legacy default stream and
+ * allocates an 8-byte-per-thread result buffer, uses the legacy default stream and
  * blocks until the launches finish.  Returns NE_OK, NE_ERR_INVALID_ARG or
  * NE_ERR_CUDA.
  */

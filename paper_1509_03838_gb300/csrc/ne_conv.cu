@@ -279,15 +279,20 @@ conv_kernel(const ConvArgs p) {
     const uint32_t full = p.M >= 32 ? 0xffffffffu : ((1u << p.M) - 1u);
     const int r = __ffs((int)(~(uint32_t)mask & full)) - 1;
     const int64_t end = min(n0 + (int64_t)CONV_TILE, p.Nout);
-    constexpr int V = VEC ? Vec<W>::n : 1;
-    const int64_t vend = n0 + ((end - n0) / V) * V;
-    for (int64_t n = n0 + (int64_t)threadIdx.x * V; n < vend;
-         n += (int64_t)CONV_THREADS * V)
-      recover_columns<W, 0, V, true>(ybase, p.ldy, p.M, n, p.l, r, ybase,
-                                     p.ldy);
-    for (int64_t n = vend + threadIdx.x; n < end; n += CONV_THREADS)
-      recover_columns<W, 0, 1, true>(ybase, p.ldy, p.M, n, p.l, r, ybase,
-                                     p.ldy);
+    if (p.M <= 9) {
+      // thread t owns columns n0 + t + 256 i: every warp access is one
+      // contiguous 256-byte (int64) or 128-byte (int32) segment
+      constexpr int NV = 4;
+#pragma unroll 1
+      for (int64_t n = n0 + threadIdx.x; n < end;
+           n += (int64_t)CONV_THREADS * NV)
+        recover_columns_batched<W, NV, 8>(ybase, p.ldy, p.M, n, CONV_THREADS,
+                                          end, p.l, r, ybase, p.ldy);
+    } else {
+      for (int64_t n = n0 + threadIdx.x; n < end; n += CONV_THREADS)
+        recover_columns<W, 0, 1, true>(ybase, p.ldy, p.M, n, p.l, r, ybase,
+                                       p.ldy);
+    }
   }
 }
 
@@ -357,12 +362,12 @@ extern "C" {
 int ne_conv(const void* x, int64_t ldx, int M, int64_t N, const int32_t* g,
             int K, void* y, int64_t ldy, int w, int64_t max_abs_x,
             uint32_t live_mask, void* stream) {
-  if (!x || !y || !g || M < 1 || M > 32 || N < 0 || K < 1 ||
-      K > CONV_MAX_K || ldx < N || (w != 32 && w != 64) || max_abs_x < 0)
+  if (M < 1 || M > 32 || N < 0 || K < 1 || K > CONV_MAX_K || ldx < N ||
+      (w != 32 && w != 64) || max_abs_x < 0)
     return NE_ERR_INVALID_ARG;
+  if (N == 0) return NE_OK;  // nothing to convolve; no output is written
   const int64_t Nout = N + K - 1;
-  if (ldy < Nout) return NE_ERR_INVALID_ARG;
-  if (N == 0) return NE_OK;
+  if (!x || !y || !g || ldy < Nout) return NE_ERR_INVALID_ARG;
   const int wb = w / 8;
   if (overlaps(x, rows_bytes(M, ldx, N, wb), y, rows_bytes(M, ldy, Nout, wb)))
     return NE_ERR_INVALID_ARG;
@@ -397,9 +402,9 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
                       int64_t max_abs_c, int64_t max_abs_g, int failed,
                       int fail_mode, void* d, int64_t ldd, void* ws,
                       size_t ws_bytes, void* stream) {
-  if (!c || !g || !d || M < 3 || M > 32 || N < 0 || K < 1 ||
-      K > CONV_MAX_K || ldc < N || (w != 32 && w != 64) || l <= 0 ||
-      l >= w || (M - 1) * l > w || max_abs_c < 0 || max_abs_g < 0)
+  if (M < 3 || M > 32 || N < 0 || K < 1 || K > CONV_MAX_K || ldc < N ||
+      (w != 32 && w != 64) || l <= 0 || l >= w || (M - 1) * l > w ||
+      max_abs_c < 0 || max_abs_g < 0)
     return NE_ERR_INVALID_ARG;
   if (fail_mode != NE_FAIL_NONE && fail_mode != NE_FAIL_SKIP &&
       fail_mode != NE_FAIL_DROP)
@@ -407,13 +412,13 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   if (fail_mode == NE_FAIL_NONE ? failed != -1 : (failed < 0 || failed >= M))
     return NE_ERR_INVALID_ARG;
   const int64_t Nout = N + K - 1;
-  if (ldd < Nout) return NE_ERR_INVALID_ARG;
   // dynamic range (Eq. 13 / exact limit): |d| <= K max|c| max|g|
   const unsigned __int128 need = (unsigned __int128)K *
                                  (unsigned __int128)max_abs_c *
                                  (unsigned __int128)max_abs_g;
   if (need > exact_limit(M, w, l)) return NE_ERR_RANGE;
-  if (N == 0) return NE_OK;
+  if (N == 0) return NE_OK;  // nothing to convolve; no output is written
+  if (!c || !g || !d || ldd < Nout) return NE_ERR_INVALID_ARG;
   const int wb = w / 8;
   if (overlaps(c, rows_bytes(M, ldc, N, wb), d, rows_bytes(M, ldd, Nout, wb)))
     return NE_ERR_INVALID_ARG;

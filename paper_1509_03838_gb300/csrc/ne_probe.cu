@@ -2,10 +2,15 @@
 // convolution's roofline.  Every thread runs eight independent chains of
 // one kind of multiply-add for `iters` rounds; the host times the launch
 // with CUDA events and reports multiply-add instructions per second.
+// 8 blocks x 256 threads per SM give 16 warps per scheduler, each with 8
+// independent chains, enough to cover the multiply-add latency.
 //   kind 0: mad.lo.u32      (32-bit multiply-add, the w = 32 MAC)
 //   kind 1: mad.wide.s32    (32x32->64 multiply-add, the |x| < 2^31 MAC)
 //   kind 2: mad.wide.s32 + mad.lo.u32 per round (the split 64-bit MAC;
 //           counted as two instructions)
+//   kind 3: mad.lo.cc.u32 + madc.hi.s32 per round (a 64-bit multiply-add
+//           as a carry chain; two instructions)
+//   kind 4: mad.wide.s32 + fma.rn.f32 per round (two instructions)
 #include "ne_common.cuh"
 
 namespace ne {
@@ -14,32 +19,54 @@ namespace {
 template <int KIND>
 __global__ void __launch_bounds__(256) imad_probe_kernel(int iters, int seed,
                                                          unsigned long long* sink) {
+  // Non-linear recurrences (each multiplicand is the chain's own previous
+  // value), so no multiply can be hoisted, strength-reduced or folded.
   unsigned a32[8];
   unsigned long long a64[8];
-  const int b = (int)(threadIdx.x * 2654435761u) | 1;
-  const int c = seed + (int)blockIdx.x;
+  const unsigned b = (threadIdx.x * 2654435761u) | 1u;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    a32[k] = (unsigned)(k + threadIdx.x);
-    a64[k] = (unsigned long long)(k * 7 + blockIdx.x);
+    a32[k] = (unsigned)(k + threadIdx.x + seed);
+    a64[k] = (unsigned long long)(k * 7 + blockIdx.x + seed);
   }
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       if constexpr (KIND == 0) {
-        asm("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a32[k]) : "r"(b), "r"(c));
+        // a = a * a + b
+        asm volatile("mad.lo.u32 %0, %0, %0, %1;" : "+r"(a32[k]) : "r"(b));
       } else if constexpr (KIND == 1) {
-        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a64[k]) : "r"(b + k), "r"(c));
+        // A = lo(A) * b + A   (32x32->64)
+        asm volatile("{\n\t.reg .u32 t;\n\tcvt.u32.u64 t, %0;\n\t"
+                     "mad.wide.s32 %0, t, %1, %0;\n\t}"
+                     : "+l"(a64[k]) : "r"(b));
+      } else if constexpr (KIND == 2) {
+        asm volatile("{\n\t.reg .u32 t;\n\tcvt.u32.u64 t, %0;\n\t"
+                     "mad.wide.s32 %0, t, %1, %0;\n\t}"
+                     : "+l"(a64[k]) : "r"(b));
+        asm volatile("mad.lo.u32 %0, %0, %0, %1;" : "+r"(a32[k]) : "r"(b));
+      } else if constexpr (KIND == 3) {
+        // 64-bit accumulate as a carry chain: lo += (x*b).lo, hi += (x*b).hi + c
+        asm volatile("{\n\t.reg .u32 lo, hi;\n\tmov.b64 {lo, hi}, %0;\n\t"
+                     "mad.lo.cc.u32 lo, lo, %1, lo;\n\t"
+                     "madc.hi.s32 hi, lo, %1, hi;\n\t"
+                     "mov.b64 %0, {lo, hi};\n\t}"
+                     : "+l"(a64[k]) : "r"(b));
       } else {
-        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a64[k]) : "r"(b + k), "r"(c));
-        asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(a32[k]) : "r"(b - k), "r"(c));
+        // a 32x32->64 multiply-add beside an fp32 fused multiply-add
+        asm volatile("{\n\t.reg .u32 t;\n\tcvt.u32.u64 t, %0;\n\t"
+                     "mad.wide.s32 %0, t, %1, %0;\n\t}"
+                     : "+l"(a64[k]) : "r"(b));
+        float f = __uint_as_float(a32[k]);
+        asm volatile("fma.rn.f32 %0, %0, %0, %1;" : "+f"(f) : "f"(1.0f));
+        a32[k] = __float_as_uint(f);
       }
     }
   }
   unsigned long long s = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) s += a32[k] + a64[k];
-  if (s == 0x9e3779b97f4a7c15ull) sink[0] = s;  // keep the chains live
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keep every chain live
 }
 
 }  // namespace
@@ -49,14 +76,15 @@ using namespace ne;
 
 extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
                                   double* elapsed_ms) {
-  if (!instr_per_s || kind < 0 || kind > 2 || iters < 1)
+  if (!instr_per_s || kind < 0 || kind > 4 || iters < 1)
     return NE_ERR_INVALID_ARG;
   const int sms = sm_count();
   const int blocks = sms * 8;
   unsigned long long* sink = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int st = NE_OK;
-  if (cudaMalloc(&sink, sizeof(unsigned long long)) != cudaSuccess)
+  if (cudaMalloc(&sink, (size_t)blocks * 256 * sizeof(unsigned long long)) !=
+      cudaSuccess)
     return NE_ERR_CUDA;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     st = NE_ERR_CUDA;
@@ -65,7 +93,9 @@ extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
     cudaEventRecord(e0, 0);
     if (kind == 0) imad_probe_kernel<0><<<blocks, 256>>>(iters, rep, sink);
     else if (kind == 1) imad_probe_kernel<1><<<blocks, 256>>>(iters, rep, sink);
-    else imad_probe_kernel<2><<<blocks, 256>>>(iters, rep, sink);
+    else if (kind == 2) imad_probe_kernel<2><<<blocks, 256>>>(iters, rep, sink);
+    else if (kind == 3) imad_probe_kernel<3><<<blocks, 256>>>(iters, rep, sink);
+    else imad_probe_kernel<4><<<blocks, 256>>>(iters, rep, sink);
     cudaEventRecord(e1, 0);
     if (cudaEventSynchronize(e1) != cudaSuccess) { st = NE_ERR_CUDA; break; }
     float ms = 0.f;
@@ -74,7 +104,7 @@ extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
   }
   if (st == NE_OK && cudaGetLastError() != cudaSuccess) st = NE_ERR_CUDA;
   if (st == NE_OK) {
-    const double per_round = kind == 2 ? 16.0 : 8.0;
+    const double per_round = (kind >= 2) ? 16.0 : 8.0;
     const double instr = (double)blocks * 256.0 * (double)iters * per_round;
     *instr_per_s = instr / (best * 1e-3);
     if (elapsed_ms) *elapsed_ms = best;

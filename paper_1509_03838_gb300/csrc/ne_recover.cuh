@@ -130,4 +130,63 @@ __device__ __forceinline__ void recover_columns(const W* delta, int64_t ldd,
   store_words<W, V>(d + (int64_t)r * ldo + n, dcur);
 }
 
+// Recover NV columns n + i*cstride (i < NV) at once, all M-1 delta rows held
+// in registers (requires M - 1 <= MAXC): every load of the group is issued
+// before any arithmetic, so a thread keeps (M-1)*NV independent loads in
+// flight.  Reads go through L2 only (data written by other blocks).  A
+// column at or beyond `end` is skipped.  In place is allowed (d == delta).
+template <typename W, int NV, int MAXC>
+__device__ __forceinline__ void recover_columns_batched(
+    const W* delta, int64_t ldd, int M, int64_t n, int64_t cstride,
+    int64_t end, int l, int r, W* d, int64_t ldo) {
+  W cache[MAXC][NV];
+  bool live[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) live[i] = (n + i * cstride) < end;
+  int row = r + 1 == M ? 0 : r + 1;
+#pragma unroll
+  for (int q = 0; q < MAXC; ++q) {
+    if (q < M - 1) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        cache[q][i] = live[i] ? __ldcg(delta + (int64_t)row * ldd + n + i * cstride)
+                              : (W)0;
+      row = row + 1 == M ? 0 : row + 1;
+    }
+  }
+  W t[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) t[i] = cache[0][i];
+#pragma unroll
+  for (int q = 1; q < MAXC; ++q) {
+    if (q < M - 1) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        t[i] = (q & 1) ? wsub<W>(shl<W>(t[i], l), cache[q][i])
+                       : wadd<W>(shl<W>(t[i], l), cache[q][i]);
+    }
+  }
+  const int win = (M - 1) * l;
+  W dcur[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    dcur[i] = sext_low<W>((M & 1) ? wsub<W>((W)0, t[i]) : t[i], win);
+  int j = r == 0 ? M - 1 : r - 1;
+#pragma unroll
+  for (int q = MAXC - 1; q >= 0; --q) {
+    if (q <= M - 2) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const W nxt = wsub<W>(cache[q][i], dcur[i]) >> l;
+        if (live[i]) d[(int64_t)j * ldo + n + i * cstride] = dcur[i];
+        dcur[i] = nxt;
+      }
+      j = j == 0 ? M - 1 : j - 1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (live[i]) d[(int64_t)r * ldo + n + i * cstride] = dcur[i];
+}
+
 }  // namespace ne

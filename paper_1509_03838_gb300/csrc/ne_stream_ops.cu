@@ -320,10 +320,11 @@ extern "C" {
 
 int ne_entangle(const void* c, int64_t ldc, void* eps, int64_t lde, int M,
                 int64_t N, int w, int l, void* stream) {
-  if (!c || !eps || M < 3 || M > 32 || N < 0 || ldc < N || lde < N ||
+  if (M < 3 || M > 32 || N < 0 || ldc < N || lde < N ||
       (w != 32 && w != 64) || l <= 0 || l >= w)
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;
+  if (!c || !eps) return NE_ERR_INVALID_ARG;
   const int wb = w / 8;
   if (c != eps || ldc != lde) {
     if (overlaps(c, rows_bytes(M, ldc, N, wb), eps, rows_bytes(M, lde, N, wb)))
@@ -336,11 +337,12 @@ int ne_entangle(const void* c, int64_t ldc, void* eps, int64_t lde, int M,
 
 int ne_recover(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
                int l, int failed, void* d, int64_t ld_out, void* stream) {
-  if (!delta || !d || M < 3 || M > 32 || Nout < 0 || ldd < Nout ||
+  if (M < 3 || M > 32 || Nout < 0 || ldd < Nout ||
       ld_out < Nout || (w != 32 && w != 64) || l <= 0 ||
       (M - 1) * l > w || failed < 0 || failed >= M)
     return NE_ERR_INVALID_ARG;
   if (Nout == 0) return NE_OK;
+  if (!delta || !d) return NE_ERR_INVALID_ARG;
   const int wb = w / 8;
   if (delta != d || ldd != ld_out) {
     if (overlaps(delta, rows_bytes(M, ldd, Nout, wb), d,
@@ -360,9 +362,10 @@ int ne_extract(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
 
 int ne_checksum(const void* c, int64_t ldc, int M, int64_t N, int w, void* r,
                 void* stream) {
-  if (!c || !r || M < 1 || M > 64 || N < 0 || ldc < N || (w != 32 && w != 64))
+  if (M < 1 || M > 64 || N < 0 || ldc < N || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;
+  if (!c || !r) return NE_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int wb = w / 8;
   const bool vec = rows_aligned16(c, ldc, wb) && aligned16(r);
@@ -380,10 +383,11 @@ int ne_checksum(const void* c, int64_t ldc, int M, int64_t N, int w, void* r,
 
 int ne_checksum_recover(const void* d, int64_t ldd, const void* e, int M,
                         int64_t Nout, int w, int f, void* out, void* stream) {
-  if (!d || !e || !out || M < 1 || M > 64 || Nout < 0 || ldd < Nout ||
+  if (M < 1 || M > 64 || Nout < 0 || ldd < Nout ||
       (w != 32 && w != 64) || f < 0 || f >= M)
     return NE_ERR_INVALID_ARG;
   if (Nout == 0) return NE_OK;
+  if (!d || !e || !out) return NE_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int grid = grid_for(Nout);
   if (w == 32)
@@ -397,9 +401,10 @@ int ne_checksum_recover(const void* d, int64_t ldd, const void* e, int M,
 
 int ne_scale(const void* x, int64_t ldx, int M, int64_t N, int64_t sc, int w,
              void* y, int64_t ldy, void* stream) {
-  if (!x || !y || M < 1 || N < 0 || ldx < N || ldy < N || (w != 32 && w != 64))
+  if (M < 1 || N < 0 || ldx < N || ldy < N || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;
+  if (!x || !y) return NE_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int wb = w / 8;
   const bool vec = rows_aligned16(x, ldx, wb) && rows_aligned16(y, ldy, wb);
@@ -417,10 +422,11 @@ int ne_scale(const void* x, int64_t ldx, int M, int64_t N, int64_t sc, int w,
 
 int ne_add(const void* x, int64_t ldx, const void* z, int64_t ldz, int M,
            int64_t N, int w, void* y, int64_t ldy, void* stream) {
-  if (!x || !z || !y || M < 1 || N < 0 || ldx < N || ldz < N || ldy < N ||
+  if (M < 1 || N < 0 || ldx < N || ldz < N || ldy < N ||
       (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;
+  if (!x || !z || !y) return NE_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int wb = w / 8;
   const bool vec = rows_aligned16(x, ldx, wb) && rows_aligned16(z, ldz, wb) &&
@@ -438,9 +444,10 @@ int ne_add(const void* x, int64_t ldx, const void* z, int64_t ldz, int M,
 
 int ne_self_entangle(const void* g, int64_t N, int w, int l, void* out,
                      void* stream) {
-  if (!g || !out || N < 0 || (w != 32 && w != 64) || l <= 0 || l >= w)
+  if (N < 0 || (w != 32 && w != 64) || l <= 0 || l >= w)
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;
+  if (!g || !out) return NE_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int grid = grid_for(N);
   if (w == 32)
@@ -453,10 +460,10 @@ int ne_self_entangle(const void* g, int64_t N, int w, int l, void* out,
 int ne_permute(const void* x, int64_t ldx, int M, int64_t N,
                const int64_t* perm, int w, void* y, int64_t ldy,
                int32_t* bad_count, void* stream) {
-  if (!x || !y || !perm || M < 1 || N < 0 || ldx < N || ldy < N ||
-      (w != 32 && w != 64))
+  if (M < 1 || N < 0 || ldx < N || ldy < N || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;
+  if (!x || !y || !perm) return NE_ERR_INVALID_ARG;
   const int wb = w / 8;
   if (overlaps(x, rows_bytes(M, ldx, N, wb), y, rows_bytes(M, ldy, N, wb)))
     return NE_ERR_INVALID_ARG;

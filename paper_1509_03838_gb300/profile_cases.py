@@ -1,0 +1,62 @@
+"""Run one kernel of the hot path a few times on seeded data, for profilers.
+
+    python -m paper_1509_03838_gb300.profile_cases CASE [--reps R] [--N N]
+
+Cases (default data: M = 4 streams, N = 2^22 samples, K = 64 taps, 16-bit
+data and taps, 64-bit words, the benchmark's workload):
+  protected      fused entangle-on-load + conv + extraction (stream 1 dropped)
+  conv_split     plain conv, 64-bit split-operand arithmetic
+  conv_wide      plain conv, one 32x32->64 multiply-add per tap
+  entangle       out-of-place entanglement
+  recover        recovery of all streams with stream 1 missing
+  checksum       checksum stream of the ABFT baseline
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+import torch
+
+from . import build, ne, synth
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--N", type=int, default=1 << 22)
+    a = ap.parse_args()
+    build.build()
+    dev = torch.device("cuda", 0)
+    j = synth.large_job(seed=2, N=a.N)
+    M, N, K = j.M, j.N, j.K
+    p = ne.ne_params(M, 64)
+    c = torch.from_numpy(j.c).to(dev)
+    g = torch.from_numpy(j.g.astype(np.int32)).to(dev)
+    d = torch.empty((M, N + K - 1), dtype=torch.int64, device=dev)
+    ws = torch.empty(ne.ne_protected_conv_ws_bytes(M, N, K), dtype=torch.uint8,
+                     device=dev)
+    eps = torch.empty_like(c)
+    r = torch.empty(N, dtype=torch.int64, device=dev)
+    ops = {
+        "protected": lambda: ne.ne_protected_conv(
+            c, g, d, l=p.l, max_abs_c=j.bound_c, max_abs_g=j.bound_g,
+            failed=1, fail_mode=ne.NE_FAIL_DROP, ws=ws),
+        "conv_split": lambda: ne.ne_conv(c, g, d, max_abs_x=0),
+        "conv_wide": lambda: ne.ne_conv(c, g, d, max_abs_x=j.bound_c),
+        "entangle": lambda: ne.ne_entangle(c, eps, l=p.l),
+        "recover": lambda: ne.ne_recover(d, d, l=p.l, failed=1),
+        "checksum": lambda: ne.ne_checksum(c, r),
+    }
+    if a.case not in ops:
+        raise SystemExit(f"unknown case {a.case}; one of {sorted(ops)}")
+    for _ in range(a.reps):
+        ops[a.case]()
+    torch.cuda.synchronize()
+    print(f"{a.case}: {a.reps} launches ok")
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -145,12 +145,20 @@ def test_conv_live_mask_and_unaligned(ne, orc):
             assert np.all(got[m] == -7)  # a stream that was not run
 
 
-def test_conv_empty(ne):
+def test_empty_inputs_are_noops(ne):
+    """N = 0: every call returns OK without touching memory (empty tensors
+    have null data pointers)."""
     x = torch.zeros((3, 0), dtype=torch.int64, device="cuda")
-    y = torch.zeros((3, 15), dtype=torch.int64, device="cuda")
+    y = torch.full((3, 15), 4, dtype=torch.int64, device="cuda")
     g = taps(np.ones(16))
     ne.ne_conv(x, g, y)
+    p = ne.ne_params(3, 64)
+    ne.ne_protected_conv(x, g, y, l=p.l, max_abs_c=1, max_abs_g=1)
+    ne.ne_entangle(x, l=p.l)
+    ne.ne_recover(x, x, l=p.l, failed=0)
+    ne.ne_checksum(x, torch.zeros(0, dtype=torch.int64, device="cuda"))
     torch.cuda.synchronize()
+    assert torch.all(y == 4)
 
 
 # ---------------------------------------------------------------------------
