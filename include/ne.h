@@ -81,6 +81,15 @@ const char *ne_status_str(int status);
 int ne_version(void);
 
 /*
+ * ne_get_device_error -- synchronise the current device and report the
+ * library's device-side error word in *out: 0, or bit 0 set if a kernel's
+ * bounded wait for one of its own bulk copies expired (the kernel then
+ * stopped early and its outputs are incomplete).  clear != 0 resets it.
+ * Blocks the host.  Returns NE_OK, NE_ERR_INVALID_ARG or NE_ERR_CUDA.
+ */
+int ne_get_device_error(uint32_t *out, int clear);
+
+/*
  * ne_params -- entanglement parameters for M streams in w-bit words
  * (Sec. III-A after Eq. 8; Eq. 12, Eq. 13; Table I).  l and k maximise the
  * supported output bitwidth (M-2)l + k subject to (M-1)l + k <= w and

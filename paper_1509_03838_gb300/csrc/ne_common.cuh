@@ -55,6 +55,13 @@ __host__ __device__ __forceinline__ W sext_low(W x, int bits) {
   return (W)((U)x << s) >> s;
 }
 
+__host__ __device__ __forceinline__ int64_t lmax(int64_t a, int64_t b) {
+  return a > b ? a : b;
+}
+__host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) {
+  return a < b ? a : b;
+}
+
 // 16-byte vector of words.
 template <typename W> struct Vec;
 template <> struct Vec<int32_t> {
@@ -80,5 +87,10 @@ inline int status_from_cuda(cudaError_t e) {
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+
+// Host readers of the per-translation-unit device error words (bit 0: a
+// bounded wait on a bulk copy expired); `clear` resets them.
+unsigned conv_tu_device_error(bool clear);
+unsigned batch_tu_device_error(bool clear);
 
 }  // namespace ne

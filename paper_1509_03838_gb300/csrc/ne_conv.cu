@@ -1,49 +1,30 @@
 // The LSB operation of the hot path: exact 1-D full linear convolution of
-// integer streams (Eq. 9 with op = convolution), and the fused protected
-// convolution (entangle-on-load -> convolution -> extraction by the
-// (M-1)-th stream to deliver each output tile).
+// integer streams (Eq. 9 with op = convolution), plain (ne_conv) and fused
+// with the protection (ne_protected_conv: entangle-on-load -> convolution
+// -> extraction by the (M-1)-th stream to deliver each output tile).
 //
-// Design (integer stencil work on the integer multiply-add pipe; no tensor
-// cores):
-//   * One thread block = one output tile of CONV_TILE = 256 x 12 samples of
-//     one stream.  The input tile plus a K-1 halo and the taps are staged in
-//     shared memory once (128-bit coalesced loads), already split into the
-//     32-bit operands the multiply-adds consume.
-//   * Each thread owns 12 consecutive outputs and slides a register window
-//     of 12+16 samples over the taps, 16 taps per chunk: 192 multiply-adds
-//     per 7 (or 14) 128-bit shared loads of samples and 4 broadcast loads of
-//     taps.  A 48-byte stride between threads keeps the 128-bit shared loads
-//     free of bank conflicts.
-//   * Three exact arithmetic modes, chosen on the host from the word width
-//     and the declared input bound (the dynamic-range bound decides the
-//     accumulator width):
-//       MODE_I32   w = 32: one 32-bit multiply-add per tap, modulo 2^32.
-//       MODE_WIDE  w = 64 and |x| < 2^31: one 32x32->64 multiply-add per tap
-//                  into a 64-bit accumulator, modulo 2^64.
-//       MODE_SPLIT w = 64, any x: x = hi*2^32 + lo with lo the sign-extended
-//                  low word; sum x*g = sum lo*g + 2^32 sum hi*g (mod 2^64),
-//                  i.e. one 32x32->64 multiply-add plus one 32-bit
-//                  multiply-add per tap.
-//     All three are exact modulo 2^w, which is all the method needs (the
-//     entangled words are elements of Z/2^w and the recovery identities hold
-//     there).
+// Two kernels share the device core of ne_conv_core.cuh:
+//   * conv_persistent_kernel (main path, 16-byte aligned rows): one
+//     persistent block per resident slot walks the (tile, stream) work units
+//     in order.  While the block computes unit i from shared memory, one
+//     thread has already issued the 1-D bulk copies (TMA, completion on an
+//     mbarrier) of unit i+1's raw input rows, so global-memory latency hides
+//     behind the multiply-adds.  After the copy lands the block converts the
+//     raw words (entangling them on the fly for the protected kernel) into
+//     the 32-bit operand arrays.
+//   * conv_simple_kernel (fallback: unaligned rows, or kernels too long for
+//     the persistent kernel's shared-memory budget): one block per unit,
+//     staged through registers.
+// The integer multiply-add pipe bounds both; tensor cores are not used
+// (integer stencil work, not a dense contraction).
 #include <algorithm>
+#include <mutex>
 
-#include "ne_common.cuh"
-#include "ne_recover.cuh"
+#include "ne_conv_core.cuh"
 
 namespace ne {
 
 namespace {
-
-enum { MODE_I32 = 0, MODE_WIDE = 1, MODE_SPLIT = 2 };
-
-constexpr int CONV_THREADS = 256;
-constexpr int CONV_R = 12;   // outputs per thread
-constexpr int CONV_KC = 16;  // taps per register chunk
-constexpr int CONV_TILE = CONV_THREADS * CONV_R;
-constexpr int CONV_WIN = CONV_R + CONV_KC;
-constexpr int CONV_MAX_K = 8192;
 
 struct ConvArgs {
   const void* x;   // input rows (raw, entangled, or raw to entangle on load)
@@ -51,42 +32,27 @@ struct ConvArgs {
   int M;
   int64_t N;
   int64_t Nout;
+  int64_t ntiles;
   const int32_t* g;
   int K;
   int Kp;          // K rounded up to CONV_KC
   void* y;         // output rows
   int64_t ldy;
-  uint32_t live_mask;
-  int l;           // entanglement shift (protected kernel)
+  uint32_t live_mask;  // plain conv: streams to compute
+  int l;               // entanglement shift (protected kernel)
   int failed;
   int fail_mode;
-  uint32_t* ws;    // protected kernel: per-tile {claim, ready} words
+  uint32_t* ws;        // protected kernel: per-tile {claim, ready} words
 };
 
-__device__ __forceinline__ int comp(const int4& v, int c) {
-  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
-}
-
-// Split one input word into the 32-bit operands of the chosen mode.
-template <typename W, int MODE>
-__device__ __forceinline__ void split_word(W v, int& lo, int& hi) {
-  if constexpr (MODE == MODE_SPLIT) {
-    const int64_t x = (int64_t)v;
-    lo = (int)(uint32_t)(uint64_t)x;
-    hi = (int)((x - (int64_t)lo) >> 32);
-  } else {
-    lo = (int)(uint32_t)(uint64_t)(int64_t)v;
-    hi = 0;
-  }
-}
-
-// Stage s[j] = x[n0 - Kp + j] (zero outside [0, N)) for j in [0, TILE+Kp),
-// optionally entangling on load: x = row + (prev_row << l).
+// Stage s[j] = x[n0 - Kp + j] (zero outside [0, N)) for j in [0, TILE+Kp)
+// through registers, optionally entangling on load: x = row + (prev << l).
 template <typename W, int MODE, bool VEC, bool ENT>
-__device__ __forceinline__ void stage_inputs(const W* __restrict__ row,
-                                             const W* __restrict__ prow,
-                                             int64_t N, int64_t n0, int Kp,
-                                             int l, int* s_lo, int* s_hi) {
+__device__ __forceinline__ void stage_from_global(const W* __restrict__ row,
+                                                  const W* __restrict__ prow,
+                                                  int64_t N, int64_t n0,
+                                                  int Kp, int l, int* s_lo,
+                                                  int* s_hi) {
   constexpr int V = VEC ? Vec<W>::n : 1;
   const int total = CONV_TILE + Kp;
   for (int j0 = threadIdx.x * V; j0 < total; j0 += CONV_THREADS * V) {
@@ -127,98 +93,13 @@ __device__ __forceinline__ void stage_inputs(const W* __restrict__ row,
   }
 }
 
-// Register-blocked sliding-window convolution of the staged tile.
-// Output a of this thread (global n = n0 + tid*R + a) accumulates
-//   sum_t s[tid*R + a - t + Kp] * g[t].
-template <int MODE>
-__device__ __forceinline__ void conv_compute(const int* __restrict__ s_lo,
-                                             const int* __restrict__ s_hi,
-                                             const int* __restrict__ s_taps,
-                                             int Kp,
-                                             unsigned long long (&a64)[CONV_R],
-                                             unsigned (&a32)[CONV_R]) {
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int a = 0; a < CONV_R; ++a) {
-    a64[a] = 0ull;
-    a32[a] = 0u;
-  }
-  for (int t0 = 0; t0 < Kp; t0 += CONV_KC) {
-    const int base = tid * CONV_R + Kp - t0 - CONV_KC;
-    int4 wl[CONV_WIN / 4];
-    int4 wh[CONV_WIN / 4];
-    int4 tp[CONV_KC / 4];
-#pragma unroll
-    for (int q = 0; q < CONV_WIN / 4; ++q)
-      wl[q] = reinterpret_cast<const int4*>(s_lo + base)[q];
-    if constexpr (MODE == MODE_SPLIT) {
-#pragma unroll
-      for (int q = 0; q < CONV_WIN / 4; ++q)
-        wh[q] = reinterpret_cast<const int4*>(s_hi + base)[q];
-    }
-#pragma unroll
-    for (int q = 0; q < CONV_KC / 4; ++q)
-      tp[q] = reinterpret_cast<const int4*>(s_taps + t0)[q];
-#pragma unroll
-    for (int u = 0; u < CONV_KC; ++u) {
-      const int gv = comp(tp[u >> 2], u & 3);
-#pragma unroll
-      for (int a = 0; a < CONV_R; ++a) {
-        const int e = a - u + CONV_KC;
-        const int xl = comp(wl[e >> 2], e & 3);
-        if constexpr (MODE == MODE_I32) {
-          a32[a] += (unsigned)xl * (unsigned)gv;
-        } else {
-          a64[a] += (unsigned long long)((long long)xl * (long long)gv);
-          if constexpr (MODE == MODE_SPLIT)
-            a32[a] += (unsigned)comp(wh[e >> 2], e & 3) * (unsigned)gv;
-        }
-      }
-    }
-  }
-}
-
-template <typename W, int MODE>
-__device__ __forceinline__ W combine(unsigned long long a64, unsigned a32) {
-  if constexpr (MODE == MODE_I32) {
-    return (W)(int32_t)a32;
-  } else if constexpr (MODE == MODE_WIDE) {
-    return (W)(int64_t)a64;
-  } else {
-    return (W)(int64_t)(a64 + ((unsigned long long)a32 << 32));
-  }
-}
-
-// Store this thread's outputs [n, n + R) of one row (clipped to Nout).
-template <typename W, bool VEC>
-__device__ __forceinline__ void store_outputs(W* __restrict__ yrow, int64_t n,
-                                              int64_t Nout,
-                                              const W (&out)[CONV_R]) {
-  if (VEC && n + CONV_R <= Nout) {
-    constexpr int V = Vec<W>::n;
-    using VT = typename Vec<W>::T;
-#pragma unroll
-    for (int q = 0; q < CONV_R / V; ++q) {
-      VT v;
-      W* pv = reinterpret_cast<W*>(&v);
-#pragma unroll
-      for (int i = 0; i < V; ++i) pv[i] = out[q * V + i];
-      reinterpret_cast<VT*>(yrow + n)[q] = v;
-    }
-  } else {
-#pragma unroll
-    for (int a = 0; a < CONV_R; ++a)
-      if (n + a < Nout) yrow[n + a] = out[a];
-  }
-}
-
-__host__ __device__ constexpr size_t conv_smem_bytes(int Kp, int mode) {
+__host__ __device__ constexpr size_t simple_smem_bytes(int Kp, int mode) {
   return ((size_t)(CONV_TILE + Kp) * (mode == MODE_SPLIT ? 2 : 1) + Kp) * 4;
 }
 
 template <typename W, int MODE, bool VEC, bool PROT>
-__global__ void __launch_bounds__(CONV_THREADS, 2)
-conv_kernel(const ConvArgs p) {
+__global__ void __launch_bounds__(CONV_THREADS, CONV_MIN_BLOCKS)
+conv_simple_kernel(const ConvArgs p) {
   extern __shared__ int4 smem4[];
   __shared__ int s_flag;
   const int Kp = p.Kp;
@@ -237,10 +118,10 @@ conv_kernel(const ConvArgs p) {
   const W* row = reinterpret_cast<const W*>(p.x) + (int64_t)m * p.ldx;
   const W* prow = reinterpret_cast<const W*>(p.x) +
                   (int64_t)(m == 0 ? p.M - 1 : m - 1) * p.ldx;
-
   for (int j = threadIdx.x; j < Kp; j += CONV_THREADS)
     s_taps[j] = j < p.K ? __ldg(p.g + j) : 0;
-  stage_inputs<W, MODE, VEC, PROT>(row, prow, p.N, n0, Kp, p.l, s_lo, s_hi);
+  stage_from_global<W, MODE, VEC, PROT>(row, prow, p.N, n0, Kp, p.l, s_lo,
+                                        s_hi);
   __syncthreads();
 
   unsigned long long a64[CONV_R];
@@ -249,85 +130,227 @@ conv_kernel(const ConvArgs p) {
   W out[CONV_R];
 #pragma unroll
   for (int a = 0; a < CONV_R; ++a) out[a] = combine<W, MODE>(a64[a], a32[a]);
-
   W* ybase = reinterpret_cast<W*>(p.y);
-  const int64_t nt = n0 + (int64_t)threadIdx.x * CONV_R;
   if constexpr (!PROT) {
-    store_outputs<W, VEC>(ybase + (int64_t)m * p.ldy, nt, p.Nout, out);
+    store_outputs<W, VEC>(ybase + (int64_t)m * p.ldy,
+                          n0 + (int64_t)threadIdx.x * CONV_R, p.Nout, out);
   } else {
-    // ---- fail-stop: a stream whose result is lost never delivers -------
-    if (p.fail_mode == NE_FAIL_DROP && m == p.failed) return;
-    uint32_t* claim = p.ws + 2 * tile;
-    uint32_t* ready = claim + 1;
-    // Claim a delivery slot: only the first M-1 streams of a tile deliver;
-    // a later one is redundant (its output is already recoverable).
-    if (threadIdx.x == 0) s_flag = (int)atomicAdd(claim, 1u);
-    __syncthreads();
-    if (s_flag >= p.M - 1) return;
-    store_outputs<W, VEC>(ybase + (int64_t)m * p.ldy, nt, p.Nout, out);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const uint32_t mask = atomicOr(ready, 1u << m) | (1u << m);
-      s_flag = (__popc(mask) == p.M - 1) ? (int)mask : -1;
-    }
-    __syncthreads();
-    const int mask = s_flag;
-    if (mask == -1) return;
-    __threadfence();
-    // ---- this block delivered (M-1)-th: extract the whole tile ----------
-    const uint32_t full = p.M >= 32 ? 0xffffffffu : ((1u << p.M) - 1u);
-    const int r = __ffs((int)(~(uint32_t)mask & full)) - 1;
-    const int64_t end = min(n0 + (int64_t)CONV_TILE, p.Nout);
-    if (p.M <= 9) {
-      // thread t owns columns n0 + t + 256 i: every warp access is one
-      // contiguous 256-byte (int64) or 128-byte (int32) segment
-      constexpr int NV = 4;
-#pragma unroll 1
-      for (int64_t n = n0 + threadIdx.x; n < end;
-           n += (int64_t)CONV_THREADS * NV)
-        recover_columns_batched<W, NV, 8>(ybase, p.ldy, p.M, n, CONV_THREADS,
-                                          end, p.l, r, ybase, p.ldy);
-    } else {
-      for (int64_t n = n0 + threadIdx.x; n < end; n += CONV_THREADS)
-        recover_columns<W, 0, 1, true>(ybase, p.ldy, p.M, n, p.l, r, ybase,
-                                       p.ldy);
-    }
+    if (p.fail_mode == NE_FAIL_DROP && m == p.failed) return;  // result lost
+    protected_epilogue<W, VEC>(ybase, p.ldy, p.M, m, tile, n0, p.Nout, p.l,
+                               p.ws, out, &s_flag);
   }
 }
 
-template <typename W, int MODE, bool VEC, bool PROT>
-int launch_conv_v(const ConvArgs& a, int64_t ntiles, cudaStream_t s) {
-  const size_t smem = conv_smem_bytes(a.Kp, MODE);
-  static bool attr_set = false;  // per instantiation; idempotent
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(
-        conv_kernel<W, MODE, VEC, PROT>,
-        cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)conv_smem_bytes(CONV_MAX_K, MODE_SPLIT));
-    if (e != cudaSuccess) return NE_ERR_CUDA;
-    attr_set = true;
+// ---------------------------------------------------------------------------
+// persistent, bulk-copy-fed kernel
+// ---------------------------------------------------------------------------
+template <typename W>
+__host__ __device__ constexpr size_t persistent_smem_bytes(int Kp, int mode,
+                                                           bool prot) {
+  return (size_t)(CONV_TILE + Kp) * sizeof(W) * (prot ? 2 : 1) +
+         simple_smem_bytes(Kp, mode);
+}
+
+// Is a unit of stream m computed at all?  (plain conv: live streams;
+// protected: every stream except one that fail-stopped before starting)
+template <bool PROT>
+__device__ __forceinline__ bool unit_runs(const ConvArgs& p, int m) {
+  if constexpr (PROT)
+    return !(p.fail_mode == NE_FAIL_SKIP && m == p.failed);
+  else
+    return (p.live_mask >> m) & 1u;
+}
+
+template <bool PROT>
+__device__ __forceinline__ int64_t next_unit(const ConvArgs& p, int64_t u,
+                                             int64_t U) {
+  for (; u < U; u += gridDim.x)
+    if (unit_runs<PROT>(p, (int)(u % p.M))) return u;
+  return U;
+}
+
+// Issue the bulk copies of unit u's raw input window (one thread).  The
+// window x[n0-Kp, n0+TILE) is clipped to [0, N); the copied part is the
+// largest multiple of 16 bytes, the rest (at most 3 words) is read directly
+// during the conversion.  Completion arrives on `bar`.
+template <typename W, bool PROT>
+__device__ __forceinline__ void issue_unit_copy(const ConvArgs& p, int64_t u,
+                                                W* raw0, W* raw1,
+                                                uint64_t* bar) {
+  const int64_t tile = u / p.M;
+  const int m = (int)(u - tile * p.M);
+  const int64_t n0 = tile * CONV_TILE;
+  const int64_t lo = lmax(0, n0 - p.Kp);
+  const int64_t hi = lmin(p.N, n0 + CONV_TILE);
+  constexpr int per16 = 16 / (int)sizeof(W);
+  const int64_t cnt = ((hi - lo) / per16) * per16;
+  const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(W));
+  const int64_t off = lo - (n0 - p.Kp);
+  const W* xb = reinterpret_cast<const W*>(p.x);
+  if (bytes == 0) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+    return;
   }
-  const int64_t blocks = ntiles * a.M;
+  mbar_arrive_expect_tx(bar, bytes * (PROT ? 2u : 1u));
+  bulk_copy_g2s(raw0 + off, xb + (int64_t)m * p.ldx + lo, bytes, bar);
+  if constexpr (PROT) {
+    const int mp = m == 0 ? p.M - 1 : m - 1;
+    bulk_copy_g2s(raw1 + off, xb + (int64_t)mp * p.ldx + lo, bytes, bar);
+  }
+}
+
+template <typename W, int MODE, bool PROT>
+__global__ void __launch_bounds__(CONV_THREADS, CONV_MIN_BLOCKS)
+conv_persistent_kernel(const ConvArgs p) {
+  extern __shared__ int4 smem4[];
+  __shared__ uint64_t bar;
+  __shared__ int s_flag;
+  const int Kp = p.Kp;
+  const int span = CONV_TILE + Kp;
+  W* raw0 = reinterpret_cast<W*>(smem4);
+  W* raw1 = raw0 + span;  // only with PROT
+  int* s_lo = reinterpret_cast<int*>(raw0 + (size_t)span * (PROT ? 2 : 1));
+  int* s_hi = s_lo + span;
+  int* s_taps = s_lo + (size_t)span * (MODE == MODE_SPLIT ? 2 : 1);
+  const int64_t U = p.ntiles * p.M;
+  const W* xb = reinterpret_cast<const W*>(p.x);
+  W* ybase = reinterpret_cast<W*>(p.y);
+
+  for (int j = threadIdx.x; j < Kp; j += CONV_THREADS)
+    s_taps[j] = j < p.K ? __ldg(p.g + j) : 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  int64_t u = next_unit<PROT>(p, blockIdx.x, U);
+  if (threadIdx.x == 0 && u < U) issue_unit_copy<W, PROT>(p, u, raw0, raw1, &bar);
+  uint32_t parity = 0;
+  while (u < U) {
+    const int64_t nxt = next_unit<PROT>(p, u + gridDim.x, U);
+    const int64_t tile = u / p.M;
+    const int m = (int)(u - tile * p.M);
+    const int64_t n0 = tile * CONV_TILE;
+    if (!mbar_wait_bounded(&bar, parity)) return;
+    parity ^= 1u;
+    // ---- convert the landed raw window into 32-bit operands -----------
+    {
+      const int64_t lo = lmax(0, n0 - Kp);
+      const int64_t hi = lmin(p.N, n0 + CONV_TILE);
+      constexpr int per16 = 16 / (int)sizeof(W);
+      const int64_t bulk_end = lo + ((hi - lo) / per16) * per16;
+      const W* row = xb + (int64_t)m * p.ldx;
+      const W* prow = xb + (int64_t)(m == 0 ? p.M - 1 : m - 1) * p.ldx;
+      for (int j = threadIdx.x; j < span; j += CONV_THREADS) {
+        const int64_t gi = n0 - Kp + j;
+        W v = 0;
+        if (gi >= lo && gi < bulk_end) {
+          v = raw0[j];
+          if constexpr (PROT) v = wadd<W>(v, shl<W>(raw1[j], p.l));
+        } else if (gi >= bulk_end && gi < hi) {
+          v = __ldg(row + gi);
+          if constexpr (PROT) v = wadd<W>(v, shl<W>(__ldg(prow + gi), p.l));
+        }
+        int a, b;
+        split_word<W, MODE>(v, a, b);
+        s_lo[j] = a;
+        if constexpr (MODE == MODE_SPLIT) s_hi[j] = b;
+      }
+    }
+    __syncthreads();
+    // ---- prefetch the next unit while this one computes ---------------
+    if (threadIdx.x == 0 && nxt < U) {
+      fence_proxy_async_smem();
+      issue_unit_copy<W, PROT>(p, nxt, raw0, raw1, &bar);
+    }
+    unsigned long long a64[CONV_R];
+    unsigned a32[CONV_R];
+    conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32);
+    W out[CONV_R];
+#pragma unroll
+    for (int a = 0; a < CONV_R; ++a) out[a] = combine<W, MODE>(a64[a], a32[a]);
+    if constexpr (!PROT) {
+      store_outputs<W, true>(ybase + (int64_t)m * p.ldy,
+                             n0 + (int64_t)threadIdx.x * CONV_R, p.Nout, out);
+    } else {
+      if (!(p.fail_mode == NE_FAIL_DROP && m == p.failed))
+        protected_epilogue<W, true>(ybase, p.ldy, p.M, m, tile, n0, p.Nout,
+                                    p.l, p.ws, out, &s_flag);
+    }
+    __syncthreads();
+    u = nxt;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+constexpr size_t kSmemBudget = 200 * 1024;  // per block, of 227 KB
+
+template <typename K>
+int set_max_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes) == cudaSuccess
+             ? NE_OK
+             : NE_ERR_CUDA;
+}
+
+template <typename W, int MODE, bool VEC, bool PROT>
+int launch_simple(const ConvArgs& a, cudaStream_t s) {
+  const size_t smem = simple_smem_bytes(a.Kp, MODE);
+  static std::once_flag once;
+  static int attr = NE_OK;
+  std::call_once(once, [] {
+    attr = set_max_smem(conv_simple_kernel<W, MODE, VEC, PROT>,
+                        simple_smem_bytes(CONV_MAX_K, MODE_SPLIT));
+  });
+  if (attr != NE_OK) return attr;
+  const int64_t blocks = a.ntiles * a.M;
   if (blocks > 0x7fffffffLL) return NE_ERR_UNSUPPORTED;
-  conv_kernel<W, MODE, VEC, PROT><<<(unsigned)blocks, CONV_THREADS, smem, s>>>(a);
+  conv_simple_kernel<W, MODE, VEC, PROT>
+      <<<(unsigned)blocks, CONV_THREADS, smem, s>>>(a);
   return status_from_cuda(cudaGetLastError());
 }
 
 template <typename W, int MODE, bool PROT>
-int launch_conv(const ConvArgs& a, int64_t ntiles, bool vec, cudaStream_t s) {
-  return vec ? launch_conv_v<W, MODE, true, PROT>(a, ntiles, s)
-             : launch_conv_v<W, MODE, false, PROT>(a, ntiles, s);
+int launch_persistent(const ConvArgs& a, cudaStream_t s) {
+  const size_t smem = persistent_smem_bytes<W>(a.Kp, MODE, PROT);
+  static std::once_flag once;
+  static int attr = NE_OK;
+  std::call_once(once, [] {
+    attr = set_max_smem(conv_persistent_kernel<W, MODE, PROT>, kSmemBudget);
+  });
+  if (attr != NE_OK) return attr;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, conv_persistent_kernel<W, MODE, PROT>, CONV_THREADS, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t U = a.ntiles * a.M;
+  const int64_t grid = std::min<int64_t>(U, (int64_t)sm_count() * per_sm);
+  conv_persistent_kernel<W, MODE, PROT>
+      <<<(unsigned)grid, CONV_THREADS, smem, s>>>(a);
+  return status_from_cuda(cudaGetLastError());
+}
+
+template <typename W, int MODE, bool PROT>
+int launch_conv(const ConvArgs& a, bool vec, cudaStream_t s) {
+  if (vec && persistent_smem_bytes<W>(a.Kp, MODE, PROT) <= kSmemBudget)
+    return launch_persistent<W, MODE, PROT>(a, s);
+  return vec ? launch_simple<W, MODE, true, PROT>(a, s)
+             : launch_simple<W, MODE, false, PROT>(a, s);
 }
 
 template <bool PROT>
 int dispatch_conv(const ConvArgs& a, int w, int mode, bool vec,
                   cudaStream_t s) {
-  const int64_t ntiles = (a.Nout + CONV_TILE - 1) / CONV_TILE;
-  if (w == 32) return launch_conv<int32_t, MODE_I32, PROT>(a, ntiles, vec, s);
-  if (mode == MODE_WIDE)
-    return launch_conv<int64_t, MODE_WIDE, PROT>(a, ntiles, vec, s);
-  return launch_conv<int64_t, MODE_SPLIT, PROT>(a, ntiles, vec, s);
+  if (w == 32) return launch_conv<int32_t, MODE_I32, PROT>(a, vec, s);
+  if (mode == MODE_WIDE) return launch_conv<int64_t, MODE_WIDE, PROT>(a, vec, s);
+  return launch_conv<int64_t, MODE_SPLIT, PROT>(a, vec, s);
 }
 
 inline bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
@@ -353,6 +376,18 @@ inline unsigned __int128 exact_limit(int M, int w, int l) {
 
 }  // namespace
 
+// Host reader of this translation unit's device error word.
+unsigned conv_tu_device_error(bool clear) {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_ne_device_error, sizeof(v)) != cudaSuccess)
+    return 0x80000000u;
+  if (clear && v) {
+    const unsigned z = 0;
+    cudaMemcpyToSymbol(g_ne_device_error, &z, sizeof(z));
+  }
+  return v;
+}
+
 }  // namespace ne
 
 using namespace ne;
@@ -377,6 +412,7 @@ int ne_conv(const void* x, int64_t ldx, int M, int64_t N, const int32_t* g,
   a.M = M;
   a.N = N;
   a.Nout = Nout;
+  a.ntiles = (Nout + CONV_TILE - 1) / CONV_TILE;
   a.g = g;
   a.K = K;
   a.Kp = (K + CONV_KC - 1) / CONV_KC * CONV_KC;
@@ -432,6 +468,7 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   a.M = M;
   a.N = N;
   a.Nout = Nout;
+  a.ntiles = (Nout + CONV_TILE - 1) / CONV_TILE;
   a.g = g;
   a.K = K;
   a.Kp = (K + CONV_KC - 1) / CONV_KC * CONV_KC;

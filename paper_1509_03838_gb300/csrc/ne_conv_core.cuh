@@ -1,0 +1,262 @@
+// Device building blocks of the exact integer convolution (Eq. 9 with op =
+// full linear convolution) shared by the single-job kernels (ne_conv.cu)
+// and the persistent batch kernel (ne_batch.cu).
+//
+// Tile geometry: one output tile = CONV_TILE = CONV_THREADS x CONV_R outputs
+// of one stream.  Its input window is x[n0 - Kp, n0 + CONV_TILE) (Kp = K
+// rounded up to CONV_KC, zero outside [0, N)), held in shared memory as the
+// 32-bit operands the multiply-adds consume.
+//
+// Exact arithmetic modes (chosen on the host from the word width and the
+// declared input bound -- the dynamic-range bound decides the accumulator):
+//   MODE_I32   w = 32: one 32-bit multiply-add per tap, modulo 2^32.
+//   MODE_WIDE  w = 64, |x| < 2^31: one 32x32->64 multiply-add per tap.
+//   MODE_SPLIT w = 64, any x: x = hi*2^32 + lo (lo the sign-extended low
+//              word), sum x*g = sum lo*g + 2^32 sum hi*g (mod 2^64).
+// All are exact modulo 2^w, the ring the method works in.
+#pragma once
+
+#include "ne_common.cuh"
+#include "ne_recover.cuh"
+
+namespace ne {
+
+enum { MODE_I32 = 0, MODE_WIDE = 1, MODE_SPLIT = 2 };
+
+#ifndef NE_CONV_THREADS
+#define NE_CONV_THREADS 256
+#endif
+constexpr int CONV_THREADS = NE_CONV_THREADS;
+constexpr int CONV_MIN_BLOCKS = 512 / CONV_THREADS;  // 512 threads per SM
+constexpr int CONV_R = 12;   // outputs per thread (48-byte stride: no bank
+                             // conflicts for 128-bit shared loads)
+constexpr int CONV_KC = 16;  // taps per register chunk
+constexpr int CONV_TILE = CONV_THREADS * CONV_R;
+constexpr int CONV_WIN = CONV_R + CONV_KC;
+constexpr int CONV_MAX_K = 8192;
+
+// Device-side error word of the including translation unit (bit 0: a
+// bounded wait on a bulk copy expired).  Each translation unit has its own
+// copy (no relocatable device code) and exposes it through a host reader.
+static __device__ unsigned int g_ne_device_error = 0;
+
+__device__ __forceinline__ int comp4(const int4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+// Split one word into the 32-bit operands of the chosen mode.
+template <typename W, int MODE>
+__device__ __forceinline__ void split_word(W v, int& lo, int& hi) {
+  if constexpr (MODE == MODE_SPLIT) {
+    const int64_t x = (int64_t)v;
+    lo = (int)(uint32_t)(uint64_t)x;
+    hi = (int)((x - (int64_t)lo) >> 32);
+  } else {
+    lo = (int)(uint32_t)(uint64_t)(int64_t)v;
+    hi = 0;
+  }
+}
+
+// Register-blocked sliding-window convolution of a staged tile: output a of
+// this thread (n = n0 + tid*R + a) accumulates sum_t s[tid*R + a - t + Kp]
+// * g[t].  Each 16-tap chunk loads a 28-sample window (7 or 14 128-bit
+// shared loads) and 16 taps (4 broadcast loads) for 192 multiply-adds.
+template <int MODE>
+__device__ __forceinline__ void conv_compute(const int* __restrict__ s_lo,
+                                             const int* __restrict__ s_hi,
+                                             const int* __restrict__ s_taps,
+                                             int Kp,
+                                             unsigned long long (&a64)[CONV_R],
+                                             unsigned (&a32)[CONV_R]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int a = 0; a < CONV_R; ++a) {
+    a64[a] = 0ull;
+    a32[a] = 0u;
+  }
+#pragma unroll 1
+  for (int t0 = 0; t0 < Kp; t0 += CONV_KC) {
+    const int base = tid * CONV_R + Kp - t0 - CONV_KC;
+    int4 wl[CONV_WIN / 4];
+    int4 wh[CONV_WIN / 4];
+    int4 tp[CONV_KC / 4];
+#pragma unroll
+    for (int q = 0; q < CONV_WIN / 4; ++q)
+      wl[q] = reinterpret_cast<const int4*>(s_lo + base)[q];
+    if constexpr (MODE == MODE_SPLIT) {
+#pragma unroll
+      for (int q = 0; q < CONV_WIN / 4; ++q)
+        wh[q] = reinterpret_cast<const int4*>(s_hi + base)[q];
+    }
+#pragma unroll
+    for (int q = 0; q < CONV_KC / 4; ++q)
+      tp[q] = reinterpret_cast<const int4*>(s_taps + t0)[q];
+#pragma unroll
+    for (int u = 0; u < CONV_KC; ++u) {
+      const int gv = comp4(tp[u >> 2], u & 3);
+#pragma unroll
+      for (int a = 0; a < CONV_R; ++a) {
+        const int e = a - u + CONV_KC;
+        const int xl = comp4(wl[e >> 2], e & 3);
+        if constexpr (MODE == MODE_I32) {
+          a32[a] += (unsigned)xl * (unsigned)gv;
+        } else {
+          a64[a] += (unsigned long long)((long long)xl * (long long)gv);
+          if constexpr (MODE == MODE_SPLIT)
+            a32[a] += (unsigned)comp4(wh[e >> 2], e & 3) * (unsigned)gv;
+        }
+      }
+    }
+  }
+}
+
+template <typename W, int MODE>
+__device__ __forceinline__ W combine(unsigned long long a64, unsigned a32) {
+  if constexpr (MODE == MODE_I32) {
+    return (W)(int32_t)a32;
+  } else if constexpr (MODE == MODE_WIDE) {
+    return (W)(int64_t)a64;
+  } else {
+    return (W)(int64_t)(a64 + ((unsigned long long)a32 << 32));
+  }
+}
+
+// Store this thread's outputs [n, n + R) of one row (clipped to Nout).
+template <typename W, bool VEC>
+__device__ __forceinline__ void store_outputs(W* __restrict__ yrow, int64_t n,
+                                              int64_t Nout,
+                                              const W (&out)[CONV_R]) {
+  if (VEC && n + CONV_R <= Nout) {
+    constexpr int V = Vec<W>::n;
+    using VT = typename Vec<W>::T;
+#pragma unroll
+    for (int q = 0; q < CONV_R / V; ++q) {
+      VT v;
+      W* pv = reinterpret_cast<W*>(&v);
+#pragma unroll
+      for (int i = 0; i < V; ++i) pv[i] = out[q * V + i];
+      reinterpret_cast<VT*>(yrow + n)[q] = v;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < CONV_R; ++a)
+      if (n + a < Nout) yrow[n + a] = out[a];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fail-stop protocol of the fused protected convolution, per output tile.
+// A stream that delivers first claims a slot; only the first M-1 claimants
+// publish their entangled tile into the output rows (a later one is
+// redundant: its output is already recoverable).  The publisher that
+// completes the set of M-1 extracts all M true outputs of the tile in
+// place (Eq. 16-19 via the w-bit chain).  No block ever waits for another.
+// ws: {claim, ready} per tile, zero at launch.  Must be called by every
+// thread of the block (it contains block barriers).
+// ---------------------------------------------------------------------------
+template <typename W, bool VEC>
+__device__ __forceinline__ void protected_epilogue(
+    W* __restrict__ ybase, int64_t ldy, int M, int m, int64_t tile, int64_t n0,
+    int64_t Nout, int l, uint32_t* ws, const W (&out)[CONV_R], int* s_flag) {
+  uint32_t* claim = ws + 2 * tile;
+  uint32_t* ready = claim + 1;
+  if (threadIdx.x == 0) *s_flag = (int)atomicAdd(claim, 1u);
+  __syncthreads();
+  const bool publish = *s_flag < M - 1;
+  __syncthreads();
+  if (!publish) return;
+  const int64_t nt = n0 + (int64_t)threadIdx.x * CONV_R;
+  store_outputs<W, VEC>(ybase + (int64_t)m * ldy, nt, Nout, out);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t mask = atomicOr(ready, 1u << m) | (1u << m);
+    *s_flag = (__popc(mask) == M - 1) ? (int)mask : -1;
+  }
+  __syncthreads();
+  const int mask = *s_flag;
+  __syncthreads();
+  if (mask == -1) return;
+  __threadfence();
+  const uint32_t full = M >= 32 ? 0xffffffffu : ((1u << M) - 1u);
+  const int r = __ffs((int)(~(uint32_t)mask & full)) - 1;
+  const int64_t end = min(n0 + (int64_t)CONV_TILE, Nout);
+  if (M <= 9) {
+    // thread t owns columns n0 + t + CONV_THREADS i: every warp access is one
+    // contiguous segment; all M-1 rows of NV columns are in flight at once
+    constexpr int NV = 2;
+#pragma unroll 1
+    for (int64_t n = n0 + threadIdx.x; n < end;
+         n += (int64_t)CONV_THREADS * NV)
+      recover_columns_batched<W, NV, 8>(ybase, ldy, M, n, CONV_THREADS, end,
+                                        l, r, ybase, ldy);
+  } else {
+    for (int64_t n = n0 + threadIdx.x; n < end; n += CONV_THREADS)
+      recover_columns<W, 0, 1, true>(ybase, ldy, M, n, l, r, ybase, ldy);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + 1-D bulk copy (TMA) helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar,
+                                                      uint32_t bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+          smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+}
+// dst, src 16-byte aligned; bytes a non-zero multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src,
+                                              uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for a bulk-copy phase: returns false (and flags the error)
+// if the phase has not completed after `limit` polls.  Every thread of the
+// block must call it; the verdict is made uniform across the block.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar,
+                                                  uint32_t parity) {
+  constexpr uint32_t limit = 1u << 24;
+  bool done = false;
+  for (uint32_t it = 0; it < limit; ++it) {
+    if (mbar_try_wait(bar, parity)) {
+      done = true;
+      break;
+    }
+  }
+  const bool all = __syncthreads_and(done ? 1 : 0) != 0;
+  if (!all && threadIdx.x == 0) atomicOr(&g_ne_device_error, 1u);
+  return all;
+}
+
+}  // namespace ne

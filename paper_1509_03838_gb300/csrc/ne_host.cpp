@@ -48,6 +48,16 @@ const char* ne_status_str(int status) {
 
 int ne_version(void) { return 100; }
 
+int ne_get_device_error(uint32_t* out, int clear) {
+  if (!out) return NE_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return NE_ERR_CUDA;
+  const unsigned v = ne::conv_tu_device_error(clear != 0) |
+                     ne::batch_tu_device_error(clear != 0);
+  if (v & 0x80000000u) return NE_ERR_CUDA;
+  *out = v;
+  return NE_OK;
+}
+
 // Parameter rule (Eq. 12 constraint, Table I objective).  For a fixed l the
 // best admissible k is min(l, w - (M-1)l), so the objective (M-2)l + k equals
 // (M-1)l while l <= w/M and w - l beyond: it peaks at l = floor(w/M) or

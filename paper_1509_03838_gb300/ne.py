@@ -70,6 +70,7 @@ class Params:
 _SIGS = {
     "ne_status_str": ([_i32], ctypes.c_char_p),
     "ne_version": ([], _i32),
+    "ne_get_device_error": ([ctypes.POINTER(_u32), _i32], _i32),
     "ne_params": ([_i32, _i32, ctypes.POINTER(_Params)], _i32),
     "ne_choose_width": ([_i32, _i32, _i64, _i64, ctypes.POINTER(_Params)], _i32),
     "ne_entangle": ([_vp, _i64, _vp, _i64, _i32, _i64, _i32, _i32, _vp], _i32),
@@ -169,6 +170,14 @@ def ne_choose_width(M: int, K: int, max_abs_c: int, max_abs_g: int) -> Params:
     _check(lib().ne_choose_width(M, K, max_abs_c, max_abs_g, ctypes.byref(p)),
            "ne_choose_width")
     return Params(p.M, p.w, p.l, p.k, p.d_max_paper, p.d_max_exact)
+
+
+def ne_get_device_error(clear: bool = True) -> int:
+    """Synchronise and read (and by default clear) the device error word."""
+    v = _u32()
+    _check(lib().ne_get_device_error(ctypes.byref(v), int(clear)),
+           "ne_get_device_error")
+    return int(v.value)
 
 
 def ne_protected_conv_ws_bytes(M: int, N: int, K: int) -> int:
