@@ -129,14 +129,18 @@ int ne_entangle(const void *c, int64_t ldc, void *eps, int64_t lde, int M,
  * for every stream m whose bit is set in live_mask (bit m = stream m; other
  * rows of y are not written: a fail-stopped stream).  x: M rows of N words
  * (ldx); y: M rows of N+K-1 words (ldy >= N+K-1); g: K int32 taps on the
- * device.  max_abs_x is the caller's bound on |x| (0 = unknown); for w = 64
- * a bound below 2^31 lets the kernel use a single 32x32->64 multiply-add per
- * tap instead of two.  The result is exact modulo 2^w either way.
+ * device.  [x_min, x_max] is the caller's declared range of the input
+ * words (x_min > x_max: unknown).  For w = 64 a range spanning at most 2^32
+ * values lets the kernel shift the inputs into 32 bits and use a single
+ * 32x32->64 multiply-add per tap (the shift is undone exactly by adding
+ * b * sum of the taps meeting the input); otherwise each tap takes two
+ * multiply-adds.  The result is exact modulo 2^w either way; values outside
+ * a declared range give wrong (but defined) outputs.
  * Requires 1 <= K <= 8192, 1 <= M <= 32.  Works on raw streams (the
  * unprotected baseline) and on entangled streams alike.
  */
 int ne_conv(const void *x, int64_t ldx, int M, int64_t N, const int32_t *g,
-            int K, void *y, int64_t ldy, int w, int64_t max_abs_x,
+            int K, void *y, int64_t ldy, int w, int64_t x_min, int64_t x_max,
             uint32_t live_mask, void *stream);
 
 /*
@@ -170,8 +174,13 @@ int ne_extract(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
  *   c: M raw input rows of N words (ldc); g: K int32 taps;
  *   d: M output rows (ldd >= N+K-1), receives the true outputs d_m = c_m * g.
  *      It also serves as the landing buffer of the entangled tiles.
- *   max_abs_c, max_abs_g: caller's bounds on |c| and |g|; the call returns
- *      NE_ERR_RANGE if K*max_abs_c*max_abs_g > d_max_exact for (M, w).
+ *   [c_min, c_max]: caller's declared range of the inputs (c_min <= c_max);
+ *   max_abs_g: bound on |g|.  With B = max(|c_min|, |c_max|) the call
+ *      returns NE_ERR_RANGE if K*B*max_abs_g exceeds the exact output range
+ *      for (M, w, l) or B(2^l + 1) does not fit w signed bits.  The range
+ *      also picks the arithmetic: entangled words lie in
+ *      [c_min(2^l+1), c_max(2^l+1)], and a span of at most 2^32 values
+ *      takes one 32x32->64 multiply-add per tap (see ne_conv).
  *   failed, fail_mode: failure injection (failed in [0, M) or -1 with
  *      NE_FAIL_NONE).
  *   ws: device workspace of ne_protected_conv_ws_bytes() bytes (per-tile
@@ -180,8 +189,8 @@ int ne_extract(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
  * (M-1)-th; a late M-th stream discards its result.
  */
 int ne_protected_conv(const void *c, int64_t ldc, int M, int64_t N,
-                      const int32_t *g, int K, int w, int l,
-                      int64_t max_abs_c, int64_t max_abs_g, int failed,
+                      const int32_t *g, int K, int w, int l, int64_t c_min,
+                      int64_t c_max, int64_t max_abs_g, int failed,
                       int fail_mode, void *d, int64_t ldd, void *ws,
                       size_t ws_bytes, void *stream);
 

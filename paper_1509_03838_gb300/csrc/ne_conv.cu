@@ -18,6 +18,8 @@
 // The integer multiply-add pipe bounds both; tensor cores are not used
 // (integer stencil work, not a dense contraction).
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "ne_conv_core.cuh"
@@ -43,6 +45,7 @@ struct ConvArgs {
   int failed;
   int fail_mode;
   uint32_t* ws;        // protected kernel: per-tile {claim, ready} words
+  long long bias;      // MODE_WIDE range shift b (x - b fits 32 bits)
 };
 
 // Stage s[j] = x[n0 - Kp + j] (zero outside [0, N)) for j in [0, TILE+Kp)
@@ -51,8 +54,8 @@ template <typename W, int MODE, bool VEC, bool ENT>
 __device__ __forceinline__ void stage_from_global(const W* __restrict__ row,
                                                   const W* __restrict__ prow,
                                                   int64_t N, int64_t n0,
-                                                  int Kp, int l, int* s_lo,
-                                                  int* s_hi) {
+                                                  int Kp, int l, W bias,
+                                                  int* s_lo, int* s_hi) {
   constexpr int V = VEC ? Vec<W>::n : 1;
   const int total = CONV_TILE + Kp;
   for (int j0 = threadIdx.x * V; j0 < total; j0 += CONV_THREADS * V) {
@@ -85,16 +88,32 @@ __device__ __forceinline__ void stage_from_global(const W* __restrict__ row,
     }
 #pragma unroll
     for (int q = 0; q < V; ++q) {
+      const int64_t gq = gi + q;
       int lo, hi;
-      split_word<W, MODE>(v[q], lo, hi);
+      // inputs outside [0, N) are zero and are not shifted
+      split_word<W, MODE>((gq >= 0 && gq < N) ? wsub<W>(v[q], bias) : (W)0,
+                          lo, hi);
       s_lo[j0 + q] = lo;
       if constexpr (MODE == MODE_SPLIT) s_hi[j0 + q] = hi;
     }
   }
 }
 
-__host__ __device__ constexpr size_t simple_smem_bytes(int Kp, int mode) {
-  return ((size_t)(CONV_TILE + Kp) * (mode == MODE_SPLIT ? 2 : 1) + Kp) * 4;
+// Operand region (32-bit lo [and hi] arrays), large enough to be reused as
+// the output staging tile (out_stage_words() words of wb bytes), rounded to
+// 16 bytes.  Then the taps (Kp int32) and, for MODE_WIDE, their prefix sums
+// (Kp int64).
+__host__ __device__ constexpr size_t operand_bytes(int Kp, int mode, int wb) {
+  return (((size_t)(CONV_TILE + Kp) * (mode == MODE_SPLIT ? 2 : 1) * 4 >
+                   (size_t)out_stage_words() * wb
+               ? (size_t)(CONV_TILE + Kp) * (mode == MODE_SPLIT ? 2 : 1) * 4
+               : (size_t)out_stage_words() * wb) +
+          15) / 16 * 16;
+}
+__host__ __device__ constexpr size_t simple_smem_bytes(int Kp, int mode,
+                                                       int wb) {
+  return operand_bytes(Kp, mode, wb) + (size_t)Kp * 4 +
+         (mode == MODE_WIDE ? (size_t)Kp * 8 : 0);
 }
 
 template <typename W, int MODE, bool VEC, bool PROT>
@@ -105,7 +124,12 @@ conv_simple_kernel(const ConvArgs p) {
   const int Kp = p.Kp;
   int* s_lo = reinterpret_cast<int*>(smem4);
   int* s_hi = s_lo + (CONV_TILE + Kp);
-  int* s_taps = s_lo + (CONV_TILE + Kp) * (MODE == MODE_SPLIT ? 2 : 1);
+  int* s_taps = reinterpret_cast<int*>(
+      reinterpret_cast<unsigned char*>(smem4) +
+      operand_bytes(Kp, MODE, (int)sizeof(W)));
+  long long* s_pref = reinterpret_cast<long long*>(s_taps + Kp);
+  __shared__ long long s_warp[CONV_THREADS / 32];
+  W* s_out = reinterpret_cast<W*>(smem4);  // reuses the operand region
 
   const int64_t tile = blockIdx.x / p.M;
   const int m = (int)(blockIdx.x - tile * p.M);
@@ -120,24 +144,44 @@ conv_simple_kernel(const ConvArgs p) {
                   (int64_t)(m == 0 ? p.M - 1 : m - 1) * p.ldx;
   for (int j = threadIdx.x; j < Kp; j += CONV_THREADS)
     s_taps[j] = j < p.K ? __ldg(p.g + j) : 0;
-  stage_from_global<W, MODE, VEC, PROT>(row, prow, p.N, n0, Kp, p.l, s_lo,
-                                        s_hi);
+  stage_from_global<W, MODE, VEC, PROT>(row, prow, p.N, n0, Kp, p.l,
+                                        (W)p.bias, s_lo, s_hi);
   __syncthreads();
+  // range shift: outputs of an interior tile all see every tap (add the
+  // constant b * sum g); only the tiles at the two ends need the prefix sums
+  const bool edge = n0 < (int64_t)p.K - 1 || n0 + CONV_TILE > p.N;
+  unsigned long long shift_c = 0;
+  if constexpr (MODE == MODE_WIDE) {
+    if (p.bias != 0) {
+      if (edge)
+        tap_prefix(s_taps, p.K, s_pref, s_warp);
+      else
+        shift_c = (unsigned long long)p.bias *
+                  (unsigned long long)tap_total(s_taps, p.K, s_warp);
+    }
+  }
 
   unsigned long long a64[CONV_R];
   unsigned a32[CONV_R];
   conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32);
   W out[CONV_R];
+  const int64_t nt = n0 + (int64_t)threadIdx.x * CONV_R;
 #pragma unroll
-  for (int a = 0; a < CONV_R; ++a) out[a] = combine<W, MODE>(a64[a], a32[a]);
+  for (int a = 0; a < CONV_R; ++a) {
+    if constexpr (MODE == MODE_WIDE) {
+      if (p.bias != 0)
+        a64[a] += edge ? shift_correction(p.bias, s_pref, nt + a, p.N, p.K)
+                       : shift_c;
+    }
+    out[a] = combine<W, MODE>(a64[a], a32[a]);
+  }
   W* ybase = reinterpret_cast<W*>(p.y);
   if constexpr (!PROT) {
-    store_outputs<W, VEC>(ybase + (int64_t)m * p.ldy,
-                          n0 + (int64_t)threadIdx.x * CONV_R, p.Nout, out);
+    write_tile<W>(ybase + (int64_t)m * p.ldy, n0, p.Nout, out, s_out);
   } else {
     if (p.fail_mode == NE_FAIL_DROP && m == p.failed) return;  // result lost
-    protected_epilogue<W, VEC>(ybase, p.ldy, p.M, m, tile, n0, p.Nout, p.l,
-                               p.ws, out, &s_flag);
+    protected_epilogue<W>(ybase, p.ldy, p.M, m, tile, n0, p.Nout, p.l, p.ws,
+                          out, s_out, &s_flag);
   }
 }
 
@@ -148,7 +192,7 @@ template <typename W>
 __host__ __device__ constexpr size_t persistent_smem_bytes(int Kp, int mode,
                                                            bool prot) {
   return (size_t)(CONV_TILE + Kp) * sizeof(W) * (prot ? 2 : 1) +
-         simple_smem_bytes(Kp, mode);
+         simple_smem_bytes(Kp, mode, (int)sizeof(W));
 }
 
 // Is a unit of stream m computed at all?  (plain conv: live streams;
@@ -213,7 +257,12 @@ conv_persistent_kernel(const ConvArgs p) {
   W* raw1 = raw0 + span;  // only with PROT
   int* s_lo = reinterpret_cast<int*>(raw0 + (size_t)span * (PROT ? 2 : 1));
   int* s_hi = s_lo + span;
-  int* s_taps = s_lo + (size_t)span * (MODE == MODE_SPLIT ? 2 : 1);
+  int* s_taps = reinterpret_cast<int*>(
+      reinterpret_cast<unsigned char*>(s_lo) +
+      operand_bytes(Kp, MODE, (int)sizeof(W)));
+  long long* s_pref = reinterpret_cast<long long*>(s_taps + Kp);
+  __shared__ long long s_warp[CONV_THREADS / 32];
+  W* s_out = reinterpret_cast<W*>(s_lo);  // reuses the operand region
   const int64_t U = p.ntiles * p.M;
   const W* xb = reinterpret_cast<const W*>(p.x);
   W* ybase = reinterpret_cast<W*>(p.y);
@@ -225,6 +274,10 @@ conv_persistent_kernel(const ConvArgs p) {
     fence_mbar_init();
   }
   __syncthreads();
+  if constexpr (MODE == MODE_WIDE) {
+    if (p.bias != 0) tap_prefix(s_taps, p.K, s_pref, s_warp);
+  }
+  const W bias = (W)p.bias;
 
   int64_t u = next_unit<PROT>(p, blockIdx.x, U);
   if (threadIdx.x == 0 && u < U) issue_unit_copy<W, PROT>(p, u, raw0, raw1, &bar);
@@ -255,7 +308,8 @@ conv_persistent_kernel(const ConvArgs p) {
           if constexpr (PROT) v = wadd<W>(v, shl<W>(__ldg(prow + gi), p.l));
         }
         int a, b;
-        split_word<W, MODE>(v, a, b);
+        split_word<W, MODE>((gi >= 0 && gi < p.N) ? wsub<W>(v, bias) : (W)0,
+                            a, b);
         s_lo[j] = a;
         if constexpr (MODE == MODE_SPLIT) s_hi[j] = b;
       }
@@ -270,15 +324,21 @@ conv_persistent_kernel(const ConvArgs p) {
     unsigned a32[CONV_R];
     conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32);
     W out[CONV_R];
+    const int64_t nt = n0 + (int64_t)threadIdx.x * CONV_R;
 #pragma unroll
-    for (int a = 0; a < CONV_R; ++a) out[a] = combine<W, MODE>(a64[a], a32[a]);
+    for (int a = 0; a < CONV_R; ++a) {
+      if constexpr (MODE == MODE_WIDE) {
+        if (p.bias != 0)
+          a64[a] += shift_correction(p.bias, s_pref, nt + a, p.N, p.K);
+      }
+      out[a] = combine<W, MODE>(a64[a], a32[a]);
+    }
     if constexpr (!PROT) {
-      store_outputs<W, true>(ybase + (int64_t)m * p.ldy,
-                             n0 + (int64_t)threadIdx.x * CONV_R, p.Nout, out);
+      write_tile<W>(ybase + (int64_t)m * p.ldy, n0, p.Nout, out, s_out);
     } else {
       if (!(p.fail_mode == NE_FAIL_DROP && m == p.failed))
-        protected_epilogue<W, true>(ybase, p.ldy, p.M, m, tile, n0, p.Nout,
-                                    p.l, p.ws, out, &s_flag);
+        protected_epilogue<W>(ybase, p.ldy, p.M, m, tile, n0, p.Nout, p.l,
+                              p.ws, out, s_out, &s_flag);
     }
     __syncthreads();
     u = nxt;
@@ -300,12 +360,12 @@ int set_max_smem(K kernel, size_t bytes) {
 
 template <typename W, int MODE, bool VEC, bool PROT>
 int launch_simple(const ConvArgs& a, cudaStream_t s) {
-  const size_t smem = simple_smem_bytes(a.Kp, MODE);
+  const size_t smem = simple_smem_bytes(a.Kp, MODE, (int)sizeof(W));
   static std::once_flag once;
   static int attr = NE_OK;
   std::call_once(once, [] {
     attr = set_max_smem(conv_simple_kernel<W, MODE, VEC, PROT>,
-                        simple_smem_bytes(CONV_MAX_K, MODE_SPLIT));
+                        simple_smem_bytes(CONV_MAX_K, MODE_SPLIT, 8));
   });
   if (attr != NE_OK) return attr;
   const int64_t blocks = a.ntiles * a.M;
@@ -337,9 +397,21 @@ int launch_persistent(const ConvArgs& a, cudaStream_t s) {
   return status_from_cuda(cudaGetLastError());
 }
 
+// Kernel choice for aligned inputs: the one-block-per-unit kernel (default:
+// measured faster for the single-job shapes) or the persistent bulk-copy
+// kernel (NE_CONV_KERNEL=persistent).
+inline bool use_persistent() {
+  static const bool v = [] {
+    const char* e = getenv("NE_CONV_KERNEL");
+    return e && strcmp(e, "persistent") == 0;
+  }();
+  return v;
+}
+
 template <typename W, int MODE, bool PROT>
 int launch_conv(const ConvArgs& a, bool vec, cudaStream_t s) {
-  if (vec && persistent_smem_bytes<W>(a.Kp, MODE, PROT) <= kSmemBudget)
+  if (vec && use_persistent() &&
+      persistent_smem_bytes<W>(a.Kp, MODE, PROT) <= kSmemBudget)
     return launch_persistent<W, MODE, PROT>(a, s);
   return vec ? launch_simple<W, MODE, true, PROT>(a, s)
              : launch_simple<W, MODE, false, PROT>(a, s);
@@ -360,6 +432,23 @@ inline bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 
 inline size_t rows_bytes(int rows, int64_t ld, int64_t n, int wb) {
   return ((size_t)(rows - 1) * (size_t)ld + (size_t)n) * (size_t)wb;
+}
+
+// Arithmetic mode for w-bit words whose values lie in [lo, hi] (if known):
+// 32-bit words multiply-add in 32 bits; 64-bit words whose range spans at
+// most 2^32 values take one 32x32->64 multiply-add per tap after a shift by
+// *bias (0 when the range already fits 32 bits); any other 64-bit words use
+// the split operands.
+inline int choose_mode(int w, bool known, __int128 lo, __int128 hi,
+                       long long* bias) {
+  *bias = 0;
+  if (w == 32) return MODE_I32;
+  if (!known || hi - lo > (__int128)0xffffffffLL) return MODE_SPLIT;
+  const __int128 i32min = -((__int128)1 << 31), i32max = ((__int128)1 << 31) - 1;
+  if (lo >= i32min && hi <= i32max) return MODE_WIDE;
+  // x - b in [-2^31, hi - lo - 2^31]; b is used modulo 2^64
+  *bias = (long long)(uint64_t)(unsigned __int128)(lo - i32min);
+  return MODE_WIDE;
 }
 
 // Exact range limit for an arbitrary shift l (see ne_params).
@@ -395,10 +484,10 @@ using namespace ne;
 extern "C" {
 
 int ne_conv(const void* x, int64_t ldx, int M, int64_t N, const int32_t* g,
-            int K, void* y, int64_t ldy, int w, int64_t max_abs_x,
+            int K, void* y, int64_t ldy, int w, int64_t x_min, int64_t x_max,
             uint32_t live_mask, void* stream) {
   if (M < 1 || M > 32 || N < 0 || K < 1 || K > CONV_MAX_K || ldx < N ||
-      (w != 32 && w != 64) || max_abs_x < 0)
+      (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;  // nothing to convolve; no output is written
   const int64_t Nout = N + K - 1;
@@ -419,10 +508,11 @@ int ne_conv(const void* x, int64_t ldx, int M, int64_t N, const int32_t* g,
   a.y = y;
   a.ldy = ldy;
   a.live_mask = live_mask;
-  const int mode = (w == 32) ? MODE_I32
-                   : (max_abs_x > 0 && max_abs_x <= 0x7fffffffLL) ? MODE_WIDE
-                                                                  : MODE_SPLIT;
-  const bool vec = rows_aligned16(x, ldx, wb) && rows_aligned16(y, ldy, wb);
+  const int mode = choose_mode(w, x_min <= x_max, (__int128)x_min,
+                               (__int128)x_max, &a.bias);
+  // input rows decide the staging path (bulk copies need 16-byte aligned
+  // rows); outputs are stored through shared memory for any alignment
+  const bool vec = rows_aligned16(x, ldx, wb);
   return dispatch_conv<false>(a, w, mode, vec, (cudaStream_t)stream);
 }
 
@@ -434,14 +524,19 @@ size_t ne_protected_conv_ws_bytes(int M, int64_t N, int K) {
 }
 
 int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
-                      const int32_t* g, int K, int w, int l,
-                      int64_t max_abs_c, int64_t max_abs_g, int failed,
+                      const int32_t* g, int K, int w, int l, int64_t c_min,
+                      int64_t c_max, int64_t max_abs_g, int failed,
                       int fail_mode, void* d, int64_t ldd, void* ws,
                       size_t ws_bytes, void* stream) {
   if (M < 3 || M > 32 || N < 0 || K < 1 || K > CONV_MAX_K || ldc < N ||
       (w != 32 && w != 64) || l <= 0 || l >= w || (M - 1) * l > w ||
-      max_abs_c < 0 || max_abs_g < 0)
+      c_min > c_max || max_abs_g < 0)
     return NE_ERR_INVALID_ARG;
+  const unsigned __int128 max_abs_c =
+      (unsigned __int128)(c_min < 0 ? -(__int128)c_min : (__int128)c_min) >
+              (unsigned __int128)(c_max < 0 ? -(__int128)c_max : (__int128)c_max)
+          ? (unsigned __int128)(c_min < 0 ? -(__int128)c_min : (__int128)c_min)
+          : (unsigned __int128)(c_max < 0 ? -(__int128)c_max : (__int128)c_max);
   if (fail_mode != NE_FAIL_NONE && fail_mode != NE_FAIL_SKIP &&
       fail_mode != NE_FAIL_DROP)
     return NE_ERR_INVALID_ARG;
@@ -449,10 +544,12 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
     return NE_ERR_INVALID_ARG;
   const int64_t Nout = N + K - 1;
   // dynamic range (Eq. 13 / exact limit): |d| <= K max|c| max|g|
-  const unsigned __int128 need = (unsigned __int128)K *
-                                 (unsigned __int128)max_abs_c *
-                                 (unsigned __int128)max_abs_g;
-  if (need > exact_limit(M, w, l)) return NE_ERR_RANGE;
+  const unsigned __int128 need =
+      (unsigned __int128)K * max_abs_c * (unsigned __int128)max_abs_g;
+  if (need > exact_limit(M, w, l) ||
+      max_abs_c > (((unsigned __int128)1 << (w - 1)) - 1) /
+                      (((unsigned __int128)1 << l) + 1))
+    return NE_ERR_RANGE;
   if (N == 0) return NE_OK;  // nothing to convolve; no output is written
   if (!c || !g || !d || ldd < Nout) return NE_ERR_INVALID_ARG;
   const int wb = w / 8;
@@ -479,12 +576,12 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   a.failed = failed;
   a.fail_mode = fail_mode;
   a.ws = (uint32_t*)ws;
-  // bound on |eps| = |c_m + 2^l c_{m-1}| <= max|c| (2^l + 1)
-  const unsigned __int128 eps_max =
-      (unsigned __int128)max_abs_c * (((unsigned __int128)1 << l) + 1);
-  const int mode = (w == 32) ? MODE_I32
-                   : (eps_max <= 0x7fffffffULL) ? MODE_WIDE : MODE_SPLIT;
-  const bool vec = rows_aligned16(c, ldc, wb) && rows_aligned16(d, ldd, wb);
+  // eps = c_m + 2^l c_{m-1} is increasing in both inputs, so it lies in
+  // [c_min (2^l + 1), c_max (2^l + 1)]
+  const __int128 f = ((__int128)1 << l) + 1;
+  const int mode = choose_mode(w, true, (__int128)c_min * f,
+                               (__int128)c_max * f, &a.bias);
+  const bool vec = rows_aligned16(c, ldc, wb);
   return dispatch_conv<true>(a, w, mode, vec, s);
 }
 

@@ -10,7 +10,10 @@
 // Exact arithmetic modes (chosen on the host from the word width and the
 // declared input bound -- the dynamic-range bound decides the accumulator):
 //   MODE_I32   w = 32: one 32-bit multiply-add per tap, modulo 2^32.
-//   MODE_WIDE  w = 64, |x| < 2^31: one 32x32->64 multiply-add per tap.
+//   MODE_WIDE  w = 64 and the declared range of x spans at most 2^32
+//              values: x - b fits 32 bits for a bias b, sum x*g = sum
+//              (x-b)*g + b*G(n) (G(n) = sum of the taps that meet the input
+//              at output n): one 32x32->64 multiply-add per tap.
 //   MODE_SPLIT w = 64, any x: x = hi*2^32 + lo (lo the sign-extended low
 //              word), sum x*g = sum lo*g + 2^32 sum hi*g (mod 2^64).
 // All are exact modulo 2^w, the ring the method works in.
@@ -24,7 +27,7 @@ namespace ne {
 enum { MODE_I32 = 0, MODE_WIDE = 1, MODE_SPLIT = 2 };
 
 #ifndef NE_CONV_THREADS
-#define NE_CONV_THREADS 256
+#define NE_CONV_THREADS 128
 #endif
 constexpr int CONV_THREADS = NE_CONV_THREADS;
 constexpr int CONV_MIN_BLOCKS = 512 / CONV_THREADS;  // 512 threads per SM
@@ -121,27 +124,102 @@ __device__ __forceinline__ W combine(unsigned long long a64, unsigned a32) {
   }
 }
 
-// Store this thread's outputs [n, n + R) of one row (clipped to Nout).
-template <typename W, bool VEC>
-__device__ __forceinline__ void store_outputs(W* __restrict__ yrow, int64_t n,
-                                              int64_t Nout,
-                                              const W (&out)[CONV_R]) {
-  if (VEC && n + CONV_R <= Nout) {
-    constexpr int V = Vec<W>::n;
-    using VT = typename Vec<W>::T;
+// Write one output tile [n0, n0 + TILE) of a row (clipped to Nout) through
+// shared memory: each thread parks its R consecutive outputs, then the block
+// stores the tile with warp-contiguous accesses (thread t writes words
+// t, t + THREADS, ...), whatever the row's alignment.  Word j is parked at
+// j + j/16 (one pad word per 16) so that the strided parking is free of
+// bank conflicts.  s_out holds out_stage_words() words and may alias operand
+// buffers the block has finished reading.  Contains block barriers: every
+// thread must call it.
+__host__ __device__ constexpr int out_stage_words() {
+  return CONV_TILE + CONV_TILE / 16;
+}
+__device__ __forceinline__ int out_slot(int j) { return j + (j >> 4); }
+
+template <typename W>
+__device__ __forceinline__ void write_tile(W* __restrict__ yrow, int64_t n0,
+                                           int64_t Nout,
+                                           const W (&out)[CONV_R],
+                                           W* __restrict__ s_out) {
+  __syncthreads();  // the block is done reading whatever s_out aliases
 #pragma unroll
-    for (int q = 0; q < CONV_R / V; ++q) {
-      VT v;
-      W* pv = reinterpret_cast<W*>(&v);
+  for (int a = 0; a < CONV_R; ++a)
+    s_out[out_slot(threadIdx.x * CONV_R + a)] = out[a];
+  __syncthreads();
+  const int nvalid = (int)lmin((int64_t)CONV_TILE, Nout - n0);
+  for (int j = threadIdx.x; j < nvalid; j += CONV_THREADS)
+    yrow[n0 + j] = s_out[out_slot(j)];
+}
+
+// ---------------------------------------------------------------------------
+// Range shift of MODE_WIDE.  The conv of a shifted input x - b differs from
+// the conv of x by b*G(n), G(n) = sum of g[t] over the taps t that meet the
+// input at output n: 0 <= n - t < N.  tap_prefix() fills s_pref[t] =
+// g[0] + ... + g[t] (64-bit) with a block-wide scan; every thread must call
+// it.  s_warp holds CONV_THREADS/32 words of scratch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tap_prefix(const int* __restrict__ s_taps,
+                                           int K, long long* __restrict__ s_pref,
+                                           long long* __restrict__ s_warp) {
+  const int chunk = (K + CONV_THREADS - 1) / CONV_THREADS;
+  const int t0 = min(K, (int)threadIdx.x * chunk);
+  const int t1 = min(K, t0 + chunk);
+  long long loc = 0;
+  for (int t = t0; t < t1; ++t) loc += s_taps[t];
+  // inclusive scan of the per-thread sums: within warps, then across warps
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long inc = loc;
 #pragma unroll
-      for (int i = 0; i < V; ++i) pv[i] = out[q * V + i];
-      reinterpret_cast<VT*>(yrow + n)[q] = v;
-    }
-  } else {
-#pragma unroll
-    for (int a = 0; a < CONV_R; ++a)
-      if (n + a < Nout) yrow[n + a] = out[a];
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
   }
+  if (lane == 31) s_warp[wid] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long run = 0;
+    for (int w = 0; w < CONV_THREADS / 32; ++w) {
+      const long long v = s_warp[w];
+      s_warp[w] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  long long run = s_warp[wid] + inc - loc;  // exclusive prefix of this chunk
+  for (int t = t0; t < t1; ++t) {
+    run += s_taps[t];
+    s_pref[t] = run;
+  }
+  __syncthreads();
+}
+
+// Sum of all K taps (every thread gets it); s_warp: CONV_THREADS/32 words.
+__device__ __forceinline__ long long tap_total(const int* __restrict__ s_taps,
+                                               int K,
+                                               long long* __restrict__ s_warp) {
+  long long v = 0;
+  for (int t = threadIdx.x; t < K; t += CONV_THREADS) v += s_taps[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
+  __syncthreads();
+  long long tot = 0;
+#pragma unroll
+  for (int w = 0; w < CONV_THREADS / 32; ++w) tot += s_warp[w];
+  __syncthreads();
+  return tot;
+}
+
+// b * G(n) modulo 2^64 for output n of an N-sample input and K taps.
+__device__ __forceinline__ unsigned long long shift_correction(
+    long long bias, const long long* __restrict__ s_pref, int64_t n, int64_t N,
+    int K) {
+  const int64_t hi = lmin((int64_t)K - 1, n);
+  const int64_t lo = lmax((int64_t)0, n - N + 1);
+  if (hi < lo) return 0ull;
+  const long long G = s_pref[hi] - (lo > 0 ? s_pref[lo - 1] : 0ll);
+  return (unsigned long long)bias * (unsigned long long)G;
 }
 
 // ---------------------------------------------------------------------------
@@ -154,10 +232,30 @@ __device__ __forceinline__ void store_outputs(W* __restrict__ yrow, int64_t n,
 // ws: {claim, ready} per tile, zero at launch.  Must be called by every
 // thread of the block (it contains block barriers).
 // ---------------------------------------------------------------------------
-template <typename W, bool VEC>
+// Extract the tile's `span` columns from n0 in place, failed stream r.
+template <typename W, int NV, int MAXC>
+__device__ __forceinline__ void extract_tile(W* ybase, int64_t ldy, int M,
+                                             int r, int64_t n0, int span,
+                                             int l) {
+  W* rows[MAXC];
+  int row = r + 1 == M ? 0 : r + 1;
+#pragma unroll
+  for (int q = 0; q < MAXC; ++q) {
+    rows[q] = ybase + (int64_t)row * ldy + n0;
+    row = row + 1 == M ? 0 : row + 1;
+  }
+  W* row_r = ybase + (int64_t)r * ldy + n0;
+#pragma unroll 1
+  for (int n = threadIdx.x; n < span; n += CONV_THREADS * NV)
+    recover_columns_batched<W, NV, MAXC>(rows, row_r, M, n, CONV_THREADS, span,
+                                         l);
+}
+
+template <typename W>
 __device__ __forceinline__ void protected_epilogue(
     W* __restrict__ ybase, int64_t ldy, int M, int m, int64_t tile, int64_t n0,
-    int64_t Nout, int l, uint32_t* ws, const W (&out)[CONV_R], int* s_flag) {
+    int64_t Nout, int l, uint32_t* ws, const W (&out)[CONV_R], W* s_out,
+    int* s_flag) {
   uint32_t* claim = ws + 2 * tile;
   uint32_t* ready = claim + 1;
   if (threadIdx.x == 0) *s_flag = (int)atomicAdd(claim, 1u);
@@ -165,8 +263,7 @@ __device__ __forceinline__ void protected_epilogue(
   const bool publish = *s_flag < M - 1;
   __syncthreads();
   if (!publish) return;
-  const int64_t nt = n0 + (int64_t)threadIdx.x * CONV_R;
-  store_outputs<W, VEC>(ybase + (int64_t)m * ldy, nt, Nout, out);
+  write_tile<W>(ybase + (int64_t)m * ldy, n0, Nout, out, s_out);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -181,15 +278,13 @@ __device__ __forceinline__ void protected_epilogue(
   const uint32_t full = M >= 32 ? 0xffffffffu : ((1u << M) - 1u);
   const int r = __ffs((int)(~(uint32_t)mask & full)) - 1;
   const int64_t end = min(n0 + (int64_t)CONV_TILE, Nout);
-  if (M <= 9) {
-    // thread t owns columns n0 + t + CONV_THREADS i: every warp access is one
-    // contiguous segment; all M-1 rows of NV columns are in flight at once
-    constexpr int NV = 2;
-#pragma unroll 1
-    for (int64_t n = n0 + threadIdx.x; n < end;
-         n += (int64_t)CONV_THREADS * NV)
-      recover_columns_batched<W, NV, 8>(ybase, ldy, M, n, CONV_THREADS, end,
-                                        l, r, ybase, ldy);
+  // thread t owns columns n0 + t + CONV_THREADS i: every warp access is one
+  // contiguous segment; all M-1 rows of NV columns are in flight at once
+  const int span = (int)(end - n0);
+  if (M <= 4) {
+    extract_tile<W, 4, 3>(ybase, ldy, M, r, n0, span, l);
+  } else if (M <= 9) {
+    extract_tile<W, 2, 8>(ybase, ldy, M, r, n0, span, l);
   } else {
     for (int64_t n = n0 + threadIdx.x; n < end; n += CONV_THREADS)
       recover_columns<W, 0, 1, true>(ybase, ldy, M, n, l, r, ybase, ldy);

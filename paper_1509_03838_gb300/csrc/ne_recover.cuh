@@ -133,25 +133,23 @@ __device__ __forceinline__ void recover_columns(const W* delta, int64_t ldd,
 // Recover NV columns n + i*cstride (i < NV) at once, all M-1 delta rows held
 // in registers (requires M - 1 <= MAXC): every load of the group is issued
 // before any arithmetic, so a thread keeps (M-1)*NV independent loads in
-// flight.  Reads go through L2 only (data written by other blocks).  A
-// column at or beyond `end` is skipped.  In place is allowed (d == delta).
+// flight.  rows[q] = row (r + 1 + q) mod M of the tile, q < M-1 (delta and
+// d share them: in place).  Reads go through L2 only (data written by
+// other blocks).  Columns at or beyond `end` are skipped.
 template <typename W, int NV, int MAXC>
 __device__ __forceinline__ void recover_columns_batched(
-    const W* delta, int64_t ldd, int M, int64_t n, int64_t cstride,
-    int64_t end, int l, int r, W* d, int64_t ldo) {
+    W* const (&rows)[MAXC], W* __restrict__ row_r, int M, int n, int cstride,
+    int end, int l) {
   W cache[MAXC][NV];
   bool live[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) live[i] = (n + i * cstride) < end;
-  int row = r + 1 == M ? 0 : r + 1;
 #pragma unroll
   for (int q = 0; q < MAXC; ++q) {
     if (q < M - 1) {
 #pragma unroll
       for (int i = 0; i < NV; ++i)
-        cache[q][i] = live[i] ? __ldcg(delta + (int64_t)row * ldd + n + i * cstride)
-                              : (W)0;
-      row = row + 1 == M ? 0 : row + 1;
+        cache[q][i] = live[i] ? __ldcg(rows[q] + n + i * cstride) : (W)0;
     }
   }
   W t[NV];
@@ -171,22 +169,20 @@ __device__ __forceinline__ void recover_columns_batched(
 #pragma unroll
   for (int i = 0; i < NV; ++i)
     dcur[i] = sext_low<W>((M & 1) ? wsub<W>((W)0, t[i]) : t[i], win);
-  int j = r == 0 ? M - 1 : r - 1;
 #pragma unroll
   for (int q = MAXC - 1; q >= 0; --q) {
     if (q <= M - 2) {
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
         const W nxt = wsub<W>(cache[q][i], dcur[i]) >> l;
-        if (live[i]) d[(int64_t)j * ldo + n + i * cstride] = dcur[i];
+        if (live[i]) rows[q][n + i * cstride] = dcur[i];
         dcur[i] = nxt;
       }
-      j = j == 0 ? M - 1 : j - 1;
     }
   }
 #pragma unroll
   for (int i = 0; i < NV; ++i)
-    if (live[i]) d[(int64_t)r * ldo + n + i * cstride] = dcur[i];
+    if (live[i]) row_r[n + i * cstride] = dcur[i];
 }
 
 }  // namespace ne

@@ -75,12 +75,13 @@ _SIGS = {
     "ne_choose_width": ([_i32, _i32, _i64, _i64, ctypes.POINTER(_Params)], _i32),
     "ne_entangle": ([_vp, _i64, _vp, _i64, _i32, _i64, _i32, _i32, _vp], _i32),
     "ne_conv": ([_vp, _i64, _i32, _i64, _vp, _i32, _vp, _i64, _i32, _i64,
-                 _u32, _vp], _i32),
+                 _i64, _u32, _vp], _i32),
     "ne_recover": ([_vp, _i64, _i32, _i64, _i32, _i32, _i32, _vp, _i64, _vp],
                    _i32),
     "ne_extract": ([_vp, _i64, _i32, _i64, _i32, _i32, _vp, _i64, _vp], _i32),
     "ne_protected_conv": ([_vp, _i64, _i32, _i64, _vp, _i32, _i32, _i32, _i64,
-                           _i64, _i32, _i32, _vp, _i64, _vp, _sz, _vp], _i32),
+                           _i64, _i64, _i32, _i32, _vp, _i64, _vp, _sz, _vp],
+                          _i32),
     "ne_protected_conv_ws_bytes": ([_i32, _i64, _i32], _sz),
     "ne_checksum": ([_vp, _i64, _i32, _i64, _i32, _vp, _vp], _i32),
     "ne_checksum_recover": ([_vp, _i64, _vp, _i32, _i64, _i32, _i32, _vp, _vp],
@@ -202,9 +203,12 @@ def ne_entangle(c: torch.Tensor, eps: torch.Tensor | None = None, *, l: int,
 
 
 def ne_conv(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
-            max_abs_x: int = 0, live_mask: int = 0xFFFFFFFF,
-            N: int | None = None, stream=None) -> torch.Tensor:
-    """y_m = x_m * g (full linear convolution, Eq. 9) for live streams."""
+            x_range: tuple[int, int] | None = None,
+            live_mask: int = 0xFFFFFFFF, N: int | None = None,
+            stream=None) -> torch.Tensor:
+    """y_m = x_m * g (full linear convolution, Eq. 9) for live streams.
+    x_range = (x_min, x_max): declared range of the inputs, or None."""
+    x_min, x_max = x_range if x_range is not None else (1, 0)
     px, M, n, ldx = _rows(x, "x")
     py, _, _, ldy = _rows(y, "y")
     if g.dtype != torch.int32 or not g.is_cuda:
@@ -213,7 +217,8 @@ def ne_conv(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
     assert _word_bits(y) == w
     _check(lib().ne_conv(px, ldx, M, n if N is None else N,
                          ctypes.c_void_p(g.data_ptr()), g.numel(), py, ldy, w,
-                         max_abs_x, live_mask & 0xFFFFFFFF, _stream(stream)),
+                         x_min, x_max, live_mask & 0xFFFFFFFF,
+                         _stream(stream)),
            "ne_conv")
     return y
 
@@ -239,11 +244,12 @@ def ne_extract(delta: torch.Tensor, d: torch.Tensor, *, l: int,
 
 
 def ne_protected_conv(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
-                      l: int, max_abs_c: int, max_abs_g: int,
+                      l: int, c_range: tuple[int, int], max_abs_g: int,
                       failed: int = -1, fail_mode: int = NE_FAIL_NONE,
                       ws: torch.Tensor | None = None, N: int | None = None,
                       stream=None) -> torch.Tensor:
-    """Entangle-on-load -> conv -> extract/recover, one launch (d = c * g)."""
+    """Entangle-on-load -> conv -> extract/recover, one launch (d = c * g).
+    c_range = (c_min, c_max): declared range of the inputs."""
     pc, M, n, ldc = _rows(c, "c")
     pd, _, _, ldd = _rows(d, "d")
     n = n if N is None else N
@@ -253,7 +259,8 @@ def ne_protected_conv(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
     if ws is None:
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=c.device)
     _check(lib().ne_protected_conv(pc, ldc, M, n, ctypes.c_void_p(g.data_ptr()),
-                                   K, w, l, max_abs_c, max_abs_g, failed,
+                                   K, w, l, int(c_range[0]),
+                                   int(c_range[1]), max_abs_g, failed,
                                    fail_mode, pd, ldd,
                                    ctypes.c_void_p(ws.data_ptr()),
                                    ws.numel() * ws.element_size(),

@@ -5,8 +5,8 @@
 Cases (default data: M = 4 streams, N = 2^22 samples, K = 64 taps, 16-bit
 data and taps, 64-bit words, the benchmark's workload):
   protected      fused entangle-on-load + conv + extraction (stream 1 dropped)
-  conv_split     plain conv, 64-bit split-operand arithmetic
-  conv_wide      plain conv, one 32x32->64 multiply-add per tap
+  conv_split     plain conv, range not declared: split 64-bit operands
+  conv_wide      plain conv, declared range: one 32x32->64 multiply-add/tap
   entangle       out-of-place entanglement
   recover        recovery of all streams with stream 1 missing
   checksum       checksum stream of the ABFT baseline
@@ -41,10 +41,10 @@ def main() -> int:
     r = torch.empty(N, dtype=torch.int64, device=dev)
     ops = {
         "protected": lambda: ne.ne_protected_conv(
-            c, g, d, l=p.l, max_abs_c=j.bound_c, max_abs_g=j.bound_g,
+            c, g, d, l=p.l, c_range=j.c_range, max_abs_g=j.bound_g,
             failed=1, fail_mode=ne.NE_FAIL_DROP, ws=ws),
-        "conv_split": lambda: ne.ne_conv(c, g, d, max_abs_x=0),
-        "conv_wide": lambda: ne.ne_conv(c, g, d, max_abs_x=j.bound_c),
+        "conv_split": lambda: ne.ne_conv(c, g, d),
+        "conv_wide": lambda: ne.ne_conv(c, g, d, x_range=j.c_range),
         "entangle": lambda: ne.ne_entangle(c, eps, l=p.l),
         "recover": lambda: ne.ne_recover(d, d, l=p.l, failed=1),
         "checksum": lambda: ne.ne_checksum(c, r),

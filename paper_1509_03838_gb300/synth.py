@@ -55,6 +55,11 @@ class StreamJob:
     def K(self) -> int:
         return self.g.shape[0]
 
+    @property
+    def c_range(self) -> tuple[int, int]:
+        """Declared (min, max) of the inputs: uniform in [-b, b)."""
+        return (-self.bound_c, self.bound_c - 1)
+
 
 def stream_job(seed: int, M: int, N: int, K: int, data_bits: int,
                tap_bits: int, w: int, failed: int | None = None) -> StreamJob:

@@ -117,10 +117,10 @@ def test_argument_errors_return_before_launch(ne):
     # l out of range
     assert L.ne_entangle(DUMMY, 8, DUMMY, 8, 3, 8, 32, 32, s) == ne.NE_ERR_INVALID_ARG
     # K = 0, K too large
-    assert L.ne_conv(DUMMY, 8, 3, 8, DUMMY, 0, DUMMY, 8, 64, 0, 7, s) == ne.NE_ERR_INVALID_ARG
-    assert L.ne_conv(DUMMY, 8, 3, 8, DUMMY, 9000, DUMMY, 9100, 64, 0, 7, s) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_conv(DUMMY, 8, 3, 8, DUMMY, 0, DUMMY, 8, 64, 1, 0, 7, s) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_conv(DUMMY, 8, 3, 8, DUMMY, 9000, DUMMY, 9100, 64, 1, 0, 7, s) == ne.NE_ERR_INVALID_ARG
     # output leading dimension shorter than N + K - 1
-    assert L.ne_conv(DUMMY, 8, 3, 8, DUMMY, 4, DUMMY, 10, 64, 0, 7, s) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_conv(DUMMY, 8, 3, 8, DUMMY, 4, DUMMY, 10, 64, 1, 0, 7, s) == ne.NE_ERR_INVALID_ARG
     # failed index out of range
     assert L.ne_recover(DUMMY, 8, 4, 8, 64, 16, 4, DUMMY, 8, s) == ne.NE_ERR_INVALID_ARG
     # (M-1) l > w
@@ -133,22 +133,33 @@ def test_protected_conv_range_and_failure_checks(ne):
     p = ne.ne_params(4, 64)
     # K * max|c| * max|g| beyond the exact limit -> NE_ERR_RANGE
     st = L.ne_protected_conv(DUMMY, 1 << 20, 4, 1 << 20, DUMMY, 64, 64, p.l,
-                             1 << 30, 1 << 30, -1, ne.NE_FAIL_NONE, DUMMY,
-                             (1 << 20) + 63, DUMMY, 1 << 20, s)
+                             -(1 << 30), 1 << 30, 1 << 30, -1, ne.NE_FAIL_NONE,
+                             DUMMY, (1 << 20) + 63, DUMMY, 1 << 20, s)
+    assert st == ne.NE_ERR_RANGE
+    # the declared range must be ordered
+    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, 5, 4, 100,
+                             -1, ne.NE_FAIL_NONE, DUMMY, 71, DUMMY, 1 << 20, s)
+    assert st == ne.NE_ERR_INVALID_ARG
+    # entangled words must fit the word: |c| (2^l + 1) < 2^(w-1)
+    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, 0, 1 << 48,
+                             0, -1, ne.NE_FAIL_NONE, DUMMY, 71, DUMMY, 1 << 20,
+                             s)
     assert st == ne.NE_ERR_RANGE
     # failure mode without a stream, and a stream without a mode
-    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, 100, 100,
-                             -1, ne.NE_FAIL_SKIP, DUMMY, 71, DUMMY, 1 << 20, s)
+    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, -100, 100,
+                             100, -1, ne.NE_FAIL_SKIP, DUMMY, 71, DUMMY,
+                             1 << 20, s)
     assert st == ne.NE_ERR_INVALID_ARG
-    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, 100, 100,
-                             2, ne.NE_FAIL_NONE, DUMMY, 71, DUMMY, 1 << 20, s)
+    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, -100, 100,
+                             100, 2, ne.NE_FAIL_NONE, DUMMY, 71, DUMMY,
+                             1 << 20, s)
     assert st == ne.NE_ERR_INVALID_ARG
     # workspace too small
     need = ne.ne_protected_conv_ws_bytes(4, 64, 8)
     assert need > 0
-    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, 100, 100,
-                             -1, ne.NE_FAIL_NONE, ctypes.c_void_p(0x100000), 71,
-                             DUMMY, need - 1, s)
+    st = L.ne_protected_conv(DUMMY, 64, 4, 64, DUMMY, 8, 64, p.l, -100, 100,
+                             100, -1, ne.NE_FAIL_NONE,
+                             ctypes.c_void_p(0x100000), 71, DUMMY, need - 1, s)
     assert st == ne.NE_ERR_NOMEM
 
 

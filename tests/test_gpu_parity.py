@@ -1,6 +1,6 @@
 """GPU parity: every kernel of the hot path against the CPU oracle, bit-exact.
 
-Sizes span several 3072-sample output tiles with ragged tails; edge cases
+Sizes span several 1536-sample output tiles with ragged tails; edge cases
 cover N = 0, N < K, K = 1, the maximum K, unaligned rows (scalar paths),
 in-place operation and every failed-stream index under every failure mode.
 """
@@ -12,7 +12,7 @@ from paper_1509_03838_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TILE = 3072
+TILE = 1536  # output samples per block (128 threads x 12)
 
 
 @pytest.fixture(scope="module")
@@ -89,27 +89,38 @@ def test_entangle(ne, orc, w, M, N, pad):
 # ---------------------------------------------------------------------------
 
 CONV_CASES = [
-    # w, M, N, K, input bits, declared bound (0 = unknown)
-    (32, 3, 2 * TILE + 77, 16, 7, 1 << 7),          # int32 words
-    (32, 4, 5000, 1, 12, 1 << 12),                  # K = 1
-    (64, 4, 3 * TILE + 1, 64, 15, 1 << 15),         # 64-bit, |x| < 2^31
-    (64, 4, 3 * TILE + 1, 64, 15, 0),               # 64-bit, split operands
-    (64, 3, 4000, 17, 40, 0),                       # wide entangled-size words
-    (64, 5, 513, 300, 20, 0),                       # N < K + tile
-    (64, 3, 9, 200, 20, 0),                         # N < K
-    (32, 3, 100, 8192, 5, 1 << 5),                  # maximum K
+    # w, M, N, K, inputs in [lo, hi], declared range (None = not declared)
+    (32, 3, 2 * TILE + 77, 16, (-128, 127), (-128, 127)),         # int32 words
+    (32, 4, 5000, 1, (-4096, 4095), (-4096, 4095)),               # K = 1
+    (64, 4, 3 * TILE + 1, 64, (-2**15, 2**15 - 1), (-2**15, 2**15 - 1)),
+    (64, 4, 3 * TILE + 1, 64, (-2**15, 2**15 - 1), None),         # split
+    (64, 3, 4000, 17, (-2**40, 2**40), None),                     # wide words
+    (64, 5, 513, 300, (-2**20, 2**20), (-2**20, 2**20)),          # N < K + tile
+    (64, 3, 9, 200, (-2**20, 2**20), None),                       # N < K
+    (32, 3, 100, 8192, (-32, 31), (-32, 31)),                     # maximum K
+    # declared ranges beyond 32 bits that span at most 2^32 values: the
+    # inputs are shifted into 32 bits and the shift is undone exactly
+    (64, 4, 2 * TILE + 5, 64, (-2**31 - 2**15, 2**31 - 2**15 - 1),
+     (-2**31 - 2**15, 2**31 - 2**15 - 1)),                        # span 2^32-1
+    (64, 3, 3 * TILE - 7, 33, (2**40, 2**40 + 2**32 - 1),
+     (2**40, 2**40 + 2**32 - 1)),                                 # offset
+    (64, 3, 9, 200, (-2**45 - 2**31, -2**45 + 2**31 - 1),
+     (-2**45 - 2**31, -2**45 + 2**31 - 1)),                       # edges only
+    (64, 5, 700, 1024, (-2**33, -2**33 + 2**30), (-2**33, -2**33 + 2**30)),
 ]
 
 
 @pytest.mark.parametrize("case", CONV_CASES)
 def test_conv(ne, orc, case):
-    w, M, N, K, bits, bound = case
-    gen = synth.rng(N * 7 + K)
-    x = synth.uniform_int(gen, (M, N), -(1 << bits), 1 << bits)
+    w, M, N, K, (lo, hi), declared = case
+    gen = synth.rng(N * 7 + K + (hi & 0xffff))
+    x = synth.uniform_int(gen, (M, N), lo, hi + 1)
+    x[:, 0] = lo
+    x[:, -1] = hi
     g = synth.uniform_int(gen, (K,), -(1 << 15), 1 << 15)
     expect = orc.conv(x, g, w, strict=False)
     y = torch.zeros((M, N + K - 1), dtype=dt(w), device="cuda")
-    ne.ne_conv(dev(x, w), taps(g), y, max_abs_x=bound)
+    ne.ne_conv(dev(x, w), taps(g), y, x_range=declared)
     torch.cuda.synchronize()
     assert np.array_equal(host(y), expect)
 
@@ -153,7 +164,7 @@ def test_empty_inputs_are_noops(ne):
     g = taps(np.ones(16))
     ne.ne_conv(x, g, y)
     p = ne.ne_params(3, 64)
-    ne.ne_protected_conv(x, g, y, l=p.l, max_abs_c=1, max_abs_g=1)
+    ne.ne_protected_conv(x, g, y, l=p.l, c_range=(-1, 1), max_abs_g=1)
     ne.ne_entangle(x, l=p.l)
     ne.ne_recover(x, x, l=p.l, failed=0)
     ne.ne_checksum(x, torch.zeros(0, dtype=torch.int64, device="cuda"))
@@ -246,7 +257,8 @@ def test_protected_conv_all_failures(ne, orc, case):
             _, _, d_or = orc.protected_conv(c, g, w, p.l, r)
             assert np.array_equal(d_or, plain)
         d = torch.full((M, N + K - 1), 99, dtype=dt(w), device="cuda")
-        ne.ne_protected_conv(cd, gd, d, l=p.l, max_abs_c=1 << bc,
+        ne.ne_protected_conv(cd, gd, d, l=p.l,
+                             c_range=(-(1 << bc), (1 << bc) - 1),
                              max_abs_g=1 << bg, failed=r, fail_mode=fm)
         torch.cuda.synchronize()
         assert np.array_equal(host(d), plain), (fm, r)
@@ -262,7 +274,8 @@ def test_protected_conv_repeat_reuses_workspace(ne, orc):
     cd, gd = dev(c, w), taps(g)
     for it in range(3):
         d = torch.zeros((M, N + K - 1), dtype=torch.int64, device="cuda")
-        ne.ne_protected_conv(cd, gd, d, l=p.l, max_abs_c=b, max_abs_g=b,
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-b, b - 1),
+                             max_abs_g=b,
                              failed=it % M, fail_mode=ne.NE_FAIL_DROP, ws=ws)
         torch.cuda.synchronize()
         assert np.array_equal(host(d), plain)
@@ -275,7 +288,7 @@ def test_protected_conv_range_error(ne):
     g = taps(np.ones(16))
     d = torch.zeros((M, 79), dtype=torch.int32, device="cuda")
     with pytest.raises(ne.NEError) as ei:
-        ne.ne_protected_conv(c, g, d, l=p.l, max_abs_c=1 << 10,
+        ne.ne_protected_conv(c, g, d, l=p.l, c_range=(-(1 << 10), 1 << 10),
                              max_abs_g=1 << 10)
     assert ei.value.status == ne.NE_ERR_RANGE
 
@@ -296,7 +309,7 @@ def test_checksum_path(ne, orc, w, M):
     torch.cuda.synchronize()
     assert np.array_equal(host(buf[M]), orc.checksum(c, w))
     out = torch.zeros((M + 1, N + K - 1), dtype=dt(w), device="cuda")
-    ne.ne_conv(buf, taps(g), out, max_abs_x=M << 12)
+    ne.ne_conv(buf, taps(g), out, x_range=(-M << 12, M << 12))
     plain = orc.conv(c, g, w)
     e = out[M].clone()
     for f in range(M):
@@ -370,7 +383,9 @@ def test_small_workload_every_failure(ne, orc):
     for r in range(j.M):
         delta = torch.full((j.M, j.N + j.K - 1), 5, dtype=torch.int32,
                            device="cuda")
-        ne.ne_conv(eps, taps(j.g), delta, max_abs_x=j.bound_c * (1 + 2 ** p.l),
+        f = 1 + 2 ** p.l
+        ne.ne_conv(eps, taps(j.g), delta,
+                   x_range=(j.c_range[0] * f, j.c_range[1] * f),
                    live_mask=0b111 & ~(1 << r))
         d = torch.empty_like(delta)
         ne.ne_recover(delta, d, l=p.l, failed=r)
@@ -428,7 +443,7 @@ def test_large_workload_full_size(ne, orc):
     ref = None
     for r in range(M):
         d = torch.empty((M, N + K - 1), dtype=torch.int64, device="cuda")
-        ne.ne_protected_conv(cd, gd, d, l=p.l, max_abs_c=j.bound_c,
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=j.c_range,
                              max_abs_g=j.bound_g, failed=r,
                              fail_mode=ne.NE_FAIL_DROP, ws=ws)
         torch.cuda.synchronize()
