@@ -197,6 +197,36 @@ int ne_protected_conv(const void *c, int64_t ldc, int M, int64_t N,
 /* Workspace bytes ne_protected_conv needs for (M, N, K). Host-only. */
 size_t ne_protected_conv_ws_bytes(int M, int64_t N, int K);
 
+/* Largest N + K - 1 that ne_protected_conv_noalloc accepts. */
+#define NE_NOALLOC_MAX_NOUT 100663296LL /* 2^25 * 3 output samples */
+
+/*
+ * ne_protected_conv_noalloc -- ne_protected_conv for callers that cannot
+ * allocate device memory at call time (the paper has no counterpart: this
+ * is a property of the library, not of the method).  Examples: a library
+ * embedded in another framework whose allocator has already reserved the
+ * device's memory, or a call on a path where allocation is not permitted.
+ * Same arguments, results and errors as ne_protected_conv, minus the
+ * workspace: the per-tile arrival words live in a fixed array inside
+ * libne.so's own device memory, sized for N + K - 1 <= NE_NOALLOC_MAX_NOUT
+ * (512 KiB; every GPU that loads the library holds it until the process
+ * exits).  Larger jobs return NE_ERR_NOMEM before any launch.
+ *   - No cudaMalloc, cudaFree or other allocating call is made.  The array
+ *     keeps the last call's contents; each call clears the words it uses
+ *     (an asynchronous memset on `stream`) before its launch.
+ *   - All calls share the one array per device: calls whose launches can
+ *     overlap on the GPU (different streams, or different host threads)
+ *     race and give wrong results.  Order them on one stream.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ */
+int ne_protected_conv_noalloc(const void *c, int64_t ldc, int M, int64_t N,
+                              const int32_t *g, int K, int w, int l,
+                              int64_t c_min, int64_t c_max, int64_t max_abs_g,
+                              int failed, int fail_mode, void *d, int64_t ldd,
+                              void *stream);
+
 /*
  * ne_checksum -- checksum stream of the ABFT baseline (Eq. 3-4):
  *     r[n] = sum_m c_m[n]  (mod 2^w),  0 <= n < N.

@@ -586,3 +586,111 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free protected convolution.  Some callers cannot allocate
+// device memory when they call in: code embedded in another framework that
+// has already reserved the device's memory for its own allocator, or code on
+// a path where allocation is not permitted (a latency-critical loop or a
+// callback).  For them the per-tile arrival words live in a fixed array in
+// the library's own device memory, sized for NE_NOALLOC_MAX_NOUT output
+// samples per stream.  Every GPU that loads the library holds the array
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace ne {
+namespace {
+
+constexpr int64_t kNoallocTiles =
+    (NE_NOALLOC_MAX_NOUT + CONV_TILE - 1) / CONV_TILE;
+static __device__ __align__(256) uint32_t g_noalloc_arrivals[2 * kNoallocTiles];
+
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_ptr[64] = {};  // device address of the array, per device
+
+// Device address of the array on the current device.  The host-side name of
+// a __device__ array is not a device address, so it is looked up once per
+// device (with that device current) and cached.
+int noalloc_arrivals(uint32_t** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NE_ERR_CUDA;
+  if (dev < 0 || dev >= 64) return NE_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_arrivals) != cudaSuccess || !p)
+      return NE_ERR_CUDA;
+    g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return NE_OK;
+}
+
+}  // namespace
+}  // namespace ne
+
+extern "C" int ne_protected_conv_noalloc(const void* c, int64_t ldc, int M,
+                                         int64_t N, const int32_t* g, int K,
+                                         int w, int l, int64_t c_min,
+                                         int64_t c_max, int64_t max_abs_g,
+                                         int failed, int fail_mode, void* d,
+                                         int64_t ldd, void* stream) {
+  if (M < 3 || M > 32 || N < 0 || K < 1 || K > CONV_MAX_K || ldc < N ||
+      (w != 32 && w != 64) || l <= 0 || l >= w || (M - 1) * l > w ||
+      c_min > c_max || max_abs_g < 0)
+    return NE_ERR_INVALID_ARG;
+  if (fail_mode != NE_FAIL_NONE && fail_mode != NE_FAIL_SKIP &&
+      fail_mode != NE_FAIL_DROP)
+    return NE_ERR_INVALID_ARG;
+  if (fail_mode == NE_FAIL_NONE ? failed != -1 : (failed < 0 || failed >= M))
+    return NE_ERR_INVALID_ARG;
+  const unsigned __int128 abs_lo =
+      (unsigned __int128)(c_min < 0 ? -(__int128)c_min : (__int128)c_min);
+  const unsigned __int128 abs_hi =
+      (unsigned __int128)(c_max < 0 ? -(__int128)c_max : (__int128)c_max);
+  const unsigned __int128 max_abs_c = abs_lo > abs_hi ? abs_lo : abs_hi;
+  const unsigned __int128 need =
+      (unsigned __int128)K * max_abs_c * (unsigned __int128)max_abs_g;
+  if (need > exact_limit(M, w, l) ||
+      max_abs_c > (((unsigned __int128)1 << (w - 1)) - 1) /
+                      (((unsigned __int128)1 << l) + 1))
+    return NE_ERR_RANGE;
+  if (N == 0) return NE_OK;
+  const int64_t Nout = N + K - 1;
+  if (!c || !g || !d || ldd < Nout) return NE_ERR_INVALID_ARG;
+  // the fixed array covers NE_NOALLOC_MAX_NOUT output samples per stream
+  if (Nout > NE_NOALLOC_MAX_NOUT) return NE_ERR_NOMEM;
+  const int wb = w / 8;
+  if (overlaps(c, rows_bytes(M, ldc, N, wb), d, rows_bytes(M, ldd, Nout, wb)))
+    return NE_ERR_INVALID_ARG;
+  uint32_t* ws = nullptr;
+  const int st = noalloc_arrivals(&ws);
+  if (st != NE_OK) return st;
+  const int64_t ntiles = (Nout + CONV_TILE - 1) / CONV_TILE;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the array keeps the previous call's words: clear the ones this call uses
+  if (cudaMemsetAsync(ws, 0, (size_t)ntiles * 2 * sizeof(uint32_t), s) !=
+      cudaSuccess)
+    return NE_ERR_CUDA;
+  ConvArgs a{};
+  a.x = c;
+  a.ldx = ldc;
+  a.M = M;
+  a.N = N;
+  a.Nout = Nout;
+  a.ntiles = ntiles;
+  a.g = g;
+  a.K = K;
+  a.Kp = (K + CONV_KC - 1) / CONV_KC * CONV_KC;
+  a.y = d;
+  a.ldy = ldd;
+  a.live_mask = 0xffffffffu;
+  a.l = l;
+  a.failed = failed;
+  a.fail_mode = fail_mode;
+  a.ws = ws;
+  const __int128 f = ((__int128)1 << l) + 1;
+  const int mode = choose_mode(w, true, (__int128)c_min * f,
+                               (__int128)c_max * f, &a.bias);
+  const bool vec = rows_aligned16(c, ldc, wb);
+  return dispatch_conv<true>(a, w, mode, vec, s);
+}

@@ -83,6 +83,9 @@ _SIGS = {
                            _i64, _i64, _i32, _i32, _vp, _i64, _vp, _sz, _vp],
                           _i32),
     "ne_protected_conv_ws_bytes": ([_i32, _i64, _i32], _sz),
+    "ne_protected_conv_noalloc": ([_vp, _i64, _i32, _i64, _vp, _i32, _i32,
+                                   _i32, _i64, _i64, _i64, _i32, _i32, _vp,
+                                   _i64, _vp], _i32),
     "ne_checksum": ([_vp, _i64, _i32, _i64, _i32, _vp, _vp], _i32),
     "ne_checksum_recover": ([_vp, _i64, _vp, _i32, _i64, _i32, _i32, _vp, _vp],
                             _i32),
@@ -265,6 +268,29 @@ def ne_protected_conv(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
                                    ctypes.c_void_p(ws.data_ptr()),
                                    ws.numel() * ws.element_size(),
                                    _stream(stream)), "ne_protected_conv")
+    return d
+
+
+NE_NOALLOC_MAX_NOUT = 100663296
+
+
+def ne_protected_conv_noalloc(c: torch.Tensor, g: torch.Tensor,
+                              d: torch.Tensor, *, l: int,
+                              c_range: tuple[int, int], max_abs_g: int,
+                              failed: int = -1, fail_mode: int = NE_FAIL_NONE,
+                              N: int | None = None,
+                              stream=None) -> torch.Tensor:
+    """ne_protected_conv without a workspace argument, for callers that
+    cannot allocate device memory at call time: the arrival words live in a
+    fixed array inside libne.so (N + K - 1 <= NE_NOALLOC_MAX_NOUT).  Calls
+    share that array, so keep them ordered on one stream."""
+    pc, M, n, ldc = _rows(c, "c")
+    pd, _, _, ldd = _rows(d, "d")
+    n = n if N is None else N
+    _check(lib().ne_protected_conv_noalloc(
+        pc, ldc, M, n, ctypes.c_void_p(g.data_ptr()), g.numel(),
+        _word_bits(c), l, int(c_range[0]), int(c_range[1]), max_abs_g, failed,
+        fail_mode, pd, ldd, _stream(stream)), "ne_protected_conv_noalloc")
     return d
 
 
