@@ -227,6 +227,86 @@ int ne_protected_conv_noalloc(const void *c, int64_t ldc, int M, int64_t N,
                               int failed, int fail_mode, void *d, int64_t ldd,
                               void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched protected convolution: many independent jobs (uneven M, N, K,
+ * word width, failure) in one persistent launch.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  const void *c;      /* M rows of N raw input words (device), leading dim ldc */
+  int64_t ldc;
+  const int32_t *g;   /* K taps (device)                                     */
+  void *d;            /* M rows of N+K-1 output words (device), ldd          */
+  int64_t ldd;
+  int64_t N;          /* samples per input row (0: the job is skipped)       */
+  int32_t M;          /* streams, 3..32                                      */
+  int32_t K;          /* taps, 1..4096                                       */
+  int32_t w;          /* word width: 32 or 64                                */
+  int32_t l;          /* entanglement shift; 0 = the paper's rule (ne_params) */
+  int64_t c_min, c_max; /* declared input range                            */
+  int64_t max_abs_g;  /* declared bound on |g|                               */
+  int32_t failed;     /* fail-stopped stream, -1 with NE_FAIL_NONE           */
+  int32_t fail_mode;  /* ne_fail_mode                                        */
+} ne_job;
+
+/* Opaque batch context: owns the device job table, the work-unit prefix,
+ * the per-tile arrival words, the work counter, an optional captured graph
+ * and the tuning choices.  One context serves one stream at a time. */
+typedef struct ne_ctx ne_ctx;
+
+int ne_ctx_create(ne_ctx **out);          /* allocates a counter; NE_OK      */
+int ne_ctx_destroy(ne_ctx *ctx);          /* frees all context memory        */
+/* Index of the job that made the last ne_batch_prepare fail, or -1. */
+int ne_ctx_bad_job(const ne_ctx *ctx);
+
+/*
+ * ne_batch_prepare -- check and plan a batch (host, synchronous; grows the
+ * context's device workspace with cudaMalloc when needed).  Each job is
+ * checked exactly like ne_protected_conv (range, failure arguments,
+ * overlap); the first bad job makes the call return its status and
+ * ne_ctx_bad_job() name it.  Every job's result equals what
+ * ne_protected_conv would produce for it.  The job array may be freed after
+ * the call; the device buffers it names must stay valid until the launches
+ * that use them complete.
+ */
+int ne_batch_prepare(ne_ctx *ctx, const ne_job *jobs, int n_jobs);
+
+/*
+ * ne_batch_launch -- run the prepared batch: clears the arrival words and
+ * the work counter (asynchronous memsets) and makes one persistent launch,
+ * all on `stream`.  No host synchronisation, allocation or device-side
+ * waiting; capturable in a CUDA graph.  Returns NE_ERR_INVALID_ARG if the
+ * block size changed since the last prepare.
+ */
+int ne_batch_launch(ne_ctx *ctx, void *stream);
+
+/* ne_batch_prepare followed by ne_batch_launch. */
+int ne_batch_submit(ne_ctx *ctx, const ne_job *jobs, int n_jobs,
+                    void *stream);
+
+/* Launch configuration: threads per block (64, 128 or 256; the output tile
+ * is 12 x threads samples) and resident blocks per SM (0 = as many as fit).
+ * A new block size takes effect at the next ne_batch_prepare. */
+int ne_batch_set_config(ne_ctx *ctx, int threads, int blocks_per_sm);
+
+/* Capture ne_batch_launch of the prepared batch into a CUDA graph owned by
+ * the context (replaced on the next prepare or capture), and launch it. */
+int ne_batch_graph_capture(ne_ctx *ctx);
+int ne_batch_graph_launch(ne_ctx *ctx, void *stream);
+
+/*
+ * ne_batch_autotune -- time every block size (64/128/256) with several
+ * blocks-per-SM settings on this batch (`reps` timed launches each, after a
+ * warm-up, CUDA events on `stream`; blocks the host), keep the fastest for
+ * batches of the same shape (and in the tuning file, if one is set), and
+ * leave the batch prepared with it.  Outputs are overwritten by the trial
+ * launches (they end with the correct results).
+ */
+int ne_batch_autotune(ne_ctx *ctx, const ne_job *jobs, int n_jobs, int reps,
+                      void *stream, int *threads, int *blocks_per_sm,
+                      float *ms);
+/* Tuning cache file (text; read now, rewritten after each autotune). */
+int ne_batch_set_tune_file(ne_ctx *ctx, const char *path);
+
 /*
  * ne_checksum -- checksum stream of the ABFT baseline (Eq. 3-4):
  *     r[n] = sum_m c_m[n]  (mod 2^w),  0 <= n < N.

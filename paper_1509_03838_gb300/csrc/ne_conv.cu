@@ -105,9 +105,9 @@ __device__ __forceinline__ void stage_from_global(const W* __restrict__ row,
 // (Kp int64).
 __host__ __device__ constexpr size_t operand_bytes(int Kp, int mode, int wb) {
   return (((size_t)(CONV_TILE + Kp) * (mode == MODE_SPLIT ? 2 : 1) * 4 >
-                   (size_t)out_stage_words() * wb
+                   (size_t)out_stage_words<CONV_THREADS>() * wb
                ? (size_t)(CONV_TILE + Kp) * (mode == MODE_SPLIT ? 2 : 1) * 4
-               : (size_t)out_stage_words() * wb) +
+               : (size_t)out_stage_words<CONV_THREADS>() * wb) +
           15) / 16 * 16;
 }
 __host__ __device__ constexpr size_t simple_smem_bytes(int Kp, int mode,

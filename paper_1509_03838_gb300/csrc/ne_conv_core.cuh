@@ -2,8 +2,9 @@
 // full linear convolution) shared by the single-job kernels (ne_conv.cu)
 // and the persistent batch kernel (ne_batch.cu).
 //
-// Tile geometry: one output tile = CONV_TILE = CONV_THREADS x CONV_R outputs
-// of one stream.  Its input window is x[n0 - Kp, n0 + CONV_TILE) (Kp = K
+// Tile geometry: one output tile = T threads x CONV_R outputs of one stream
+// (T = CONV_THREADS for the single-job kernels; the batch kernel also
+// instantiates other block sizes).  Its input window is x[n0 - Kp, n0 + CONV_TILE) (Kp = K
 // rounded up to CONV_KC, zero outside [0, N)), held in shared memory as the
 // 32-bit operands the multiply-adds consume.
 //
@@ -132,12 +133,13 @@ __device__ __forceinline__ W combine(unsigned long long a64, unsigned a32) {
 // bank conflicts.  s_out holds out_stage_words() words and may alias operand
 // buffers the block has finished reading.  Contains block barriers: every
 // thread must call it.
+template <int T = CONV_THREADS>
 __host__ __device__ constexpr int out_stage_words() {
-  return CONV_TILE + CONV_TILE / 16;
+  return T * CONV_R + T * CONV_R / 16;
 }
 __device__ __forceinline__ int out_slot(int j) { return j + (j >> 4); }
 
-template <typename W>
+template <typename W, int T = CONV_THREADS>
 __device__ __forceinline__ void write_tile(W* __restrict__ yrow, int64_t n0,
                                            int64_t Nout,
                                            const W (&out)[CONV_R],
@@ -147,8 +149,8 @@ __device__ __forceinline__ void write_tile(W* __restrict__ yrow, int64_t n0,
   for (int a = 0; a < CONV_R; ++a)
     s_out[out_slot(threadIdx.x * CONV_R + a)] = out[a];
   __syncthreads();
-  const int nvalid = (int)lmin((int64_t)CONV_TILE, Nout - n0);
-  for (int j = threadIdx.x; j < nvalid; j += CONV_THREADS)
+  const int nvalid = (int)lmin((int64_t)T * CONV_R, Nout - n0);
+  for (int j = threadIdx.x; j < nvalid; j += T)
     yrow[n0 + j] = s_out[out_slot(j)];
 }
 
@@ -157,12 +159,13 @@ __device__ __forceinline__ void write_tile(W* __restrict__ yrow, int64_t n0,
 // the conv of x by b*G(n), G(n) = sum of g[t] over the taps t that meet the
 // input at output n: 0 <= n - t < N.  tap_prefix() fills s_pref[t] =
 // g[0] + ... + g[t] (64-bit) with a block-wide scan; every thread must call
-// it.  s_warp holds CONV_THREADS/32 words of scratch.
+// it.  s_warp holds T/32 words of scratch.
 // ---------------------------------------------------------------------------
+template <int T = CONV_THREADS>
 __device__ __forceinline__ void tap_prefix(const int* __restrict__ s_taps,
                                            int K, long long* __restrict__ s_pref,
                                            long long* __restrict__ s_warp) {
-  const int chunk = (K + CONV_THREADS - 1) / CONV_THREADS;
+  const int chunk = (K + T - 1) / T;
   const int t0 = min(K, (int)threadIdx.x * chunk);
   const int t1 = min(K, t0 + chunk);
   long long loc = 0;
@@ -179,7 +182,7 @@ __device__ __forceinline__ void tap_prefix(const int* __restrict__ s_taps,
   __syncthreads();
   if (threadIdx.x == 0) {
     long long run = 0;
-    for (int w = 0; w < CONV_THREADS / 32; ++w) {
+    for (int w = 0; w < T / 32; ++w) {
       const long long v = s_warp[w];
       s_warp[w] = run;
       run += v;
@@ -194,19 +197,20 @@ __device__ __forceinline__ void tap_prefix(const int* __restrict__ s_taps,
   __syncthreads();
 }
 
-// Sum of all K taps (every thread gets it); s_warp: CONV_THREADS/32 words.
+// Sum of all K taps (every thread gets it); s_warp: T/32 words.
+template <int T = CONV_THREADS>
 __device__ __forceinline__ long long tap_total(const int* __restrict__ s_taps,
                                                int K,
                                                long long* __restrict__ s_warp) {
   long long v = 0;
-  for (int t = threadIdx.x; t < K; t += CONV_THREADS) v += s_taps[t];
+  for (int t = threadIdx.x; t < K; t += T) v += s_taps[t];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
   __syncthreads();
   long long tot = 0;
 #pragma unroll
-  for (int w = 0; w < CONV_THREADS / 32; ++w) tot += s_warp[w];
+  for (int w = 0; w < T / 32; ++w) tot += s_warp[w];
   __syncthreads();
   return tot;
 }
@@ -233,7 +237,7 @@ __device__ __forceinline__ unsigned long long shift_correction(
 // thread of the block (it contains block barriers).
 // ---------------------------------------------------------------------------
 // Extract the tile's `span` columns from n0 in place, failed stream r.
-template <typename W, int NV, int MAXC>
+template <typename W, int NV, int MAXC, int T = CONV_THREADS>
 __device__ __forceinline__ void extract_tile(W* ybase, int64_t ldy, int M,
                                              int r, int64_t n0, int span,
                                              int l) {
@@ -246,12 +250,11 @@ __device__ __forceinline__ void extract_tile(W* ybase, int64_t ldy, int M,
   }
   W* row_r = ybase + (int64_t)r * ldy + n0;
 #pragma unroll 1
-  for (int n = threadIdx.x; n < span; n += CONV_THREADS * NV)
-    recover_columns_batched<W, NV, MAXC>(rows, row_r, M, n, CONV_THREADS, span,
-                                         l);
+  for (int n = threadIdx.x; n < span; n += T * NV)
+    recover_columns_batched<W, NV, MAXC>(rows, row_r, M, n, T, span, l);
 }
 
-template <typename W>
+template <typename W, int T = CONV_THREADS>
 __device__ __forceinline__ void protected_epilogue(
     W* __restrict__ ybase, int64_t ldy, int M, int m, int64_t tile, int64_t n0,
     int64_t Nout, int l, uint32_t* ws, const W (&out)[CONV_R], W* s_out,
@@ -263,7 +266,7 @@ __device__ __forceinline__ void protected_epilogue(
   const bool publish = *s_flag < M - 1;
   __syncthreads();
   if (!publish) return;
-  write_tile<W>(ybase + (int64_t)m * ldy, n0, Nout, out, s_out);
+  write_tile<W, T>(ybase + (int64_t)m * ldy, n0, Nout, out, s_out);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -277,16 +280,16 @@ __device__ __forceinline__ void protected_epilogue(
   __threadfence();
   const uint32_t full = M >= 32 ? 0xffffffffu : ((1u << M) - 1u);
   const int r = __ffs((int)(~(uint32_t)mask & full)) - 1;
-  const int64_t end = min(n0 + (int64_t)CONV_TILE, Nout);
-  // thread t owns columns n0 + t + CONV_THREADS i: every warp access is one
+  const int64_t end = min(n0 + (int64_t)T * CONV_R, Nout);
+  // thread t owns columns n0 + t + T i: every warp access is one
   // contiguous segment; all M-1 rows of NV columns are in flight at once
   const int span = (int)(end - n0);
   if (M <= 4) {
-    extract_tile<W, 4, 3>(ybase, ldy, M, r, n0, span, l);
+    extract_tile<W, 4, 3, T>(ybase, ldy, M, r, n0, span, l);
   } else if (M <= 9) {
-    extract_tile<W, 2, 8>(ybase, ldy, M, r, n0, span, l);
+    extract_tile<W, 2, 8, T>(ybase, ldy, M, r, n0, span, l);
   } else {
-    for (int64_t n = n0 + threadIdx.x; n < end; n += CONV_THREADS)
+    for (int64_t n = n0 + threadIdx.x; n < end; n += T)
       recover_columns<W, 0, 1, true>(ybase, ldy, M, n, l, r, ybase, ldy);
   }
 }

@@ -97,6 +97,34 @@ _SIGS = {
     "ne_probe_imad_rate": ([_i32, _i32, ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double)], _i32),
 }
+
+
+class NeJob(ctypes.Structure):
+    """C layout of ne_job (include/ne.h)."""
+    _fields_ = [("c", _vp), ("ldc", _i64), ("g", _vp), ("d", _vp),
+                ("ldd", _i64), ("N", _i64), ("M", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("l", ctypes.c_int32), ("c_min", _i64), ("c_max", _i64),
+                ("max_abs_g", _i64), ("failed", ctypes.c_int32),
+                ("fail_mode", ctypes.c_int32)]
+
+
+_ctxp = ctypes.c_void_p
+_SIGS.update({
+    "ne_ctx_create": ([ctypes.POINTER(_ctxp)], _i32),
+    "ne_ctx_destroy": ([_ctxp], _i32),
+    "ne_ctx_bad_job": ([_ctxp], _i32),
+    "ne_batch_prepare": ([_ctxp, ctypes.POINTER(NeJob), _i32], _i32),
+    "ne_batch_launch": ([_ctxp, _vp], _i32),
+    "ne_batch_submit": ([_ctxp, ctypes.POINTER(NeJob), _i32, _vp], _i32),
+    "ne_batch_set_config": ([_ctxp, _i32, _i32], _i32),
+    "ne_batch_graph_capture": ([_ctxp], _i32),
+    "ne_batch_graph_launch": ([_ctxp, _vp], _i32),
+    "ne_batch_autotune": ([_ctxp, ctypes.POINTER(NeJob), _i32, _i32, _vp,
+                           ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                           ctypes.POINTER(ctypes.c_float)], _i32),
+    "ne_batch_set_tune_file": ([_ctxp, ctypes.c_char_p], _i32),
+})
 # optional entry points added by later modules register here
 EXTRA_SIGS: dict = {}
 
@@ -366,3 +394,84 @@ def ne_probe_imad_rate(kind: int, iters: int = 4096):
     _check(lib().ne_probe_imad_rate(kind, iters, ctypes.byref(rate),
                                     ctypes.byref(ms)), "ne_probe_imad_rate")
     return rate.value, ms.value
+
+
+# ---------------------------------------------------------------------------
+# batched protected convolution
+# ---------------------------------------------------------------------------
+
+def make_job(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
+             c_range: tuple[int, int], max_abs_g: int, failed: int = -1,
+             fail_mode: int = NE_FAIL_NONE, l: int = 0) -> NeJob:
+    """An ne_job for c [M, N] -> d [M, N+K-1] (tensors stay owned by the
+    caller and must outlive the launches that use them)."""
+    pc, M, n, ldc = _rows(c, "c")
+    pd, _, _, ldd = _rows(d, "d")
+    return NeJob(pc.value, ldc, g.data_ptr(), pd.value, ldd, n, M, g.numel(),
+                 _word_bits(c), l, int(c_range[0]), int(c_range[1]),
+                 int(max_abs_g), failed, fail_mode)
+
+
+class Batch:
+    """Owns an ne_ctx: prepare a job list once, launch it many times (also
+    through a captured CUDA graph), autotune its launch configuration."""
+
+    def __init__(self, tune_file: str | None = None):
+        self._ctx = _ctxp()
+        _check(lib().ne_ctx_create(ctypes.byref(self._ctx)), "ne_ctx_create")
+        self._jobs = None
+        if tune_file:
+            _check(lib().ne_batch_set_tune_file(self._ctx, tune_file.encode()),
+                   "ne_batch_set_tune_file")
+
+    def close(self):
+        if self._ctx:
+            lib().ne_ctx_destroy(self._ctx)
+            self._ctx = _ctxp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _array(self, jobs):
+        arr = (NeJob * len(jobs))(*jobs)
+        self._jobs = arr
+        return arr
+
+    def prepare(self, jobs) -> None:
+        arr = self._array(jobs)
+        st = lib().ne_batch_prepare(self._ctx, arr, len(jobs))
+        if st != NE_OK:
+            raise NEError(st, f"ne_batch_prepare (job {lib().ne_ctx_bad_job(self._ctx)})")
+
+    def launch(self, stream=None) -> None:
+        _check(lib().ne_batch_launch(self._ctx, _stream(stream)),
+               "ne_batch_launch")
+
+    def submit(self, jobs, stream=None) -> None:
+        arr = self._array(jobs)
+        st = lib().ne_batch_submit(self._ctx, arr, len(jobs), _stream(stream))
+        if st != NE_OK:
+            raise NEError(st, f"ne_batch_submit (job {lib().ne_ctx_bad_job(self._ctx)})")
+
+    def set_config(self, threads: int, blocks_per_sm: int = 0) -> None:
+        _check(lib().ne_batch_set_config(self._ctx, threads, blocks_per_sm),
+               "ne_batch_set_config")
+
+    def capture_graph(self) -> None:
+        _check(lib().ne_batch_graph_capture(self._ctx), "ne_batch_graph_capture")
+
+    def launch_graph(self, stream=None) -> None:
+        _check(lib().ne_batch_graph_launch(self._ctx, _stream(stream)),
+               "ne_batch_graph_launch")
+
+    def autotune(self, jobs, reps: int = 2, stream=None):
+        arr = self._array(jobs)
+        t, b, ms = _i32(), _i32(), ctypes.c_float()
+        _check(lib().ne_batch_autotune(self._ctx, arr, len(jobs), reps,
+                                       _stream(stream), ctypes.byref(t),
+                                       ctypes.byref(b), ctypes.byref(ms)),
+               "ne_batch_autotune")
+        return t.value, b.value, ms.value
