@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ne", "reference"], default="ne")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU oracle sample")
     return ap.parse_args()
@@ -424,6 +426,9 @@ def run_ne(args):
     e2e_val = world * ops_job * args.steps / (t_e2e * 1e-3) / 1e9
 
     clk = clocks.summary(t_start, t_end)
+    del c_h, d_h, g_h
+    batch = None if args.no_batch else bench_batch(ne, synth, dev, stream)
+    served = None if args.no_serve else bench_serve(dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(args.cpu_seconds)
@@ -448,10 +453,100 @@ def run_ne(args):
                     "d2h_bytes_per_step": d.numel() * 8},
             "gpu_launches": args.steps,
             "clocks": clk,
-            "p99_ms_served": None,
+            "batch": batch,
+            "serve": served,
+            "p99_ms_served": served["p99_ms"] if served else None,
         }
         print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_batch(ne, synth, dev, stream):
+    """4096 independent protected jobs (M in {3..8}, N log-uniform in
+    [2^10, 2^18], K in {8..256}, 16-bit data and taps, 64-bit words, one
+    failed stream each): one autotuned persistent launch replayed from a
+    captured CUDA graph, vs one ne_protected_conv launch per job.  Inputs
+    are drawn on the device from a seeded generator (same shapes as the
+    parity test's host-drawn inputs)."""
+    import torch
+    spec = synth.batch_spec(seed=3)
+    n = len(spec)
+    M, N, K = spec.M, spec.N, spec.K
+    cw = int((M * N).sum())
+    dw = int((M * (N + K - 1)).sum())
+    gw = int(K.sum())
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+    cbuf = torch.empty(cw, dtype=torch.int64, device=dev).random_(
+        -(1 << 15), 1 << 15, generator=gen)
+    gbuf = torch.empty(gw, dtype=torch.int32, device=dev).random_(
+        -(1 << 15), 1 << 15, generator=gen)
+    dbuf = torch.empty(dw, dtype=torch.int64, device=dev)
+    views, jobs = [], []
+    co = go = do = 0
+    for i in range(n):
+        m, nn, k = int(M[i]), int(N[i]), int(K[i])
+        c = cbuf[co:co + m * nn].view(m, nn)
+        g = gbuf[go:go + k]
+        d = dbuf[do:do + m * (nn + k - 1)].view(m, nn + k - 1)
+        co += m * nn
+        go += k
+        do += m * (nn + k - 1)
+        f = int(spec.failed[i])
+        views.append((c, g, d, f))
+        jobs.append(ne.make_job(c, g, d, c_range=(-(1 << 15), (1 << 15) - 1),
+                                max_abs_g=1 << 15, failed=f,
+                                fail_mode=ne.NE_FAIL_DROP))
+    macs = float((M * N * K).sum())
+    b = ne.Batch()
+    threads, bps, _ = b.autotune(jobs, reps=1)
+    b.capture_graph()
+    b.launch_graph()
+    reps = 5
+    t_graph, _ = timed(lambda i: b.launch_graph(), reps, 1, stream)
+    ms_batch = t_graph / reps
+    ws = torch.empty(max(ne.ne_protected_conv_ws_bytes(int(M[i]), int(N[i]),
+                                                       int(K[i]))
+                         for i in range(n)), dtype=torch.uint8, device=dev)
+
+    def per_job(_):
+        for c, g, d, f in views:
+            ne.ne_protected_conv(c, g, d, l=ne.ne_params(c.shape[0], 64).l,
+                                 c_range=(-(1 << 15), (1 << 15) - 1),
+                                 max_abs_g=1 << 15, failed=f,
+                                 fail_mode=ne.NE_FAIL_DROP, ws=ws)
+    per_job(0)
+    t_loop, _ = timed(per_job, 2, 1, stream)
+    ms_loop = t_loop / 2
+    b.close()
+    del cbuf, dbuf, gbuf, views, jobs
+    return {"workload": "4096 jobs, M in {3..8}, N log-uniform [2^10,2^18], "
+                        "K in {8..256}, 16-bit data/taps, 64-bit words, one "
+                        "failed stream per job",
+            "macs": macs, "ms_graph_launch": ms_batch,
+            "gops_batched": 2 * macs / (ms_batch * 1e-3) / 1e9,
+            "ms_one_launch_per_job": ms_loop,
+            "gops_one_launch_per_job": 2 * macs / (ms_loop * 1e-3) / 1e9,
+            "speedup_vs_one_launch_per_job": ms_loop / ms_batch,
+            "tuned": {"threads": threads, "blocks_per_sm": bps}}
+
+
+def bench_serve(dev, n_jobs=6000):
+    """Poisson arrivals at 20k jobs/s of protected convolutions (M in
+    {3..6}, N log-uniform [2^12, 2^20], K in {16..512}, 16-bit data, 10 %
+    with an injected fail-stop) through the continuous-batching loop."""
+    from paper_1509_03838_gb300 import serve, synth
+    spec = synth.serve_spec(seed=5, n_jobs=n_jobs)
+    warm = synth.serve_spec(seed=6, n_jobs=300)
+    serve.serve(warm, budget_bytes=8 << 30, streams=3, seed=1, device=dev)
+    r = serve.serve(spec, budget_bytes=8 << 30, streams=3, seed=2, device=dev)
+    return {"workload": f"{n_jobs} jobs, Poisson 20k jobs/s, M in {{3..6}}, N "
+                        "log-uniform [2^12,2^20], K in {16..512}, 16-bit "
+                        "data, 10% injected single-stream fail-stop",
+            "p50_ms": r.p50_ms, "p99_ms": r.p99_ms,
+            "jobs_per_s": r.jobs_per_s, "gops": r.gops, "batches": r.batches,
+            "peak_device_bytes": r.peak_bytes, "budget_bytes": r.budget_bytes,
+            "offered_jobs_per_s": 20000.0}
 
 
 def main():

@@ -246,6 +246,11 @@ typedef struct {
   int64_t max_abs_g;  /* declared bound on |g|                               */
   int32_t failed;     /* fail-stopped stream, -1 with NE_FAIL_NONE           */
   int32_t fail_mode;  /* ne_fail_mode                                        */
+  int32_t entangled;  /* 0: c holds the raw inputs (entangled on load);      */
+                      /* 1: c already holds eps (ne_entangle in place), the  */
+                      /*    paper's in-place storage; c_range still names    */
+                      /*    the raw inputs' range                            */
+  int32_t reserved;   /* must be 0                                           */
 } ne_job;
 
 /* Opaque batch context: owns the device job table, the work-unit prefix,
@@ -259,8 +264,12 @@ int ne_ctx_destroy(ne_ctx *ctx);          /* frees all context memory        */
 int ne_ctx_bad_job(const ne_ctx *ctx);
 
 /*
- * ne_batch_prepare -- check and plan a batch (host, synchronous; grows the
- * context's device workspace with cudaMalloc when needed).  Each job is
+ * ne_batch_prepare -- check and plan a batch on the host (grows the
+ * context's device workspace with cudaMalloc and its pinned staging with
+ * cudaMallocHost only when the batch is larger than any before; otherwise
+ * no CUDA call).  The job table is staged in pinned host memory and copied
+ * by the next ne_batch_launch, so a context must not be prepared again
+ * while a launch of it may still be reading that staging (wait for it).  Each job is
  * checked exactly like ne_protected_conv (range, failure arguments,
  * overlap); the first bad job makes the call return its status and
  * ne_ctx_bad_job() name it.  Every job's result equals what
@@ -271,9 +280,10 @@ int ne_ctx_bad_job(const ne_ctx *ctx);
 int ne_batch_prepare(ne_ctx *ctx, const ne_job *jobs, int n_jobs);
 
 /*
- * ne_batch_launch -- run the prepared batch: clears the arrival words and
- * the work counter (asynchronous memsets) and makes one persistent launch,
- * all on `stream`.  No host synchronisation, allocation or device-side
+ * ne_batch_launch -- run the prepared batch: copies the job table from the
+ * pinned staging, clears the arrival words and the work counter
+ * (asynchronous copies and memsets) and makes one persistent launch, all on
+ * `stream`.  No host synchronisation, allocation or device-side
  * waiting; capturable in a CUDA graph.  Returns NE_ERR_INVALID_ARG if the
  * block size changed since the last prepare.
  */

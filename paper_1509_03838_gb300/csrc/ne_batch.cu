@@ -50,7 +50,7 @@ struct JobDev {
   int64_t ldc, ldd, N, Nout;
   long long bias;   // MODE_WIDE range shift
   int64_t tile0;    // first arrival-word tile of this job
-  int32_t M, K, Kp, l, mode, failed, fail_mode, ntiles;
+  int32_t M, K, Kp, l, mode, failed, fail_mode, ntiles, entangled, pad;
 };
 
 struct BatchArgs {
@@ -106,9 +106,12 @@ __device__ __noinline__ void batch_unit(const JobDev& jb, int64_t local,
   for (int j = threadIdx.x; j < TILE + Kp; j += T) {
     const int64_t gi = n0 - Kp + j;
     W v = 0;
-    if (gi >= 0 && gi < jb.N)
-      v = wsub<W>(wadd<W>(__ldg(row + gi), shl<W>(__ldg(prow + gi), jb.l)),
-                  bias);
+    if (gi >= 0 && gi < jb.N) {
+      const W x = jb.entangled
+                      ? __ldg(row + gi)
+                      : wadd<W>(__ldg(row + gi), shl<W>(__ldg(prow + gi), jb.l));
+      v = wsub<W>(x, bias);
+    }
     int a, b;
     split_word<W, MODE>(v, a, b);
     s_lo[j] = a;
@@ -246,6 +249,8 @@ constexpr int kBatchMaxK = 4096;
 }  // namespace
 }  // namespace ne
 
+using JobDevHost = ne::JobDev;
+
 struct ne_ctx {
   // prepared batch
   std::vector<ne::JobDev> jobs;
@@ -263,6 +268,11 @@ struct ne_ctx {
   uint32_t* d_arrivals = nullptr;
   size_t cap_arrivals = 0;  // words
   unsigned long long* d_counter = nullptr;
+  // pinned host staging of the job table and unit prefix (copied by launch)
+  JobDevHost* h_jobs = nullptr;
+  size_t cap_h_jobs = 0;
+  int64_t* h_unit0 = nullptr;
+  size_t cap_h_unit0 = 0;
   // launch configuration (0 = automatic)
   int threads = 128;
   int planned_threads = 0;  // block size the prepared tiling was made for
@@ -279,6 +289,17 @@ struct ne_ctx {
 
 namespace ne {
 namespace {
+
+int grow_pinned(void** p, size_t* cap, size_t need, size_t elem) {
+  if (need <= *cap && *p) return NE_OK;
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  const size_t n = std::max<size_t>(need, 1);
+  if (cudaMallocHost(p, n * elem) != cudaSuccess) return NE_ERR_NOMEM;
+  *cap = n;
+  return NE_OK;
+}
 
 int grow(void** p, size_t* cap, size_t need, size_t elem) {
   if (need <= *cap && *p) return NE_OK;
@@ -327,6 +348,13 @@ int launch_batch(ne_ctx* ctx, cudaStream_t s) {
   if (ctx->n_jobs == 0 || ctx->total_units == 0) return NE_OK;
   // the tiling was planned for another block size: prepare again first
   if (ctx->planned_threads != ctx->threads) return NE_ERR_INVALID_ARG;
+  if (cudaMemcpyAsync(ctx->d_jobs, ctx->h_jobs,
+                      (size_t)ctx->n_jobs * sizeof(JobDev),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(ctx->d_unit0, ctx->h_unit0,
+                      ((size_t)ctx->n_jobs + 1) * sizeof(int64_t),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return NE_ERR_CUDA;
   if (cudaMemsetAsync(ctx->d_arrivals, 0,
                       (size_t)ctx->total_tiles * 2 * sizeof(uint32_t), s) !=
           cudaSuccess ||
@@ -393,6 +421,8 @@ int ne_ctx_destroy(ne_ctx* ctx) {
   cudaFree(ctx->d_unit0);
   cudaFree(ctx->d_arrivals);
   cudaFree(ctx->d_counter);
+  cudaFreeHost(ctx->h_jobs);
+  cudaFreeHost(ctx->h_unit0);
   delete ctx;
   return NE_OK;
 }
@@ -413,8 +443,9 @@ int ne_batch_prepare(ne_ctx* ctx, const ne_job* jobs, int n_jobs) {
       ctx->bad_job = i;
       return NE_ERR_INVALID_ARG;
     }
-    if (J.fail_mode != NE_FAIL_NONE && J.fail_mode != NE_FAIL_SKIP &&
-        J.fail_mode != NE_FAIL_DROP) {
+    if ((J.fail_mode != NE_FAIL_NONE && J.fail_mode != NE_FAIL_SKIP &&
+         J.fail_mode != NE_FAIL_DROP) ||
+        (J.entangled != 0 && J.entangled != 1) || J.reserved != 0) {
       ctx->bad_job = i;
       return NE_ERR_INVALID_ARG;
     }
@@ -495,6 +526,7 @@ int ne_batch_prepare(ne_ctx* ctx, const ne_job* jobs, int n_jobs) {
                           &jd.bias);
     jd.failed = J.failed;
     jd.fail_mode = J.fail_mode;
+    jd.entangled = J.entangled;
     ctx->jobs.push_back(jd);
     ctx->Kp_max = std::max(ctx->Kp_max, jd.Kp);
     mix((uint64_t)J.M);
@@ -526,13 +558,16 @@ int ne_batch_prepare(ne_ctx* ctx, const ne_job* jobs, int n_jobs) {
   if (st == NE_OK)
     st = grow((void**)&ctx->d_arrivals, &ctx->cap_arrivals,
               (size_t)tiles * 2, sizeof(uint32_t));
+  if (st == NE_OK)
+    st = grow_pinned((void**)&ctx->h_jobs, &ctx->cap_h_jobs, ctx->jobs.size(),
+                     sizeof(JobDev));
+  if (st == NE_OK)
+    st = grow_pinned((void**)&ctx->h_unit0, &ctx->cap_h_unit0,
+                     ctx->unit0.size(), sizeof(int64_t));
   if (st != NE_OK) return st;
-  if (cudaMemcpy(ctx->d_jobs, ctx->jobs.data(), ctx->jobs.size() * sizeof(JobDev),
-                 cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(ctx->d_unit0, ctx->unit0.data(),
-                 ctx->unit0.size() * sizeof(int64_t),
-                 cudaMemcpyHostToDevice) != cudaSuccess)
-    return NE_ERR_CUDA;
+  std::memcpy(ctx->h_jobs, ctx->jobs.data(), ctx->jobs.size() * sizeof(JobDev));
+  std::memcpy(ctx->h_unit0, ctx->unit0.data(),
+              ctx->unit0.size() * sizeof(int64_t));
   auto it = ctx->tuned.find(sig);
   if (it != ctx->tuned.end() && it->second.first != ctx->threads) {
     // a tuned block size changes the tiling: re-plan once with it

@@ -106,7 +106,8 @@ class NeJob(ctypes.Structure):
                 ("K", ctypes.c_int32), ("w", ctypes.c_int32),
                 ("l", ctypes.c_int32), ("c_min", _i64), ("c_max", _i64),
                 ("max_abs_g", _i64), ("failed", ctypes.c_int32),
-                ("fail_mode", ctypes.c_int32)]
+                ("fail_mode", ctypes.c_int32), ("entangled", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _ctxp = ctypes.c_void_p
@@ -402,14 +403,16 @@ def ne_probe_imad_rate(kind: int, iters: int = 4096):
 
 def make_job(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
              c_range: tuple[int, int], max_abs_g: int, failed: int = -1,
-             fail_mode: int = NE_FAIL_NONE, l: int = 0) -> NeJob:
+             fail_mode: int = NE_FAIL_NONE, l: int = 0,
+             entangled: bool = False) -> NeJob:
     """An ne_job for c [M, N] -> d [M, N+K-1] (tensors stay owned by the
-    caller and must outlive the launches that use them)."""
+    caller and must outlive the launches that use them).  entangled: c
+    already holds the entangled streams (ne_entangle in place)."""
     pc, M, n, ldc = _rows(c, "c")
     pd, _, _, ldd = _rows(d, "d")
     return NeJob(pc.value, ldc, g.data_ptr(), pd.value, ldd, n, M, g.numel(),
                  _word_bits(c), l, int(c_range[0]), int(c_range[1]),
-                 int(max_abs_g), failed, fail_mode)
+                 int(max_abs_g), failed, fail_mode, int(entangled), 0)
 
 
 class Batch:
