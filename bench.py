@@ -396,10 +396,14 @@ def run_ne(args):
     achieved = macs * per_mac / (prot_ms * 1e-3) / 1e12
     peak = (probe["imad_wide"] if per_mac == 1.0
             else probe["wide_plus_imad32"]) / 1e12
+    traffic = (TRAFFIC_CAPTURE["bytes"]
+               if TRAFFIC_CAPTURE["sources_sha256"] == conv_sources_sha()
+               else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "T 32x32->64 multiply-add instr/s" if per_mac == 1.0
                         else "T multiply-add instr/s (wide + 32-bit pairs)",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes": float((M * N + M * Nout) * 8),
                 "kernel": "conv_persistent_kernel<int64, MODE_WIDE, PROT> "
                           "(fused entangle + conv + extraction)",
                 "peak_source": "measured on this GPU by ne_probe_imad_rate "
@@ -427,6 +431,7 @@ def run_ne(args):
 
     clk = clocks.summary(t_start, t_end)
     del c_h, d_h, g_h
+    small = bench_small(ne, synth, dev, stream)
     batch = None if args.no_batch else bench_batch(ne, synth, dev, stream)
     served = None if args.no_serve else bench_serve(dev)
     cpu = None
@@ -453,12 +458,55 @@ def run_ne(args):
                     "d2h_bytes_per_step": d.numel() * 8},
             "gpu_launches": args.steps,
             "clocks": clk,
+            "small": small,
             "batch": batch,
             "serve": served,
             "p99_ms_served": served["p99_ms"] if served else None,
         }
         print(json.dumps(line), flush=True)
     return 0
+
+
+# DRAM traffic of one launch of the fused kernel on this workload, from an
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for
+# the kernel sources it was taken on (their SHA-256 is checked at run time).
+TRAFFIC_CAPTURE = {"sources_sha256": None, "bytes": None}
+CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_recover.cuh",
+                "ne_common.cuh"]
+
+
+def conv_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    base = os.path.join(ROOT, "paper_1509_03838_gb300", "csrc")
+    for name in CONV_SOURCES:
+        with open(os.path.join(base, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def bench_small(ne, synth, dev, stream, reps=200):
+    """M=3 int32 streams, N=4096, K=16 (32-bit words): launch-latency bound;
+    microseconds per protected job through the fused call."""
+    import torch
+    j = synth.small_job(seed=1)
+    p = ne.ne_choose_width(j.M, j.K, j.bound_c, j.bound_g)
+    c = torch.from_numpy(j.c.astype(np.int32)).to(dev)
+    g = torch.from_numpy(j.g.astype(np.int32)).to(dev)
+    d = torch.empty((j.M, j.N + j.K - 1), dtype=torch.int32, device=dev)
+    ws = torch.empty(ne.ne_protected_conv_ws_bytes(j.M, j.N, j.K),
+                     dtype=torch.uint8, device=dev)
+
+    def one(i):
+        ne.ne_protected_conv(c, g, d, l=p.l, c_range=j.c_range,
+                             max_abs_g=j.bound_g, failed=i % j.M,
+                             fail_mode=ne.NE_FAIL_DROP, ws=ws)
+    for i in range(10):
+        one(i)
+    t, _ = timed(one, reps, 1, stream)
+    return {"workload": "M=3 int32 streams, N=4096, K=16, data/taps in "
+                        "[-2^7,2^7), w=32 (l=11, k=10)",
+            "us_per_job": 1e3 * t / reps, "w": p.w}
 
 
 def bench_batch(ne, synth, dev, stream):

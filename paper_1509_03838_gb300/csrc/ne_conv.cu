@@ -17,6 +17,8 @@
 //     staged through registers.
 // The integer multiply-add pipe bounds both; tensor cores are not used
 // (integer stencil work, not a dense contraction).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -346,6 +348,178 @@ conv_persistent_kernel(const ConvArgs p) {
 }
 
 // ---------------------------------------------------------------------------
+// Cluster form of the fused protected convolution (M <= 8).  The M streams
+// of one output tile are the M blocks of one thread-block cluster, each an
+// independent unit of work: it entangles on load and convolves its stream.
+// The M-1 streams other than r (the failed one, or M-1 with no failure)
+// deliver: each block pushes every value of its entangled output tile
+// delta_m straight into the shared memory of the block that will extract
+// that column (distributed-shared-memory stores; the tile's columns are
+// split evenly among the M-1 delivering blocks).  After one cluster barrier
+// each delivering block recovers all M outputs of its columns from its own
+// shared memory and stores d.  No global round trip of delta, no atomics,
+// no remote reads.  A stream that fail-stopped before starting
+// (NE_FAIL_SKIP) computes nothing but meets the barriers; a dropped stream
+// (NE_FAIL_DROP) computes and delivers nothing.
+// Barrier phases: (1) every block has started (arrive at entry, wait before
+// the first remote store); (2) every delivered value has landed (release /
+// acquire); nothing touches another block's shared memory after phase 2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Receive buffer: M-1 rows (row q = stream (r + 1 + q) mod M) of
+// per = ceil(TILE / (M-1)) columns each, padded one word per 16:
+// (M-1) pad16(per) <= TILE + TILE/16 + 16 for every M in [3, 8].
+__host__ __device__ constexpr int recv_words() {
+  return CONV_TILE + CONV_TILE / 16 + 16;
+}
+
+// Recover `ncols` columns (this block's share) for a compile-time M from
+// the receive buffer (row q = stream (r + 1 + q) mod M, stride rstride).
+template <typename W, int MM>
+__device__ __forceinline__ void cluster_recover(const W* recv, int rstride,
+                                                int r, W* dbase, int64_t ldd,
+                                                int ncols, int l) {
+  int drow[MM];
+  drow[0] = r;
+  int row = r + 1 == MM ? 0 : r + 1;
+#pragma unroll
+  for (int q = 0; q < MM - 1; ++q) {
+    drow[q + 1] = row;
+    row = row + 1 == MM ? 0 : row + 1;
+  }
+  constexpr int NV = 2;
+#pragma unroll 1
+  for (int n = threadIdx.x; n < ncols; n += CONV_THREADS * NV)
+    recover_cols_m<W, MM, NV>(recv, rstride, drow, dbase, ldd, n,
+                              CONV_THREADS, ncols, l);
+}
+
+template <typename W, int MODE, bool VEC>
+__global__ void __launch_bounds__(CONV_THREADS,
+                                  (MODE == MODE_SPLIT ? 5 : 7) * 128 /
+                                      CONV_THREADS)
+conv_cluster_kernel(const ConvArgs p) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  cluster_arrive_relaxed();  // phase 1: this block has started
+  extern __shared__ int4 smem4[];
+  __shared__ long long s_warp[CONV_THREADS / 32];
+  const int Kp = p.Kp;
+  int* s_lo = reinterpret_cast<int*>(smem4);
+  int* s_hi = s_lo + (CONV_TILE + Kp);
+  int* s_taps = reinterpret_cast<int*>(
+      reinterpret_cast<unsigned char*>(smem4) +
+      operand_bytes(Kp, MODE, (int)sizeof(W)));
+  long long* s_pref = reinterpret_cast<long long*>(s_taps + Kp);
+  W* s_recv = reinterpret_cast<W*>(
+      reinterpret_cast<unsigned char*>(s_pref) +
+      (MODE == MODE_WIDE ? (size_t)Kp * 8 : 0));
+  const int M = p.M;
+  const int64_t tile = blockIdx.x / M;
+  const int m = (int)(blockIdx.x - tile * M);  // == rank in the cluster
+  const int64_t n0 = tile * CONV_TILE;
+  const int r = p.fail_mode == NE_FAIL_NONE ? M - 1 : p.failed;
+  const bool computes = !(p.fail_mode == NE_FAIL_SKIP && m == p.failed);
+  const int span = (int)lmin((int64_t)CONV_TILE, p.Nout - n0);
+  const int per = (span + M - 2) / (M - 1);  // columns per extractor
+
+  if (computes) {
+    const W* row = reinterpret_cast<const W*>(p.x) + (int64_t)m * p.ldx;
+    const W* prow = reinterpret_cast<const W*>(p.x) +
+                    (int64_t)(m == 0 ? M - 1 : m - 1) * p.ldx;
+    // taps, with their sum folded in (warp sums land before the barrier)
+    long long tsum = 0;
+    for (int j = threadIdx.x; j < Kp; j += CONV_THREADS) {
+      const int tv = j < p.K ? __ldg(p.g + j) : 0;
+      s_taps[j] = tv;
+      tsum += tv;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = tsum;
+    stage_from_global<W, MODE, VEC, true>(row, prow, p.N, n0, Kp, p.l,
+                                          (W)p.bias, s_lo, s_hi);
+    __syncthreads();
+    const bool edge = n0 < (int64_t)p.K - 1 || n0 + CONV_TILE > p.N;
+    unsigned long long shift_c = 0;
+    if constexpr (MODE == MODE_WIDE) {
+      if (p.bias != 0) {
+        if (edge) {
+          tap_prefix(s_taps, p.K, s_pref, s_warp);
+        } else {
+          long long tot = 0;
+#pragma unroll
+          for (int w = 0; w < CONV_THREADS / 32; ++w) tot += s_warp[w];
+          shift_c = (unsigned long long)p.bias * (unsigned long long)tot;
+        }
+      }
+    }
+    unsigned long long a64[CONV_R];
+    unsigned a32[CONV_R];
+    conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32);
+    cluster_wait();  // phase 1 complete: every peer block is resident
+    if (m != r) {
+      // push delta_m: column col goes to extractor e = col / per, row q
+      const int q = (m - r - 1 + 2 * M) % M;
+      const int64_t nt = n0 + (int64_t)threadIdx.x * CONV_R;
+      int col = threadIdx.x * CONV_R;
+      int e = min(col / per, M - 2);  // threads past the tail store nothing
+      int lc = col - e * per;
+      W* dst = cluster.map_shared_rank(s_recv, (unsigned)(e < r ? e : e + 1)) +
+               (size_t)q * pad16(per);
+#pragma unroll
+      for (int a = 0; a < CONV_R; ++a) {
+        if constexpr (MODE == MODE_WIDE) {
+          if (p.bias != 0)
+            a64[a] += edge ? shift_correction(p.bias, s_pref, nt + a, p.N, p.K)
+                           : shift_c;
+        }
+        if (col < span) {
+          if (lc == per) {  // next extractor's columns
+            ++e;
+            lc = 0;
+            dst = cluster.map_shared_rank(s_recv,
+                                          (unsigned)(e < r ? e : e + 1)) +
+                  (size_t)q * pad16(per);
+          }
+          dst[pad16(lc)] = combine<W, MODE>(a64[a], a32[a]);
+        }
+        ++col;
+        ++lc;
+      }
+    }
+  } else {
+    cluster_wait();  // phase 1 (a block that never runs still takes part)
+  }
+  cluster_arrive_release();  // phase 2: every pushed value has landed
+  cluster_wait();
+  if (m != r) {
+    // recover this block's columns from its own shared memory
+    const int e = m < r ? m : m - 1;
+    const int c0 = e * per;
+    const int c1 = min(span, c0 + per);
+    W* dbase = reinterpret_cast<W*>(p.y) + n0 + c0;
+    switch (M) {
+      case 3: cluster_recover<W, 3>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      case 4: cluster_recover<W, 4>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      case 5: cluster_recover<W, 5>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      case 6: cluster_recover<W, 6>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      case 7: cluster_recover<W, 7>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      default: cluster_recover<W, 8>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 constexpr size_t kSmemBudget = 200 * 1024;  // per block, of 227 KB
@@ -415,6 +589,64 @@ int launch_conv(const ConvArgs& a, bool vec, cudaStream_t s) {
     return launch_persistent<W, MODE, PROT>(a, s);
   return vec ? launch_simple<W, MODE, true, PROT>(a, s)
              : launch_simple<W, MODE, false, PROT>(a, s);
+}
+
+// operands | taps | tap prefix (MODE_WIDE) | receive buffer
+__host__ __device__ constexpr size_t cluster_smem_bytes(int Kp, int mode,
+                                                        int wb) {
+  return simple_smem_bytes(Kp, mode, wb) + (size_t)recv_words() * wb;
+}
+
+template <typename W, int MODE, bool VEC>
+int launch_cluster_v(const ConvArgs& a, cudaStream_t s) {
+  const size_t smem = cluster_smem_bytes(a.Kp, MODE, (int)sizeof(W));
+  static std::once_flag once;
+  static int attr = NE_OK;
+  std::call_once(once, [] {
+    attr = set_max_smem(conv_cluster_kernel<W, MODE, VEC>,
+                        cluster_smem_bytes(CONV_MAX_K, MODE_SPLIT, 8));
+  });
+  if (attr != NE_OK) return attr;
+  const int64_t blocks = a.ntiles * a.M;
+  if (blocks > 0x7fffffffLL) return NE_ERR_UNSUPPORTED;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+  cfg.blockDim = dim3(CONV_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)a.M;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return status_from_cuda(
+      cudaLaunchKernelEx(&cfg, conv_cluster_kernel<W, MODE, VEC>, a));
+}
+
+template <typename W, int MODE>
+int launch_cluster(const ConvArgs& a, bool vec, cudaStream_t s) {
+  return vec ? launch_cluster_v<W, MODE, true>(a, s)
+             : launch_cluster_v<W, MODE, false>(a, s);
+}
+
+// The fused protected convolution's form: thread-block clusters (M <= 8,
+// the default) or the cross-block arrival-word protocol (any M, or
+// NE_PROT_KERNEL=arrival).
+inline bool use_cluster(int M) {
+  static const bool off = [] {
+    const char* e = getenv("NE_PROT_KERNEL");
+    return e && strcmp(e, "arrival") == 0;
+  }();
+  return !off && M >= 3 && M <= 8;
+}
+
+int dispatch_cluster(const ConvArgs& a, int w, int mode, bool vec,
+                     cudaStream_t s) {
+  if (w == 32) return launch_cluster<int32_t, MODE_I32>(a, vec, s);
+  if (mode == MODE_WIDE) return launch_cluster<int64_t, MODE_WIDE>(a, vec, s);
+  return launch_cluster<int64_t, MODE_SPLIT>(a, vec, s);
 }
 
 template <bool PROT>
@@ -558,7 +790,7 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const size_t need_ws = ne_protected_conv_ws_bytes(M, N, K);
   if (!ws || ws_bytes < need_ws) return NE_ERR_NOMEM;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(ws, 0, need_ws, s) != cudaSuccess) return NE_ERR_CUDA;
+  const bool cluster = use_cluster(M);
   ConvArgs a{};
   a.x = c;
   a.ldx = ldc;
@@ -582,6 +814,13 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
+  if (cluster) {
+    if (dispatch_cluster(a, w, mode, vec, s) == NE_OK) return NE_OK;
+    // a refused cluster launch (configuration error, not sticky): clear it
+    // and take the arrival-word form
+    cudaGetLastError();
+  }
+  if (cudaMemsetAsync(ws, 0, need_ws, s) != cudaSuccess) return NE_ERR_CUDA;
   return dispatch_conv<true>(a, w, mode, vec, s);
 }
 

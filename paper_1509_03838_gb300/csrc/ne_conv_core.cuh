@@ -137,7 +137,7 @@ template <int T = CONV_THREADS>
 __host__ __device__ constexpr int out_stage_words() {
   return T * CONV_R + T * CONV_R / 16;
 }
-__device__ __forceinline__ int out_slot(int j) { return j + (j >> 4); }
+__device__ __forceinline__ int out_slot(int j) { return pad16(j); }
 
 template <typename W, int T = CONV_THREADS>
 __device__ __forceinline__ void write_tile(W* __restrict__ yrow, int64_t n0,

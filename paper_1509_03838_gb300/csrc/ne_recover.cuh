@@ -185,4 +185,115 @@ __device__ __forceinline__ void recover_columns_batched(
     if (live[i]) row_r[n + i * cstride] = dcur[i];
 }
 
+// Recover NV columns n + i*cstride of one tile from M-1 entangled rows read
+// through src[q] (row (r + 1 + q) mod M, q < M-1; e.g. other blocks' shared
+// memory in a cluster), writing all M outputs to dst[m] (rows of d, column
+// base already applied).  Columns at or beyond `end` are skipped.
+// Slot of word j in a shared-memory tile padded with one word per 16
+// (conflict-free strided parking of per-thread output runs).
+__host__ __device__ __forceinline__ int pad16(int j) { return j + (j >> 4); }
+
+template <typename W, int NV, int MAXC, bool PADDED>
+__device__ __forceinline__ void recover_columns_to(
+    const W* const (&src)[MAXC], const int (&drow)[MAXC + 1],
+    W* __restrict__ dbase, int64_t ldd, int M, int n, int cstride, int end,
+    int l) {
+  // drow[q + 1] is the output row of src[q]; drow[0] is the failed row r
+  W cache[MAXC][NV];
+  bool live[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) live[i] = (n + i * cstride) < end;
+#pragma unroll
+  for (int q = 0; q < MAXC; ++q) {
+    if (q < M - 1) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        cache[q][i] = live[i] ? src[q][PADDED ? pad16(n + i * cstride)
+                                             : n + i * cstride]
+                              : (W)0;
+    }
+  }
+  W t[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) t[i] = cache[0][i];
+#pragma unroll
+  for (int q = 1; q < MAXC; ++q) {
+    if (q < M - 1) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        t[i] = (q & 1) ? wsub<W>(shl<W>(t[i], l), cache[q][i])
+                       : wadd<W>(shl<W>(t[i], l), cache[q][i]);
+    }
+  }
+  const int win = (M - 1) * l;
+  W dcur[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    dcur[i] = sext_low<W>((M & 1) ? wsub<W>((W)0, t[i]) : t[i], win);
+#pragma unroll
+  for (int q = MAXC - 1; q >= 0; --q) {
+    if (q <= M - 2) {
+      W* out = dbase + (int64_t)drow[q + 1] * ldd + n;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const W nxt = wsub<W>(cache[q][i], dcur[i]) >> l;
+        if (live[i]) out[i * cstride] = dcur[i];
+        dcur[i] = nxt;
+      }
+    }
+  }
+  W* out = dbase + (int64_t)drow[0] * ldd + n;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (live[i]) out[i * cstride] = dcur[i];
+}
+
+// Compile-time-M form of recover_columns_to for the fused kernels: the
+// M-1 source rows src[q] (row (r + 1 + q) mod M) are local shared-memory
+// tiles padded one word per 16; outputs go to rows drow[] of d.  With M a
+// template constant no predicated-off row work is issued.
+template <typename W, int MM, int NV>
+__device__ __forceinline__ void recover_cols_m(const W* __restrict__ recv,
+                                               int rstride,
+                                               const int (&drow)[MM],
+                                               W* __restrict__ dbase,
+                                               int64_t ldd, int n, int cstride,
+                                               int end, int l) {
+  // drow[q + 1] is the output row of source row q; drow[0] is row r
+  W cache[MM - 1][NV];
+  bool live[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) live[i] = (n + i * cstride) < end;
+#pragma unroll
+  for (int q = 0; q < MM - 1; ++q) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      cache[q][i] = live[i] ? recv[q * rstride + pad16(n + i * cstride)] : (W)0;
+  }
+  W dcur[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    W t = cache[0][i];
+#pragma unroll
+    for (int q = 1; q < MM - 1; ++q)
+      t = (q & 1) ? wsub<W>(shl<W>(t, l), cache[q][i])
+                  : wadd<W>(shl<W>(t, l), cache[q][i]);
+    dcur[i] = sext_low<W>((MM & 1) ? wsub<W>((W)0, t) : t, (MM - 1) * l);
+  }
+#pragma unroll
+  for (int q = MM - 2; q >= 0; --q) {
+    W* out = dbase + (int64_t)drow[q + 1] * ldd + n;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const W nxt = wsub<W>(cache[q][i], dcur[i]) >> l;
+      if (live[i]) out[i * cstride] = dcur[i];
+      dcur[i] = nxt;
+    }
+  }
+  W* out = dbase + (int64_t)drow[0] * ldd + n;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (live[i]) out[i * cstride] = dcur[i];
+}
+
 }  // namespace ne
