@@ -47,7 +47,7 @@ L2_NOTE = ("inputs larger than L2: c 134 MB + d 134 MB per step vs 129 MB L2 "
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ne", "reference"], default="ne")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -310,7 +310,7 @@ def run_ne(args):
 
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
+    time.sleep(0.3)  # nvidia-smi samples every 100 ms from here on
     for i in range(args.warmup):
         protected(i)
     torch.cuda.synchronize()
@@ -324,8 +324,8 @@ def run_ne(args):
     gops = world * ops_job * args.steps / (total_ms * 1e-3) / 1e9
 
     # per-launch duration of the dominant (fused) kernel
-    _, launches = timed(protected, max(args.steps, 10), world, stream,
-                        per_launch=True)
+    _, launches = timed(protected, min(max(args.steps, 10), 200), world,
+                        stream, per_launch=True)
     prot_ms = statistics.mean(launches)
 
     # ---- baselines on the same data (same number of steps) ---------------
@@ -404,8 +404,9 @@ def run_ne(args):
                         else "T multiply-add instr/s (wide + 32-bit pairs)",
                 "frac": achieved / peak, "traffic": traffic,
                 "algorithmic_bytes": float((M * N + M * Nout) * 8),
-                "kernel": "conv_persistent_kernel<int64, MODE_WIDE, PROT> "
-                          "(fused entangle + conv + extraction)",
+                "kernel": "conv_cluster_kernel<int64, MODE_WIDE> (fused "
+                          "entangle-on-load + conv + cluster exchange + "
+                          "recovery)",
                 "peak_source": "measured on this GPU by ne_probe_imad_rate "
                                "(independent mad.wide.s32 chains, 8 per "
                                "thread, 16 warps per scheduler)",
@@ -470,7 +471,11 @@ def run_ne(args):
 # DRAM traffic of one launch of the fused kernel on this workload, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for
 # the kernel sources it was taken on (their SHA-256 is checked at run time).
-TRAFFIC_CAPTURE = {"sources_sha256": None, "bytes": None}
+TRAFFIC_CAPTURE = {
+    "sources_sha256":
+        "cf2c9b0a55a618b46c8b3e306dd6156377ae1a13c4383db8944d44591ef8ed67",
+    "bytes": 134309376 + 86481920,  # profiles/conv_cluster_protected_M4_N2e22_K64.md
+}
 CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_recover.cuh",
                 "ne_common.cuh"]
 

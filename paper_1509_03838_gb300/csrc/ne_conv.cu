@@ -396,7 +396,7 @@ __device__ __forceinline__ void cluster_recover(const W* recv, int rstride,
     drow[q + 1] = row;
     row = row + 1 == MM ? 0 : row + 1;
   }
-  constexpr int NV = 2;
+  constexpr int NV = MM <= 5 ? 4 : 2;  // independent columns per thread
 #pragma unroll 1
   for (int n = threadIdx.x; n < ncols; n += CONV_THREADS * NV)
     recover_cols_m<W, MM, NV>(recv, rstride, drow, dbase, ldd, n,
@@ -474,8 +474,13 @@ conv_cluster_kernel(const ConvArgs p) {
       int col = threadIdx.x * CONV_R;
       int e = min(col / per, M - 2);  // threads past the tail store nothing
       int lc = col - e * per;
-      W* dst = cluster.map_shared_rank(s_recv, (unsigned)(e < r ? e : e + 1)) +
-               (size_t)q * pad16(per);
+      // a block's own share is written locally, the others' remotely
+      auto slot_of = [&](int ee) -> W* {
+        const unsigned rk = (unsigned)(ee < r ? ee : ee + 1);
+        W* base = rk == (unsigned)m ? s_recv : cluster.map_shared_rank(s_recv, rk);
+        return base + (size_t)q * pad16(per);
+      };
+      W* dst = slot_of(e);
 #pragma unroll
       for (int a = 0; a < CONV_R; ++a) {
         if constexpr (MODE == MODE_WIDE) {
@@ -487,9 +492,7 @@ conv_cluster_kernel(const ConvArgs p) {
           if (lc == per) {  // next extractor's columns
             ++e;
             lc = 0;
-            dst = cluster.map_shared_rank(s_recv,
-                                          (unsigned)(e < r ? e : e + 1)) +
-                  (size_t)q * pad16(per);
+            dst = slot_of(e);
           }
           dst[pad16(lc)] = combine<W, MODE>(a64[a], a32[a]);
         }
