@@ -143,6 +143,39 @@ int ne_conv(const void *x, int64_t ldx, int M, int64_t N, const int32_t *g,
             int K, void *y, int64_t ldy, int w, int64_t x_min, int64_t x_max,
             uint32_t live_mask, void *stream);
 
+/* Kinds of ne_conv_kind (the convolution-type LSB ops of Eq. 2). */
+typedef enum {
+  NE_CONV_LINEAR = 0,   /* y[n] = sum_t x[n-t] g[t], n in [0, N+K-1)        */
+  NE_CONV_CIRCULAR = 1, /* y[n] = sum_t x[(n-t) mod N] g[t], n in [0, N);   */
+                        /* requires K <= N                                  */
+  NE_CONV_XCORR = 2     /* y[n] = sum_t x[n+t-(K-1)] g[t], n in [0, N+K-1)  */
+                        /* (full cross-correlation, lag n-(K-1))            */
+} ne_conv_kind_t;
+
+/*
+ * ne_conv_kind -- ne_conv for any kind of ne_conv_kind_t: linear
+ * convolution (identical to ne_conv), circular convolution or full
+ * cross-correlation, each on raw or entangled streams (Eq. 2 names circular
+ * convolution and cross-correlation; all are Z/2^w-linear in x, so the
+ * entangled outputs recover with ne_recover like the linear ones).  y has
+ * N (circular) or N+K-1 samples per row.  Same arithmetic modes, ranges and
+ * errors as ne_conv.
+ */
+int ne_conv_kind(const void *x, int64_t ldx, int M, int64_t N,
+                 const int32_t *g, int K, void *y, int64_t ldy, int w,
+                 int64_t x_min, int64_t x_max, uint32_t live_mask, int kind,
+                 void *stream);
+
+/*
+ * ne_dot -- the inner product <x_m, g> of every live stream (Eq. 2, op =
+ * inner product): y[m] = sum_{n<N} x_m[n] g[n] (mod 2^w), one w-bit word
+ * per stream written to y[m * ldy] (so the M results form a 1-sample
+ * "stream set" that ne_recover accepts with Nout = 1 and ld = ldy).
+ * g: N words of the same width as x (device).  Bandwidth-bound.
+ */
+int ne_dot(const void *x, int64_t ldx, int M, int64_t N, const void *g,
+           int w, void *y, int64_t ldy, uint32_t live_mask, void *stream);
+
 /*
  * ne_recover -- recover all M outputs from the M-1 entangled outputs that
  * remain after stream `failed` fail-stopped (Eq. 16-19; Eq. 10 for M = 3;
@@ -163,6 +196,28 @@ int ne_recover(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
  */
 int ne_extract(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
                int l, void *d, int64_t ld_out, void *stream);
+
+/*
+ * ne_detect -- silent-data-corruption detection with all M entangled
+ * outputs present (Remark 4; the paper leaves the procedure to future
+ * work).  Per column n: recover all M outputs from streams 1..M-1 (as
+ * ne_recover with failed = 0), then flag the column if the unused stream
+ * disagrees with them, delta_0 != d_0 + (d_{M-1} << l) (mod 2^w), or if
+ * any recovered output leaves [-d_max, d_max].  When every true output
+ * lies within the exact range (|d| <= d_max <= d_max_exact of ne_params),
+ * a column where one stream's value was altered is always flagged, and a
+ * clean column never is; alterations of two or more streams at the same
+ * column may go unnoticed.
+ *   delta: M rows (ldd) of Nout words; d: optional (NULL) M output rows
+ *   (ld_out) receiving the recovered outputs; count: device uint32 set to
+ *   the number of flagged columns (the call zeroes it on `stream` first);
+ *   positions: device int64 array receiving up to max_positions flagged
+ *   column indices (in no particular order; NULL if max_positions = 0).
+ * Bandwidth-bound: reads M rows once (and writes M if d != NULL).
+ */
+int ne_detect(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
+              int l, int64_t d_max, void *d, int64_t ld_out, uint32_t *count,
+              int64_t *positions, int max_positions, void *stream);
 
 /*
  * ne_protected_conv -- the whole protected path in one launch:

@@ -341,3 +341,90 @@ int orc_permute(const int64_t *x, int64_t N, const int64_t *perm, int64_t *y)
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Silent-data-corruption detection with all M streams (Remark 4)      */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Remark 4 notes that, with every entangled output present, corruption of
+ * one stream can be detected; the paper leaves the procedure to future
+ * work.  This oracle's reading: recover all M outputs from streams
+ * 1..M-1 (Eq. 16-19 with r = 0), then flag column n if the unused
+ * entangled output disagrees with them, delta_0 != d_0 + S_l{d_{M-1}}
+ * (mod 2^w), or if a recovered output exceeds the declared bound d_max.
+ * For outputs within the exact range this flags every column where one
+ * stream was altered.  flags[n] receives 1 for a flagged column, else 0;
+ * returns the number of flagged columns, or -1 on bad arguments.
+ */
+int64_t orc_detect(const int64_t *delta, int M, int64_t Nout, int64_t ld,
+                   int w, int l, int64_t d_max, int64_t *d, int64_t ldd,
+                   int64_t *flags)
+{
+    if (orc_recover(delta, M, Nout, ld, w, l, 0, d, ldd) != 0) return -1;
+    int64_t count = 0;
+    for (int64_t n = 0; n < Nout; ++n) {
+        i128 d0 = d[n];
+        i128 dl = d[(int64_t)(M - 1) * ldd + n];
+        i128 expect = reduce_bits(add128(d0, shift_S(dl, l)), w);
+        int bad = expect != (i128)delta[n];
+        for (int m = 0; m < M; ++m) {
+            i128 v = d[(int64_t)m * ldd + n];
+            if (v > d_max || v < -(i128)d_max) bad = 1;
+        }
+        flags[n] = bad;
+        count += bad;
+    }
+    return count;
+}
+
+/* ------------------------------------------------------------------ */
+/* More LSB operations of Eq. 2: circular convolution, cross-         */
+/* correlation, inner product (plain definitions, exact, mod 2^w)      */
+/* ------------------------------------------------------------------ */
+
+/* y[n] = sum_t x[(n - t) mod N] g[t], 0 <= n < N. */
+int64_t orc_conv_circular(const int64_t *x, int64_t N, const int64_t *g, int K,
+                          int w, int64_t *y)
+{
+    int64_t overflow = 0;
+    for (int64_t n = 0; n < N; ++n) {
+        i128 acc = 0;
+        for (int t = 0; t < K; ++t) {
+            int64_t j = ((n - t) % N + N) % N;
+            acc += (i128)x[j] * (i128)g[t];
+        }
+        if (!fits_bits(acc, w)) ++overflow;
+        y[n] = (int64_t)reduce_bits(acc, w);
+    }
+    return overflow;
+}
+
+/* Full cross-correlation: y[n] = sum_t x[n + t - (K-1)] g[t],
+ * 0 <= n < N + K - 1, x zero outside [0, N). */
+int64_t orc_xcorr(const int64_t *x, int64_t N, const int64_t *g, int K, int w,
+                  int64_t *y)
+{
+    int64_t overflow = 0;
+    for (int64_t n = 0; n < N + K - 1; ++n) {
+        i128 acc = 0;
+        for (int t = 0; t < K; ++t) {
+            int64_t j = n + t - (K - 1);
+            if (j < 0 || j >= N) continue;
+            acc += (i128)x[j] * (i128)g[t];
+        }
+        if (!fits_bits(acc, w)) ++overflow;
+        y[n] = (int64_t)reduce_bits(acc, w);
+    }
+    return overflow;
+}
+
+/* Inner product sum_n x[n] g[n], stored modulo 2^w in *y. */
+int64_t orc_dot(const int64_t *x, const int64_t *g, int64_t N, int w,
+                int64_t *y)
+{
+    i128 acc = 0;
+    for (int64_t n = 0; n < N; ++n) acc += (i128)x[n] * (i128)g[n];
+    *y = (int64_t)reduce_bits(acc, w);
+    return fits_bits(acc, w) ? 0 : 1;
+}

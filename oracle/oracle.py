@@ -14,6 +14,9 @@ marshals numpy arrays and chains the steps in the paper's order:
 * :func:`checksum`, :func:`checksum_recover` -- Eq. 3-5 (ABFT baseline)
 * :func:`scale`, :func:`add`, :func:`self_entangle`, :func:`permute`
   -- the other LSB operations of Eq. 2 and the footnote to Eq. 9
+* :func:`detect`    -- corruption detection with all M streams (Remark 4)
+* :func:`conv_circular`, :func:`xcorr`, :func:`dot` -- circular convolution,
+  cross-correlation and inner product (Eq. 2)
 """
 from __future__ import annotations
 
@@ -77,6 +80,15 @@ def _load():
             lib.orc_self_entangle.restype = i64
             lib.orc_permute.argtypes = [_i64p, i64, _i64p, _i64p]
             lib.orc_permute.restype = i32
+            lib.orc_detect.argtypes = [_i64p, i32, i64, i64, i32, i32, i64,
+                                       _i64p, i64, _i64p]
+            lib.orc_detect.restype = i64
+            lib.orc_conv_circular.argtypes = [_i64p, i64, _i64p, i32, i32, _i64p]
+            lib.orc_conv_circular.restype = i64
+            lib.orc_xcorr.argtypes = [_i64p, i64, _i64p, i32, i32, _i64p]
+            lib.orc_xcorr.restype = i64
+            lib.orc_dot.argtypes = [_i64p, _i64p, i64, i32, _i64p]
+            lib.orc_dot.restype = i64
             _lib = lib
     return _lib
 
@@ -262,3 +274,63 @@ def conv_at(x, g, w: int, positions):
         lib.orc_conv(_p(xs), xs.shape[0], _p(g), K, w, _p(ys))
         out[i] = ys[n - lo]
     return out
+
+
+def detect(delta, w: int, l: int, d_max: int):
+    """(flags[Nout], d) -- columns where the unused stream 0 disagrees with
+    the outputs recovered from streams 1..M-1, or an output leaves
+    [-d_max, d_max] (Remark 4)."""
+    delta = _arr(delta)
+    M, Nout = delta.shape
+    d = np.empty_like(delta)
+    flags = np.empty(Nout, dtype=np.int64)
+    n = _load().orc_detect(_p(delta), M, Nout, Nout, w, l, int(d_max), _p(d),
+                           Nout, _p(flags))
+    if n < 0:
+        raise ValueError("bad detect arguments")
+    return flags.astype(bool), d
+
+
+def _rowwise(fn, x, g, w, out_len):
+    x = _arr(x)
+    g = _arr(g)
+    rows = x[None, :] if x.ndim == 1 else x
+    y = np.empty((rows.shape[0], out_len(rows.shape[1], g.shape[0])),
+                 dtype=np.int64)
+    ov = 0
+    for m in range(rows.shape[0]):
+        xm = np.ascontiguousarray(rows[m])
+        ym = np.empty(y.shape[1], dtype=np.int64)
+        ov += fn(_p(xm), xm.shape[0], _p(g), g.shape[0], w, _p(ym))
+        y[m] = ym
+    return (y[0] if x.ndim == 1 else y), ov
+
+
+def conv_circular(x, g, w: int, strict: bool = True):
+    """y[n] = sum_t x[(n - t) mod N] g[t], n < N (each row)."""
+    y, ov = _rowwise(_load().orc_conv_circular, x, g, w, lambda n, k: n)
+    if strict and ov:
+        raise OracleOverflow(f"{ov} outputs exceed {w} bits")
+    return y
+
+
+def xcorr(x, g, w: int, strict: bool = True):
+    """Full cross-correlation, y[n] = sum_t x[n + t - (K-1)] g[t]."""
+    y, ov = _rowwise(_load().orc_xcorr, x, g, w, lambda n, k: n + k - 1)
+    if strict and ov:
+        raise OracleOverflow(f"{ov} outputs exceed {w} bits")
+    return y
+
+
+def dot(x, g, w: int):
+    """Inner product of each row of x with g, modulo 2^w."""
+    x = _arr(x)
+    g = _arr(g)
+    rows = x[None, :] if x.ndim == 1 else x
+    out = np.empty(rows.shape[0], dtype=np.int64)
+    for m in range(rows.shape[0]):
+        xm = np.ascontiguousarray(rows[m])
+        v = np.empty(1, dtype=np.int64)
+        _load().orc_dot(_p(xm), _p(g), xm.shape[0], w, _p(v))
+        out[m] = v[0]
+    return out[0] if x.ndim == 1 else out

@@ -48,6 +48,7 @@ struct ConvArgs {
   int fail_mode;
   uint32_t* ws;        // protected kernel: per-tile {claim, ready} words
   long long bias;      // MODE_WIDE range shift b (x - b fits 32 bits)
+  int kind;            // NE_CONV_LINEAR / NE_CONV_CIRCULAR / NE_CONV_XCORR
 };
 
 // Stage s[j] = x[n0 - Kp + j] (zero outside [0, N)) for j in [0, TILE+Kp)
@@ -112,6 +113,23 @@ __host__ __device__ constexpr size_t operand_bytes(int Kp, int mode, int wb) {
                : (size_t)out_stage_words<CONV_THREADS>() * wb) +
           15) / 16 * 16;
 }
+// Stage the window of a circular convolution: s[j] = x[(n0 - Kp + j) mod N]
+// (every index lands in the row; N >= K).
+template <typename W, int MODE>
+__device__ __forceinline__ void stage_circular(const W* __restrict__ row,
+                                               int64_t N, int64_t n0, int Kp,
+                                               W bias, int* s_lo, int* s_hi) {
+  const int total = CONV_TILE + Kp;
+  for (int j = threadIdx.x; j < total; j += CONV_THREADS) {
+    int64_t gi = (n0 - Kp + j) % N;
+    if (gi < 0) gi += N;
+    int lo, hi;
+    split_word<W, MODE>(wsub<W>(__ldg(row + gi), bias), lo, hi);
+    s_lo[j] = lo;
+    if constexpr (MODE == MODE_SPLIT) s_hi[j] = hi;
+  }
+}
+
 __host__ __device__ constexpr size_t simple_smem_bytes(int Kp, int mode,
                                                        int wb) {
   return operand_bytes(Kp, mode, wb) + (size_t)Kp * 4 +
@@ -144,14 +162,21 @@ conv_simple_kernel(const ConvArgs p) {
   const W* row = reinterpret_cast<const W*>(p.x) + (int64_t)m * p.ldx;
   const W* prow = reinterpret_cast<const W*>(p.x) +
                   (int64_t)(m == 0 ? p.M - 1 : m - 1) * p.ldx;
+  // cross-correlation = convolution with the taps reversed
   for (int j = threadIdx.x; j < Kp; j += CONV_THREADS)
-    s_taps[j] = j < p.K ? __ldg(p.g + j) : 0;
-  stage_from_global<W, MODE, VEC, PROT>(row, prow, p.N, n0, Kp, p.l,
-                                        (W)p.bias, s_lo, s_hi);
+    s_taps[j] = j < p.K ? __ldg(p.g + (p.kind == NE_CONV_XCORR ? p.K - 1 - j : j))
+                        : 0;
+  if (p.kind == NE_CONV_CIRCULAR)
+    stage_circular<W, MODE>(row, p.N, n0, Kp, (W)p.bias, s_lo, s_hi);
+  else
+    stage_from_global<W, MODE, VEC, PROT>(row, prow, p.N, n0, Kp, p.l,
+                                          (W)p.bias, s_lo, s_hi);
   __syncthreads();
   // range shift: outputs of an interior tile all see every tap (add the
-  // constant b * sum g); only the tiles at the two ends need the prefix sums
-  const bool edge = n0 < (int64_t)p.K - 1 || n0 + CONV_TILE > p.N;
+  // constant b * sum g); only the tiles at the two ends need the prefix
+  // sums.  A circular convolution has no ends.
+  const bool edge = p.kind != NE_CONV_CIRCULAR &&
+                    (n0 < (int64_t)p.K - 1 || n0 + CONV_TILE > p.N);
   unsigned long long shift_c = 0;
   if constexpr (MODE == MODE_WIDE) {
     if (p.bias != 0) {
@@ -749,6 +774,51 @@ int ne_conv(const void* x, int64_t ldx, int M, int64_t N, const int32_t* g,
   // rows); outputs are stored through shared memory for any alignment
   const bool vec = rows_aligned16(x, ldx, wb);
   return dispatch_conv<false>(a, w, mode, vec, (cudaStream_t)stream);
+}
+
+int ne_conv_kind(const void* x, int64_t ldx, int M, int64_t N,
+                 const int32_t* g, int K, void* y, int64_t ldy, int w,
+                 int64_t x_min, int64_t x_max, uint32_t live_mask, int kind,
+                 void* stream) {
+  if (kind == NE_CONV_LINEAR)
+    return ne_conv(x, ldx, M, N, g, K, y, ldy, w, x_min, x_max, live_mask,
+                   stream);
+  if ((kind != NE_CONV_CIRCULAR && kind != NE_CONV_XCORR) || M < 1 || M > 32 ||
+      N < 0 || K < 1 || K > CONV_MAX_K || ldx < N || (w != 32 && w != 64))
+    return NE_ERR_INVALID_ARG;
+  if (N == 0) return NE_OK;
+  if (kind == NE_CONV_CIRCULAR && K > N) return NE_ERR_INVALID_ARG;
+  const int64_t Nout = kind == NE_CONV_CIRCULAR ? N : N + K - 1;
+  if (!x || !y || !g || ldy < Nout) return NE_ERR_INVALID_ARG;
+  const int wb = w / 8;
+  if (overlaps(x, rows_bytes(M, ldx, N, wb), y, rows_bytes(M, ldy, Nout, wb)))
+    return NE_ERR_INVALID_ARG;
+  ConvArgs a{};
+  a.x = x;
+  a.ldx = ldx;
+  a.M = M;
+  a.N = N;
+  a.Nout = Nout;
+  a.ntiles = (Nout + CONV_TILE - 1) / CONV_TILE;
+  a.g = g;
+  a.K = K;
+  a.Kp = (K + CONV_KC - 1) / CONV_KC * CONV_KC;
+  a.y = y;
+  a.ldy = ldy;
+  a.live_mask = live_mask;
+  a.kind = kind;
+  const int mode = choose_mode(w, x_min <= x_max, (__int128)x_min,
+                               (__int128)x_max, &a.bias);
+  const bool vec = rows_aligned16(x, ldx, wb);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the one-block-per-unit kernel handles every kind
+  if (w == 32) return vec ? launch_simple<int32_t, MODE_I32, true, false>(a, s)
+                          : launch_simple<int32_t, MODE_I32, false, false>(a, s);
+  if (mode == MODE_WIDE)
+    return vec ? launch_simple<int64_t, MODE_WIDE, true, false>(a, s)
+               : launch_simple<int64_t, MODE_WIDE, false, false>(a, s);
+  return vec ? launch_simple<int64_t, MODE_SPLIT, true, false>(a, s)
+             : launch_simple<int64_t, MODE_SPLIT, false, false>(a, s);
 }
 
 size_t ne_protected_conv_ws_bytes(int M, int64_t N, int K) {

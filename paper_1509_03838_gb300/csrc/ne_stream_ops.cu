@@ -7,6 +7,8 @@
 // 4 int32 words) per thread, so each row access is one 128-bit coalesced
 // load or store.  Rows that are not 16-byte aligned fall back to one word
 // per thread.  Grids are a multiple of the SM count with a grid-stride loop.
+#include <algorithm>
+
 #include "ne_common.cuh"
 #include "ne_recover.cuh"
 
@@ -107,6 +109,98 @@ recover_kernel(const W* delta, int64_t ldd, int M, int64_t Nout, int l, int r,
     for (int64_t n = ncols * V + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
          n < Nout; n += stride)
       recover_columns<W, 0, 1, false>(delta, ldd, M, n, l, r, d, ldo);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Corruption detection with all M streams present (Remark 4): recover every
+// output from streams 1..M-1 (w-bit chain), then flag the column if the
+// unused delta_0 disagrees with d_0 + (d_{M-1} << l) (mod 2^w) or if an
+// output leaves [-d_max, d_max].  For outputs within the exact range, a
+// column where any single stream was altered is always flagged: an
+// unflagged column's outputs are an in-range solution agreeing with the
+// truth on every other row, and recovery without the altered row is exact.
+// One column per thread (warp-contiguous rows).  MM = M (3..8) or 0 (any).
+// ---------------------------------------------------------------------------
+template <typename W, int MM>
+__global__ void __launch_bounds__(kThreads)
+detect_kernel(const W* __restrict__ delta, int64_t ldd, int M_rt,
+              int64_t Nout, int l, long long d_max, W* __restrict__ d,
+              int64_t ldo, uint32_t* count, int64_t* pos, int max_pos) {
+  constexpr int CAP = MM ? MM : 32;
+  const int M = MM ? MM : M_rt;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < Nout;
+       n += stride) {
+    W v[CAP];
+#pragma unroll
+    for (int m = 0; m < CAP; ++m)
+      if (m < M) v[m] = __ldg(delta + (int64_t)m * ldd + n);
+    W t = v[1];
+#pragma unroll
+    for (int q = 1; q < CAP - 1; ++q)
+      if (q < M - 1)
+        t = (q & 1) ? wsub<W>(shl<W>(t, l), v[1 + q])
+                    : wadd<W>(shl<W>(t, l), v[1 + q]);
+    W out[CAP];
+    out[M - 1] = sext_low<W>((M & 1) ? wsub<W>((W)0, t) : t, (M - 1) * l);
+#pragma unroll
+    for (int j = CAP - 1; j >= 1; --j)
+      if (j < M) out[j - 1] = wsub<W>(v[j], out[j]) >> l;
+    bool bad = wadd<W>(out[0], shl<W>(out[M - 1], l)) != v[0];
+#pragma unroll
+    for (int m = 0; m < CAP; ++m)
+      if (m < M) {
+        const long long x = (long long)out[m];
+        bad |= (x > d_max) || (x < -d_max);
+        if (d) d[(int64_t)m * ldo + n] = out[m];
+      }
+    if (bad) {
+      const uint32_t i = atomicAdd(count, 1u);
+      if (pos && (int)i < max_pos) pos[i] = n;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inner product of every live stream with g (Eq. 2, op = <.,.>): blocks
+// reduce chunks of a row (wrapping w-bit arithmetic) and add their partial
+// sums into y[m] with one atomic each (addition modulo 2^w commutes).
+// ---------------------------------------------------------------------------
+template <typename W>
+__global__ void __launch_bounds__(kThreads)
+zero_rows_kernel(W* y, int64_t ldy, int M, uint32_t live) {
+  const int m = threadIdx.x;
+  if (m < M && ((live >> m) & 1u)) y[(int64_t)m * ldy] = 0;
+}
+
+template <typename W>
+__global__ void __launch_bounds__(kThreads)
+dot_kernel(const W* __restrict__ x, int64_t ldx, int64_t N,
+           const W* __restrict__ g, W* y, int64_t ldy, uint32_t live) {
+  using U = typename Word<W>::U;
+  const int m = blockIdx.y;
+  if (!((live >> m) & 1u)) return;
+  const W* row = x + (int64_t)m * ldx;
+  U acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+       n += stride)
+    acc += (U)__ldg(row + n) * (U)__ldg(g + n);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ U s_part[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    U tot = 0;
+    for (int i = 0; i < kThreads / 32; ++i) tot += s_part[i];
+    if constexpr (sizeof(U) == 8)
+      atomicAdd(reinterpret_cast<unsigned long long*>(y + (int64_t)m * ldy),
+                (unsigned long long)tot);
+    else
+      atomicAdd(reinterpret_cast<unsigned int*>(y + (int64_t)m * ldy),
+                (unsigned int)tot);
   }
 }
 
@@ -358,6 +452,80 @@ int ne_recover(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
 int ne_extract(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
                int l, void* d, int64_t ld_out, void* stream) {
   return ne_recover(delta, ldd, M, Nout, w, l, 0, d, ld_out, stream);
+}
+
+int ne_dot(const void* x, int64_t ldx, int M, int64_t N, const void* g,
+           int w, void* y, int64_t ldy, uint32_t live_mask, void* stream) {
+  if (M < 1 || M > 32 || N < 0 || ldx < N || (w != 32 && w != 64) ||
+      !y || ldy < 1)
+    return NE_ERR_INVALID_ARG;
+  if (N > 0 && (!x || !g)) return NE_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t per_row = std::max<int64_t>(
+      1, std::min<int64_t>((N + kThreads * 8 - 1) / (kThreads * 8),
+                           (int64_t)sm_count() * 8 / M + 1));
+  const dim3 grid((unsigned)per_row, (unsigned)M);
+  if (w == 32) {
+    zero_rows_kernel<int32_t><<<1, 32, 0, s>>>((int32_t*)y, ldy, M, live_mask);
+    if (N > 0)
+      dot_kernel<int32_t><<<grid, kThreads, 0, s>>>(
+          (const int32_t*)x, ldx, N, (const int32_t*)g, (int32_t*)y, ldy,
+          live_mask);
+  } else {
+    zero_rows_kernel<int64_t><<<1, 32, 0, s>>>((int64_t*)y, ldy, M, live_mask);
+    if (N > 0)
+      dot_kernel<int64_t><<<grid, kThreads, 0, s>>>(
+          (const int64_t*)x, ldx, N, (const int64_t*)g, (int64_t*)y, ldy,
+          live_mask);
+  }
+  return status_from_cuda(cudaGetLastError());
+}
+
+int ne_detect(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
+              int l, int64_t d_max, void* d, int64_t ld_out, uint32_t* count,
+              int64_t* positions, int max_positions, void* stream) {
+  if (M < 3 || M > 32 || Nout < 0 || ldd < Nout || (w != 32 && w != 64) ||
+      l <= 0 || (M - 1) * l > w || d_max < 0 || !count ||
+      (d && ld_out < Nout) || max_positions < 0 ||
+      (max_positions > 0 && !positions))
+    return NE_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(count, 0, sizeof(uint32_t), s) != cudaSuccess)
+    return NE_ERR_CUDA;
+  if (Nout == 0) return NE_OK;
+  if (!delta) return NE_ERR_INVALID_ARG;
+  const int wb = w / 8;
+  if (d && overlaps(delta, rows_bytes(M, ldd, Nout, wb), d,
+                    rows_bytes(M, ld_out, Nout, wb)))
+    return NE_ERR_INVALID_ARG;
+  const int grid = grid_for(Nout);
+#define NE_DETECT(WT, MMV)                                                  \
+  detect_kernel<WT, MMV><<<grid, kThreads, 0, s>>>(                        \
+      (const WT*)delta, ldd, M, Nout, l, (long long)d_max, (WT*)d, ld_out, \
+      count, positions, max_positions)
+  if (w == 32) {
+    switch (M) {
+      case 3: NE_DETECT(int32_t, 3); break;
+      case 4: NE_DETECT(int32_t, 4); break;
+      case 5: NE_DETECT(int32_t, 5); break;
+      case 6: NE_DETECT(int32_t, 6); break;
+      case 7: NE_DETECT(int32_t, 7); break;
+      case 8: NE_DETECT(int32_t, 8); break;
+      default: NE_DETECT(int32_t, 0); break;
+    }
+  } else {
+    switch (M) {
+      case 3: NE_DETECT(int64_t, 3); break;
+      case 4: NE_DETECT(int64_t, 4); break;
+      case 5: NE_DETECT(int64_t, 5); break;
+      case 6: NE_DETECT(int64_t, 6); break;
+      case 7: NE_DETECT(int64_t, 7); break;
+      case 8: NE_DETECT(int64_t, 8); break;
+      default: NE_DETECT(int64_t, 0); break;
+    }
+  }
+#undef NE_DETECT
+  return status_from_cuda(cudaGetLastError());
 }
 
 int ne_checksum(const void* c, int64_t ldc, int M, int64_t N, int w, void* r,

@@ -31,6 +31,10 @@ NE_ERR_TIMEOUT = 5
 NE_ERR_CUDA = 6
 NE_ERR_UNSUPPORTED = 7
 
+NE_CONV_LINEAR = 0
+NE_CONV_CIRCULAR = 1
+NE_CONV_XCORR = 2
+
 NE_FAIL_NONE = 0
 NE_FAIL_SKIP = 1
 NE_FAIL_DROP = 2
@@ -87,6 +91,11 @@ _SIGS = {
                                    _i32, _i64, _i64, _i64, _i32, _i32, _vp,
                                    _i64, _vp], _i32),
     "ne_checksum": ([_vp, _i64, _i32, _i64, _i32, _vp, _vp], _i32),
+    "ne_detect": ([_vp, _i64, _i32, _i64, _i32, _i32, _i64, _vp, _i64, _vp,
+                   _vp, _i32, _vp], _i32),
+    "ne_conv_kind": ([_vp, _i64, _i32, _i64, _vp, _i32, _vp, _i64, _i32, _i64,
+                      _i64, _u32, _i32, _vp], _i32),
+    "ne_dot": ([_vp, _i64, _i32, _i64, _vp, _i32, _vp, _i64, _u32, _vp], _i32),
     "ne_checksum_recover": ([_vp, _i64, _vp, _i32, _i64, _i32, _i32, _vp, _vp],
                             _i32),
     "ne_scale": ([_vp, _i64, _i32, _i64, _i64, _i32, _vp, _i64, _vp], _i32),
@@ -255,6 +264,31 @@ def ne_conv(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
     return y
 
 
+def ne_conv_kind(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
+                 kind: int, x_range: tuple[int, int] | None = None,
+                 live_mask: int = 0xFFFFFFFF, stream=None) -> torch.Tensor:
+    """Linear / circular convolution or full cross-correlation (Eq. 2)."""
+    x_min, x_max = x_range if x_range is not None else (1, 0)
+    px, M, n, ldx = _rows(x, "x")
+    py, _, _, ldy = _rows(y, "y")
+    _check(lib().ne_conv_kind(px, ldx, M, n, ctypes.c_void_p(g.data_ptr()),
+                              g.numel(), py, ldy, _word_bits(x), x_min, x_max,
+                              live_mask & 0xFFFFFFFF, kind, _stream(stream)),
+           "ne_conv_kind")
+    return y
+
+
+def ne_dot(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
+           live_mask: int = 0xFFFFFFFF, stream=None) -> torch.Tensor:
+    """y[m] = <x_m, g> (mod 2^w); y is [M, 1] (or any [M, ld] view)."""
+    px, M, n, ldx = _rows(x, "x")
+    py, _, _, ldy = _rows(y, "y")
+    _check(lib().ne_dot(px, ldx, M, n, ctypes.c_void_p(g.data_ptr()),
+                        _word_bits(x), py, ldy, live_mask & 0xFFFFFFFF,
+                        _stream(stream)), "ne_dot")
+    return y
+
+
 def ne_recover(delta: torch.Tensor, d: torch.Tensor, *, l: int, failed: int,
                Nout: int | None = None, stream=None) -> torch.Tensor:
     pdl, M, n, ldd = _rows(delta, "delta")
@@ -321,6 +355,25 @@ def ne_protected_conv_noalloc(c: torch.Tensor, g: torch.Tensor,
         _word_bits(c), l, int(c_range[0]), int(c_range[1]), max_abs_g, failed,
         fail_mode, pd, ldd, _stream(stream)), "ne_protected_conv_noalloc")
     return d
+
+
+def ne_detect(delta: torch.Tensor, *, l: int, d_max: int,
+              d: torch.Tensor | None = None, max_positions: int = 0,
+              stream=None):
+    """Flag columns where one entangled stream was altered (Remark 4).
+    Returns (count tensor [1] uint32-as-int32 view, positions tensor)."""
+    pdl, M, n, ldd = _rows(delta, "delta")
+    w = _word_bits(delta)
+    count = torch.zeros(1, dtype=torch.int32, device=delta.device)
+    pos = torch.full((max(max_positions, 1),), -1, dtype=torch.int64,
+                     device=delta.device)
+    pd, ldo = (ctypes.c_void_p(0), 0) if d is None else (_rows(d, "d")[0],
+                                                          _rows(d, "d")[3])
+    _check(lib().ne_detect(pdl, ldd, M, n, w, l, int(d_max), pd, ldo,
+                           ctypes.c_void_p(count.data_ptr()),
+                           ctypes.c_void_p(pos.data_ptr()), max_positions,
+                           _stream(stream)), "ne_detect")
+    return count, pos[:max_positions]
 
 
 def ne_checksum(c: torch.Tensor, r: torch.Tensor, *, N: int | None = None,

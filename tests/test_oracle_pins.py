@@ -400,3 +400,92 @@ def test_add_plain_kernel_needs_self_entanglement(orc):
 def test_permute_rejects_bad_index(orc):
     with pytest.raises(ValueError):
         orc.permute([1, 2, 3], [0, 1, 3])
+
+
+# ---------------------------------------------------------------------------
+# Corruption detection with all streams present (Remark 4)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M,w", [(3, 8), (4, 8), (3, 10)])
+def test_detect_exhaustive_single_stream_corruption(orc, M, w):
+    """Every tuple in the exact range: clean columns are never flagged;
+    altering any one stream by any of several amounts is always flagged."""
+    import itertools
+    l, k, _, D = orc.params(M, w)
+    vals = range(-D, D + 1)
+    d = np.array(list(itertools.product(vals, repeat=M)), dtype=np.int64).T
+    delta = orc.entangle(d, w, l, strict=False)
+    flags, rec = orc.detect(delta, w, l, D)
+    assert not flags.any() and rec.tolist() == d.tolist()
+    gen = synth.rng(M * w)
+    for q in range(M):
+        for _ in range(2):
+            e = gen.integers(1, 1 << w, size=d.shape[1])
+            bad = delta.copy()
+            bad[q] = [wrap(int(a) + int(b), w) for a, b in zip(bad[q], e)]
+            flags, _ = orc.detect(bad, w, l, D)
+            assert flags.all(), (q, int((~flags).sum()))
+
+
+def test_detect_flags_only_corrupted_columns(orc):
+    M, w = 5, 64
+    l, k, dp, de = orc.params(M, w)
+    gen = synth.rng(31)
+    d = synth.uniform_int(gen, (M, 1000), -dp, dp + 1)
+    delta = orc.entangle(d, w, l)
+    bad_cols = [3, 400, 999]
+    for i, n in enumerate(bad_cols):
+        delta[i % M, n] ^= 1 << (i * 7)
+    flags, _ = orc.detect(delta, w, l, dp)
+    assert np.flatnonzero(flags).tolist() == bad_cols
+
+
+# ---------------------------------------------------------------------------
+# Circular convolution, cross-correlation, inner product (Eq. 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,K", [(5, 1), (5, 5), (64, 17), (301, 64)])
+def test_circular_conv_is_aliased_linear_conv(orc, N, K):
+    """Circular convolution = the linear one folded modulo N (aliasing)."""
+    gen = synth.rng(N + K)
+    x = synth.uniform_int(gen, (N,), -999, 999)
+    g = synth.uniform_int(gen, (K,), -999, 999)
+    lin = np_conv(x, g)
+    folded = np.zeros(N, dtype=np.int64)
+    for n, v in enumerate(lin):
+        folded[n % N] += v
+    assert orc.conv_circular(x, g, 64).tolist() == folded.tolist()
+
+
+@pytest.mark.parametrize("N,K", [(1, 1), (7, 3), (100, 33)])
+def test_xcorr_matches_numpy_correlate(orc, N, K):
+    gen = synth.rng(N * 3 + K)
+    x = synth.uniform_int(gen, (N,), -999, 999)
+    g = synth.uniform_int(gen, (K,), -999, 999)
+    assert orc.xcorr(x, g, 64).tolist() == np.correlate(x, g, "full").tolist()
+
+
+def test_dot_matches_numpy(orc):
+    gen = synth.rng(4)
+    x = synth.uniform_int(gen, (3, 500), -(1 << 20), 1 << 20)
+    g = synth.uniform_int(gen, (500,), -(1 << 20), 1 << 20)
+    assert orc.dot(x, g, 64).tolist() == (x @ g).tolist()
+
+
+def test_other_ops_on_entangled_streams_recover(orc):
+    """Every op above is Z/2^w-linear in x, so recovery of its entangled
+    outputs gives the op on the raw inputs (Sec. II-B: any LSB op)."""
+    M, w = 4, 64
+    l, k, dp, _ = orc.params(M, w)
+    gen = synth.rng(12)
+    c = synth.uniform_int(gen, (M, 200), -(1 << 12), 1 << 12)
+    g = synth.uniform_int(gen, (40,), -(1 << 12), 1 << 12)
+    e = orc.entangle(c, w, l)
+    for op in (orc.conv_circular, orc.xcorr):
+        delta = op(e, g, w)
+        for r in range(M):
+            assert orc.recover(delta, w, l, r).tolist() == op(c, g, w).tolist()
+    gd = synth.uniform_int(gen, (200,), -(1 << 12), 1 << 12)
+    dots = orc.dot(e, gd, w)[:, None]
+    for r in range(M):
+        assert orc.recover(dots, w, l, r)[:, 0].tolist() == (c @ gd).tolist()
