@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-paper-shapes", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU oracle sample")
     return ap.parse_args()
@@ -433,6 +434,7 @@ def run_ne(args):
     clk = clocks.summary(t_start, t_end)
     del c_h, d_h, g_h
     small = bench_small(ne, synth, dev, stream)
+    paper = None if args.no_paper_shapes else bench_paper_shapes(ne, dev, stream)
     batch = None if args.no_batch else bench_batch(ne, synth, dev, stream)
     served = None if args.no_serve else bench_serve(dev)
     cpu = None
@@ -460,6 +462,7 @@ def run_ne(args):
             "gpu_launches": args.steps,
             "clocks": clk,
             "small": small,
+            "paper_shapes": paper,
             "batch": batch,
             "serve": served,
             "p99_ms_served": served["p99_ms"] if served else None,
@@ -512,6 +515,62 @@ def bench_small(ne, synth, dev, stream, reps=200):
     return {"workload": "M=3 int32 streams, N=4096, K=16, data/taps in "
                         "[-2^7,2^7), w=32 (l=11, k=10)",
             "us_per_job": 1e3 * t / reps, "w": p.w}
+
+
+def bench_paper_shapes(ne, dev, stream, reps=5):
+    """The paper's experiment shapes (Sec. V): M in {3, 8} streams of
+    N = 10^6 samples, K in {100, 1000, 4500} taps, no failure; integer data
+    and taps in [-2^14, 2^14) in 64-bit words.  Per shape: the fused
+    protected convolution, the unprotected one and the checksum ABFT
+    (checksum stream + M+1 convolutions + recovery), with overheads."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    N = 1_000_000
+    b = 1 << 14
+    rows = []
+    for M in (3, 8):
+        p = ne.ne_params(M, 64)
+        c = torch.empty((M, N), dtype=torch.int64, device=dev).random_(
+            -b, b, generator=gen)
+        cs = torch.empty((M + 1, N), dtype=torch.int64, device=dev)
+        cs[:M] = c
+        for K in (100, 1000, 4500):
+            g = torch.empty(K, dtype=torch.int32, device=dev).random_(
+                -b, b, generator=gen)
+            Nout = N + K - 1
+            d = torch.empty((M, Nout), dtype=torch.int64, device=dev)
+            dcs = torch.empty((M + 1, Nout), dtype=torch.int64, device=dev)
+            ws = torch.empty(ne.ne_protected_conv_ws_bytes(M, N, K),
+                             dtype=torch.uint8, device=dev)
+
+            def prot(i):
+                ne.ne_protected_conv(c, g, d, l=p.l, c_range=(-b, b - 1),
+                                     max_abs_g=b, ws=ws)
+
+            def unprot(i):
+                ne.ne_conv(c, g, d, x_range=(-b, b - 1))
+
+            def checksum(i):
+                ne.ne_checksum(cs[:M], cs[M])
+                ne.ne_conv(cs, g, dcs, x_range=(-M * b, M * (b - 1)))
+                ne.ne_checksum_recover(dcs[:M], dcs[M], dcs[0], f=0)
+
+            res = {}
+            for name, fn in (("protected", prot), ("unprotected", unprot),
+                             ("checksum", checksum)):
+                fn(0)
+                t, _ = timed(fn, reps, 1, stream)
+                res[name] = t / reps
+            rows.append({
+                "M": M, "N": N, "K": K, "l": p.l,
+                "ms": res,
+                "ne_overhead_pct": 100 * (res["protected"] / res["unprotected"] - 1),
+                "checksum_overhead_pct": 100 * (res["checksum"] / res["unprotected"] - 1),
+                "protected_gops": 2 * M * N * K / (res["protected"] * 1e-3) / 1e9})
+            del d, dcs, ws, g
+        del c, cs
+    return rows
 
 
 def bench_batch(ne, synth, dev, stream):

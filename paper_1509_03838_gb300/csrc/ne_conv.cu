@@ -547,6 +547,11 @@ conv_cluster_kernel(const ConvArgs p) {
   }
 }
 
+// Tap counts at which the default form changes (use_cluster()).
+constexpr int CLUSTER_K_MAX_WIDE = 90;
+constexpr int CLUSTER_K_MAX_SPLIT = 208;
+constexpr int CLUSTER_K_MIN_I32_M3 = 48;
+
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
@@ -659,15 +664,40 @@ int launch_cluster(const ConvArgs& a, bool vec, cudaStream_t s) {
              : launch_cluster_v<W, MODE, false>(a, s);
 }
 
-// The fused protected convolution's form: thread-block clusters (M <= 8,
-// the default) or the cross-block arrival-word protocol (any M, or
-// NE_PROT_KERNEL=arrival).
-inline bool use_cluster(int M) {
-  static const bool off = [] {
+// The fused protected convolution's form: thread-block clusters or the
+// cross-block arrival-word protocol.  Clusters deliver delta through shared
+// memory and win while a tile's convolution is short enough that the
+// extractor's round trip through L2 shows; once it is longer, clusters'
+// co-scheduling (M blocks at once in one GPC) costs more than that round
+// trip.  Crossovers measured on GB300 (N = 2^21, M = 3..8): 64-bit words
+// with one 32x32->64 multiply-add per tap, about K = 90 taps; with the split
+// 64-bit product, about K = 210; 32-bit words, clusters win only for M = 3
+// from K = 48 on (shorter tiles, and more blocks per cluster, favour the
+// arrival words); at M = 8 the arrival words are never slower.
+// NE_PROT_KERNEL=cluster or =arrival forces one form (clusters only for
+// 3 <= M <= 8).
+enum ProtForm { FORM_AUTO, FORM_CLUSTER, FORM_ARRIVAL };
+
+inline ProtForm forced_form() {
+  static const ProtForm f = [] {
     const char* e = getenv("NE_PROT_KERNEL");
-    return e && strcmp(e, "arrival") == 0;
+    if (e && strcmp(e, "arrival") == 0) return FORM_ARRIVAL;
+    if (e && strcmp(e, "cluster") == 0) return FORM_CLUSTER;
+    return FORM_AUTO;
   }();
-  return !off && M >= 3 && M <= 8;
+  return f;
+}
+
+inline bool use_cluster(int M, int K, int w, int mode) {
+  if (M < 3 || M > 8) return false;
+  switch (forced_form()) {
+    case FORM_CLUSTER: return true;
+    case FORM_ARRIVAL: return false;
+    default: break;
+  }
+  if (M == 8) return false;
+  if (w == 32) return M == 3 && K >= CLUSTER_K_MIN_I32_M3;
+  return K <= (mode == MODE_SPLIT ? CLUSTER_K_MAX_SPLIT : CLUSTER_K_MAX_WIDE);
 }
 
 int dispatch_cluster(const ConvArgs& a, int w, int mode, bool vec,
@@ -863,7 +893,6 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const size_t need_ws = ne_protected_conv_ws_bytes(M, N, K);
   if (!ws || ws_bytes < need_ws) return NE_ERR_NOMEM;
   cudaStream_t s = (cudaStream_t)stream;
-  const bool cluster = use_cluster(M);
   ConvArgs a{};
   a.x = c;
   a.ldx = ldc;
@@ -887,7 +916,7 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
-  if (cluster) {
+  if (use_cluster(M, K, w, mode)) {
     if (dispatch_cluster(a, w, mode, vec, s) == NE_OK) return NE_OK;
     // a refused cluster launch (configuration error, not sticky): clear it
     // and take the arrival-word form

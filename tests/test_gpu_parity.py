@@ -281,6 +281,25 @@ def test_protected_conv_repeat_reuses_workspace(ne, orc):
         assert np.array_equal(host(d), plain)
 
 
+@pytest.mark.parametrize("form", ["cluster", "arrival"])
+def test_protected_conv_forced_forms(ne, form):
+    """Both fused forms (thread-block clusters with shared-memory delivery,
+    and per-tile arrival words) on every protected case and failure mode.
+    The default picks one form by M and K; NE_PROT_KERNEL forces one, and
+    is read once per process, hence the child pytest run."""
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ, NE_PROT_KERNEL=form)
+    out = subprocess.run(
+        [sys.executable, "-m", "pytest", __file__, "-q", "-x", "-m", "gpu",
+         "-p", "no:cacheprovider", "-k",
+         "protected_conv_all_failures or protected_conv_repeat"],
+        env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout[-3000:] + out.stderr[-2000:]
+    assert " passed" in out.stdout
+
+
 def test_protected_conv_range_error(ne):
     w, M = 32, 3
     p = ne.ne_params(M, w)
