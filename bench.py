@@ -476,8 +476,8 @@ def run_ne(args):
 # the kernel sources it was taken on (their SHA-256 is checked at run time).
 TRAFFIC_CAPTURE = {
     "sources_sha256":
-        "cf2c9b0a55a618b46c8b3e306dd6156377ae1a13c4383db8944d44591ef8ed67",
-    "bytes": 134309376 + 86481920,  # profiles/conv_cluster_protected_M4_N2e22_K64.md
+        "9fe898d99f8a508409983efc82f26a4704a11a82f73c60c7237bc11614ee845a",
+    "bytes": 134311936 + 86469888,  # profiles/conv_cluster_protected_M4_N2e22_K64.md
 }
 CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_recover.cuh",
                 "ne_common.cuh"]

@@ -673,7 +673,10 @@ int launch_cluster(const ConvArgs& a, bool vec, cudaStream_t s) {
 // with one 32x32->64 multiply-add per tap, about K = 90 taps; with the split
 // 64-bit product, about K = 210; 32-bit words, clusters win only for M = 3
 // from K = 48 on (shorter tiles, and more blocks per cluster, favour the
-// arrival words); at M = 8 the arrival words are never slower.
+// arrival words); at M = 8 the arrival words are never slower.  A job whose
+// blocks all fit on the device at once (at most 4 per SM) takes clusters
+// whatever K is: nothing waits to be co-scheduled, and the arrival words'
+// workspace clear would be a second launch on a latency-bound call.
 // NE_PROT_KERNEL=cluster or =arrival forces one form (clusters only for
 // 3 <= M <= 8).
 enum ProtForm { FORM_AUTO, FORM_CLUSTER, FORM_ARRIVAL };
@@ -688,13 +691,14 @@ inline ProtForm forced_form() {
   return f;
 }
 
-inline bool use_cluster(int M, int K, int w, int mode) {
+inline bool use_cluster(int M, int K, int w, int mode, int64_t ntiles) {
   if (M < 3 || M > 8) return false;
   switch (forced_form()) {
     case FORM_CLUSTER: return true;
     case FORM_ARRIVAL: return false;
     default: break;
   }
+  if (ntiles * M <= 4LL * sm_count()) return true;
   if (M == 8) return false;
   if (w == 32) return M == 3 && K >= CLUSTER_K_MIN_I32_M3;
   return K <= (mode == MODE_SPLIT ? CLUSTER_K_MAX_SPLIT : CLUSTER_K_MAX_WIDE);
@@ -916,7 +920,7 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
-  if (use_cluster(M, K, w, mode)) {
+  if (use_cluster(M, K, w, mode, a.ntiles)) {
     if (dispatch_cluster(a, w, mode, vec, s) == NE_OK) return NE_OK;
     // a refused cluster launch (configuration error, not sticky): clear it
     // and take the arrival-word form

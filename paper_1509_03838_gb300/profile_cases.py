@@ -10,6 +10,10 @@ data and taps, 64-bit words, the benchmark's workload):
   entangle       out-of-place entanglement
   recover        recovery of all streams with stream 1 missing
   checksum       checksum stream of the ABFT baseline
+  protected_m8   fused protected conv at the paper's M = 8, N = 10^6,
+                 K = 1000 shape (data and taps in [-2^14, 2^14), no
+                 failure): the arrival-word form
+  conv_m8        unprotected conv of the same data (declared range)
 """
 from __future__ import annotations
 
@@ -49,8 +53,22 @@ def main() -> int:
         "recover": lambda: ne.ne_recover(d, d, l=p.l, failed=1),
         "checksum": lambda: ne.ne_checksum(c, r),
     }
+    if a.case in ("protected_m8", "conv_m8"):
+        gen = synth.rng(8)
+        b8, M8, N8, K8 = 1 << 14, 8, 1_000_000, 1000
+        c8 = torch.from_numpy(synth.uniform_int(gen, (M8, N8), -b8, b8)).to(dev)
+        g8 = torch.from_numpy(
+            synth.uniform_int(gen, (K8,), -b8, b8).astype(np.int32)).to(dev)
+        d8 = torch.empty((M8, N8 + K8 - 1), dtype=torch.int64, device=dev)
+        ws8 = torch.empty(ne.ne_protected_conv_ws_bytes(M8, N8, K8),
+                          dtype=torch.uint8, device=dev)
+        l8 = ne.ne_params(M8, 64).l
+        ops["protected_m8"] = lambda: ne.ne_protected_conv(
+            c8, g8, d8, l=l8, c_range=(-b8, b8 - 1), max_abs_g=b8, ws=ws8)
+        ops["conv_m8"] = lambda: ne.ne_conv(c8, g8, d8, x_range=(-b8, b8 - 1))
     if a.case not in ops:
-        raise SystemExit(f"unknown case {a.case}; one of {sorted(ops)}")
+        raise SystemExit(f"unknown case {a.case}; one of "
+                         f"{sorted(ops) + ['conv_m8', 'protected_m8']}")
     for _ in range(a.reps):
         ops[a.case]()
     torch.cuda.synchronize()
