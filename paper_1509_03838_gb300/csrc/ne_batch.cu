@@ -131,18 +131,15 @@ __device__ __noinline__ void batch_unit(const JobDev& jb, int64_t local,
   }
   unsigned long long a64[CONV_R];
   unsigned a32[CONV_R];
-  conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32);
-  W out[CONV_R];
-  const int64_t nt = n0 + (int64_t)threadIdx.x * CONV_R;
-#pragma unroll
-  for (int a = 0; a < CONV_R; ++a) {
-    if constexpr (MODE == MODE_WIDE) {
-      if (jb.bias != 0)
-        a64[a] += edge ? shift_correction(jb.bias, s_pref, nt + a, jb.N, jb.K)
-                       : shift_c;
-    }
-    out[a] = combine<W, MODE>(a64[a], a32[a]);
+  conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32, shift_c);
+  if constexpr (MODE == MODE_WIDE) {
+    if (jb.bias != 0 && edge)
+      edge_shift(a64, jb.bias, s_pref, n0 + (int64_t)threadIdx.x * CONV_R,
+                 jb.N, jb.K);
   }
+  W out[CONV_R];
+#pragma unroll
+  for (int a = 0; a < CONV_R; ++a) out[a] = combine<W, MODE>(a64[a], a32[a]);
   if (jb.fail_mode == NE_FAIL_DROP && m == jb.failed) {
     __syncthreads();  // operands are reused by the next unit
     return;           // computed, but the result is lost

@@ -190,18 +190,15 @@ conv_simple_kernel(const ConvArgs p) {
 
   unsigned long long a64[CONV_R];
   unsigned a32[CONV_R];
-  conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32);
-  W out[CONV_R];
-  const int64_t nt = n0 + (int64_t)threadIdx.x * CONV_R;
-#pragma unroll
-  for (int a = 0; a < CONV_R; ++a) {
-    if constexpr (MODE == MODE_WIDE) {
-      if (p.bias != 0)
-        a64[a] += edge ? shift_correction(p.bias, s_pref, nt + a, p.N, p.K)
-                       : shift_c;
-    }
-    out[a] = combine<W, MODE>(a64[a], a32[a]);
+  conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32, shift_c);
+  if constexpr (MODE == MODE_WIDE) {
+    if (p.bias != 0 && edge)
+      edge_shift(a64, p.bias, s_pref, n0 + (int64_t)threadIdx.x * CONV_R,
+                 p.N, p.K);
   }
+  W out[CONV_R];
+#pragma unroll
+  for (int a = 0; a < CONV_R; ++a) out[a] = combine<W, MODE>(a64[a], a32[a]);
   W* ybase = reinterpret_cast<W*>(p.y);
   if constexpr (!PROT) {
     write_tile<W>(ybase + (int64_t)m * p.ldy, n0, p.Nout, out, s_out);
@@ -490,12 +487,16 @@ conv_cluster_kernel(const ConvArgs p) {
     }
     unsigned long long a64[CONV_R];
     unsigned a32[CONV_R];
-    conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32);
+    conv_compute<MODE>(s_lo, s_hi, s_taps, Kp, a64, a32, shift_c);
+    if constexpr (MODE == MODE_WIDE) {
+      if (p.bias != 0 && edge)
+        edge_shift(a64, p.bias, s_pref, n0 + (int64_t)threadIdx.x * CONV_R,
+                   p.N, p.K);
+    }
     cluster_wait();  // phase 1 complete: every peer block is resident
     if (m != r) {
       // push delta_m: column col goes to extractor e = col / per, row q
       const int q = (m - r - 1 + 2 * M) % M;
-      const int64_t nt = n0 + (int64_t)threadIdx.x * CONV_R;
       int col = threadIdx.x * CONV_R;
       int e = min(col / per, M - 2);  // threads past the tail store nothing
       int lc = col - e * per;
@@ -508,11 +509,6 @@ conv_cluster_kernel(const ConvArgs p) {
       W* dst = slot_of(e);
 #pragma unroll
       for (int a = 0; a < CONV_R; ++a) {
-        if constexpr (MODE == MODE_WIDE) {
-          if (p.bias != 0)
-            a64[a] += edge ? shift_correction(p.bias, s_pref, nt + a, p.N, p.K)
-                           : shift_c;
-        }
         if (col < span) {
           if (lc == per) {  // next extractor's columns
             ++e;

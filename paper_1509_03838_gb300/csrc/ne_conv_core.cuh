@@ -63,19 +63,22 @@ __device__ __forceinline__ void split_word(W v, int& lo, int& hi) {
 
 // Register-blocked sliding-window convolution of a staged tile: output a of
 // this thread (n = n0 + tid*R + a) accumulates sum_t s[tid*R + a - t + Kp]
-// * g[t].  Each 16-tap chunk loads a 28-sample window (7 or 14 128-bit
-// shared loads) and 16 taps (4 broadcast loads) for 192 multiply-adds.
+// * g[t] onto the start value init (the range shift's b * sum g on interior
+// tiles, which thereby costs nothing).  Each 16-tap chunk loads a 28-sample
+// window (7 or 14 128-bit shared loads) and 16 taps (4 broadcast loads) for
+// 192 multiply-adds.
 template <int MODE>
 __device__ __forceinline__ void conv_compute(const int* __restrict__ s_lo,
                                              const int* __restrict__ s_hi,
                                              const int* __restrict__ s_taps,
                                              int Kp,
                                              unsigned long long (&a64)[CONV_R],
-                                             unsigned (&a32)[CONV_R]) {
+                                             unsigned (&a32)[CONV_R],
+                                             unsigned long long init = 0ull) {
   const int tid = threadIdx.x;
 #pragma unroll
   for (int a = 0; a < CONV_R; ++a) {
-    a64[a] = 0ull;
+    a64[a] = init;
     a32[a] = 0u;
   }
 #pragma unroll 1
@@ -213,6 +216,20 @@ __device__ __forceinline__ long long tap_total(const int* __restrict__ s_taps,
   for (int w = 0; w < T / 32; ++w) tot += s_warp[w];
   __syncthreads();
   return tot;
+}
+
+// Range shift of a tile at either end of the output (block-uniform call):
+// each of this thread's outputs n = nt + a gets its own b * G(n).
+__device__ __forceinline__ unsigned long long shift_correction(
+    long long bias, const long long* __restrict__ s_pref, int64_t n, int64_t N,
+    int K);
+__device__ __forceinline__ void edge_shift(unsigned long long (&a64)[CONV_R],
+                                           long long bias,
+                                           const long long* __restrict__ s_pref,
+                                           int64_t nt, int64_t N, int K) {
+#pragma unroll
+  for (int a = 0; a < CONV_R; ++a)
+    a64[a] += shift_correction(bias, s_pref, nt + a, N, K);
 }
 
 // b * G(n) modulo 2^64 for output n of an N-sample input and K taps.
