@@ -398,8 +398,9 @@ __device__ __forceinline__ void cluster_wait() {
 }
 
 // Receive buffer: M-1 rows (row q = stream (r + 1 + q) mod M) of
-// per = ceil(TILE / (M-1)) columns each, padded one word per 16:
-// (M-1) pad16(per) <= TILE + TILE/16 + 16 for every M in [3, 8].
+// per = ceil(TILE / (M-1)) columns each, padded two words per 32:
+// (M-1) pad2of32(per) <= 1632 <= TILE + TILE/16 + 16 for every M in [3, 8]
+// (the largest, 1632, at M = 3, 4, 5 and 7).
 __host__ __device__ constexpr int recv_words() {
   return CONV_TILE + CONV_TILE / 16 + 16;
 }
@@ -504,21 +505,45 @@ conv_cluster_kernel(const ConvArgs p) {
       auto slot_of = [&](int ee) -> W* {
         const unsigned rk = (unsigned)(ee < r ? ee : ee + 1);
         W* base = rk == (unsigned)m ? s_recv : cluster.map_shared_rank(s_recv, rk);
-        return base + (size_t)q * pad16(per);
+        return base + (size_t)q * pad2of32(per);
       };
       W* dst = slot_of(e);
+      if (sizeof(W) == 8 && (per & 1) == 0) {
+        // 16-byte pairs: col and lc stay even and per is even, so a pair
+        // never straddles two extractors, and pad2of32 keeps it aligned
+        // (rows start at multiples of pad2of32(per), an even count).  The
+        // second word of a pair at the tail may lie past span: it stays in
+        // the extractor's row and is never read.
 #pragma unroll
-      for (int a = 0; a < CONV_R; ++a) {
-        if (col < span) {
-          if (lc == per) {  // next extractor's columns
-            ++e;
-            lc = 0;
-            dst = slot_of(e);
+        for (int a = 0; a < CONV_R; a += 2) {
+          if (col < span) {
+            if (lc == per) {  // next extractor's columns
+              ++e;
+              lc = 0;
+              dst = slot_of(e);
+            }
+            longlong2 v;
+            v.x = (long long)combine<W, MODE>(a64[a], a32[a]);
+            v.y = (long long)combine<W, MODE>(a64[a + 1], a32[a + 1]);
+            *reinterpret_cast<longlong2*>(dst + pad2of32(lc)) = v;
           }
-          dst[pad16(lc)] = combine<W, MODE>(a64[a], a32[a]);
+          col += 2;
+          lc += 2;
         }
-        ++col;
-        ++lc;
+      } else {
+#pragma unroll
+        for (int a = 0; a < CONV_R; ++a) {
+          if (col < span) {
+            if (lc == per) {  // next extractor's columns
+              ++e;
+              lc = 0;
+              dst = slot_of(e);
+            }
+            dst[pad2of32(lc)] = combine<W, MODE>(a64[a], a32[a]);
+          }
+          ++col;
+          ++lc;
+        }
       }
     }
   } else {
@@ -533,12 +558,12 @@ conv_cluster_kernel(const ConvArgs p) {
     const int c1 = min(span, c0 + per);
     W* dbase = reinterpret_cast<W*>(p.y) + n0 + c0;
     switch (M) {
-      case 3: cluster_recover<W, 3>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
-      case 4: cluster_recover<W, 4>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
-      case 5: cluster_recover<W, 5>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
-      case 6: cluster_recover<W, 6>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
-      case 7: cluster_recover<W, 7>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
-      default: cluster_recover<W, 8>(s_recv, pad16(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      case 3: cluster_recover<W, 3>(s_recv, pad2of32(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      case 4: cluster_recover<W, 4>(s_recv, pad2of32(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      case 5: cluster_recover<W, 5>(s_recv, pad2of32(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      case 6: cluster_recover<W, 6>(s_recv, pad2of32(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      case 7: cluster_recover<W, 7>(s_recv, pad2of32(per), r, dbase, p.ldy, c1 - c0, p.l); break;
+      default: cluster_recover<W, 8>(s_recv, pad2of32(per), r, dbase, p.ldy, c1 - c0, p.l); break;
     }
   }
 }

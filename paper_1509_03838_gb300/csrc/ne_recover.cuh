@@ -193,6 +193,13 @@ __device__ __forceinline__ void recover_columns_batched(
 // (conflict-free strided parking of per-thread output runs).
 __host__ __device__ __forceinline__ int pad16(int j) { return j + (j >> 4); }
 
+// Slot of word j in a receive tile padded with two words per 32: even words
+// stay on even slots, so a pair (j, j+1) with j even is one aligned 16-byte
+// slot of 64-bit words.
+__host__ __device__ __forceinline__ int pad2of32(int j) {
+  return j + ((j >> 5) << 1);
+}
+
 template <typename W, int NV, int MAXC, bool PADDED>
 __device__ __forceinline__ void recover_columns_to(
     const W* const (&src)[MAXC], const int (&drow)[MAXC + 1],
@@ -250,8 +257,8 @@ __device__ __forceinline__ void recover_columns_to(
 
 // Compile-time-M form of recover_columns_to for the fused kernels: the
 // M-1 source rows src[q] (row (r + 1 + q) mod M) are local shared-memory
-// tiles padded one word per 16; outputs go to rows drow[] of d.  With M a
-// template constant no predicated-off row work is issued.
+// tiles padded two words per 32 (pad2of32); outputs go to rows drow[] of d.
+// With M a template constant no predicated-off row work is issued.
 template <typename W, int MM, int NV>
 __device__ __forceinline__ void recover_cols_m(const W* __restrict__ recv,
                                                int rstride,
@@ -268,7 +275,8 @@ __device__ __forceinline__ void recover_cols_m(const W* __restrict__ recv,
   for (int q = 0; q < MM - 1; ++q) {
 #pragma unroll
     for (int i = 0; i < NV; ++i)
-      cache[q][i] = live[i] ? recv[q * rstride + pad16(n + i * cstride)] : (W)0;
+      cache[q][i] = live[i] ? recv[q * rstride + pad2of32(n + i * cstride)]
+                            : (W)0;
   }
   W dcur[NV];
 #pragma unroll
