@@ -33,6 +33,10 @@
  *      larger l.  This reproduces every row of Table I.
  *   R5 (conv) the LSB convolution is the full linear convolution
  *      y[n] = sum_j x[j] g[n-j], 0 <= n < N+K-1, zero outside the inputs.
+ *   R6 (Sec. IV, GEMM) the stream-by-stream sum of products multiplies
+ *      each stream's block by the matrix kernel from the right,
+ *      y_m = x_m g; the paper's N x N blocks are the square case of an
+ *      R x S block and an S x T kernel.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -427,4 +431,45 @@ int64_t orc_dot(const int64_t *x, const int64_t *g, int64_t N, int w,
     for (int64_t n = 0; n < N; ++n) acc += (i128)x[n] * (i128)g[n];
     *y = (int64_t)reduce_bits(acc, w);
     return fits_bits(acc, w) ? 0 : 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Matrix products (Sec. IV: stream-by-stream sum of products with a  */
+/* matrix kernel; Sec. I: inner and outer vector products)             */
+/* ------------------------------------------------------------------ */
+
+/* One stream's matrix product y = x g: x is R x S (row stride ldx), g is
+ * S x T (row stride ldg), y is R x T (row stride ldy); every entry is the
+ * exact sum over s of x[i][s] g[s][j], stored modulo 2^w. */
+int64_t orc_gemm(const int64_t *x, int64_t R, int64_t S, int64_t ldx,
+                 const int64_t *g, int64_t T, int64_t ldg, int w,
+                 int64_t *y, int64_t ldy)
+{
+    int64_t overflow = 0;
+    for (int64_t i = 0; i < R; ++i) {
+        for (int64_t j = 0; j < T; ++j) {
+            i128 acc = 0;
+            for (int64_t s = 0; s < S; ++s)
+                acc += (i128)x[i * ldx + s] * (i128)g[s * ldg + j];
+            if (!fits_bits(acc, w)) ++overflow;
+            y[i * ldy + j] = (int64_t)reduce_bits(acc, w);
+        }
+    }
+    return overflow;
+}
+
+/* Outer product of one stream x (N samples) with the kernel vector g
+ * (P samples): y[i][j] = x[i] g[j], y row stride ldy, modulo 2^w. */
+int64_t orc_outer(const int64_t *x, int64_t N, const int64_t *g, int64_t P,
+                  int w, int64_t *y, int64_t ldy)
+{
+    int64_t overflow = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        for (int64_t j = 0; j < P; ++j) {
+            i128 v = (i128)x[i] * (i128)g[j];
+            if (!fits_bits(v, w)) ++overflow;
+            y[i * ldy + j] = (int64_t)reduce_bits(v, w);
+        }
+    }
+    return overflow;
 }

@@ -89,6 +89,11 @@ def _load():
             lib.orc_xcorr.restype = i64
             lib.orc_dot.argtypes = [_i64p, _i64p, i64, i32, _i64p]
             lib.orc_dot.restype = i64
+            lib.orc_gemm.argtypes = [_i64p, i64, i64, i64, _i64p, i64, i64,
+                                     i32, _i64p, i64]
+            lib.orc_gemm.restype = i64
+            lib.orc_outer.argtypes = [_i64p, i64, _i64p, i64, i32, _i64p, i64]
+            lib.orc_outer.restype = i64
             _lib = lib
     return _lib
 
@@ -334,3 +339,49 @@ def dot(x, g, w: int):
         _load().orc_dot(_p(xm), _p(g), xm.shape[0], w, _p(v))
         out[m] = v[0]
     return out[0] if x.ndim == 1 else out
+
+
+def gemm(x, g, w: int, strict: bool = True):
+    """Stream-by-stream matrix product (Sec. IV): x is [M][R][S] (or one
+    [R][S] matrix), g is [S][T]; returns [M][R][T] (or [R][T]) with every
+    entry sum_s x[m][i][s] g[s][j] modulo 2^w."""
+    x = np.asarray(x, dtype=np.int64)
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.int64))
+    one = x.ndim == 2
+    xs = x[None] if one else x
+    Mm, R, S = xs.shape
+    if g.shape[0] != S:
+        raise ValueError("inner dimensions differ")
+    T = g.shape[1]
+    out = np.empty((Mm, R, T), dtype=np.int64)
+    ov = 0
+    for m in range(Mm):
+        xm = np.ascontiguousarray(xs[m])
+        ym = np.empty((R, T), dtype=np.int64)
+        ov += _load().orc_gemm(_p(xm), R, S, S, _p(g), T, T, w, _p(ym), T)
+        out[m] = ym
+    if strict and ov:
+        raise OracleOverflow(f"{ov} outputs exceed {w} bits")
+    return out[0] if one else out
+
+
+def outer(x, g, w: int, strict: bool = True):
+    """Outer product of each stream with g (Sec. I): x is [M][N] (or [N]),
+    g is [P]; returns [M][N][P] (or [N][P]), y[m][i][j] = x[m][i] g[j]
+    modulo 2^w."""
+    x = _arr(x)
+    g = _arr(g)
+    one = x.ndim == 1
+    xs = x[None, :] if one else x
+    Mm, N = xs.shape
+    P = g.shape[0]
+    out = np.empty((Mm, N, P), dtype=np.int64)
+    ov = 0
+    for m in range(Mm):
+        xm = np.ascontiguousarray(xs[m])
+        ym = np.empty((N, P), dtype=np.int64)
+        ov += _load().orc_outer(_p(xm), N, _p(g), P, w, _p(ym), P)
+        out[m] = ym
+    if strict and ov:
+        raise OracleOverflow(f"{ov} outputs exceed {w} bits")
+    return out[0] if one else out

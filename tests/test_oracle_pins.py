@@ -489,3 +489,77 @@ def test_other_ops_on_entangled_streams_recover(orc):
     dots = orc.dot(e, gd, w)[:, None]
     for r in range(M):
         assert orc.recover(dots, w, l, r)[:, 0].tolist() == (c @ gd).tolist()
+
+
+# ---------------------------------------------------------------------------
+# Matrix products (Sec. IV stream-by-stream GEMM; Sec. I outer product)
+# ---------------------------------------------------------------------------
+
+def test_gemm_matches_numpy_matmul(orc):
+    """Small entries keep numpy's int64 matmul exact."""
+    gen = synth.rng(21)
+    x = synth.uniform_int(gen, (3, 17, 23), -(1 << 20), 1 << 20)
+    g = synth.uniform_int(gen, (23, 11), -(1 << 20), 1 << 20)
+    assert np.array_equal(orc.gemm(x, g, 64), x @ g)
+
+
+@pytest.mark.parametrize("w", [32, 64])
+def test_gemm_wraps_like_python_integers(orc, w):
+    """Entries large enough to overflow w bits: each output equals the exact
+    Python-integer sum reduced to a signed w-bit word."""
+    gen = synth.rng(w)
+    b = 1 << (w // 2 + 3)
+    x = synth.uniform_int(gen, (5, 7), -b, b)
+    g = synth.uniform_int(gen, (7, 4), -b, b)
+    got = orc.gemm(x, g, w, strict=False)
+    for i in range(5):
+        for j in range(4):
+            exact = sum(int(x[i, s]) * int(g[s, j]) for s in range(7))
+            assert int(got[i, j]) == wrap(exact, w)
+    with pytest.raises(orc.OracleOverflow):
+        orc.gemm(x, g, w)
+
+
+def test_gemm_special_cases(orc):
+    """Identity kernel returns the block; a one-column kernel is the inner
+    product of every row with it."""
+    gen = synth.rng(22)
+    x = synth.uniform_int(gen, (9, 6), -1000, 1000)
+    assert np.array_equal(orc.gemm(x, np.eye(6, dtype=np.int64), 64), x)
+    v = synth.uniform_int(gen, (6,), -1000, 1000)
+    assert orc.gemm(x, v[:, None], 64)[:, 0].tolist() == orc.dot(x, v, 64).tolist()
+
+
+def test_outer_matches_numpy(orc):
+    gen = synth.rng(23)
+    x = synth.uniform_int(gen, (3, 40), -(1 << 25), 1 << 25)
+    g = synth.uniform_int(gen, (17,), -(1 << 25), 1 << 25)
+    got = orc.outer(x, g, 64)
+    for m in range(3):
+        assert np.array_equal(got[m], np.outer(x[m], g))
+
+
+def test_matrix_products_on_entangled_streams_recover(orc):
+    """GEMM and outer product are Z/2^w-linear in the stream, so on entangled
+    blocks delta_m = D_m + 2^l D_{m-1} (Eq. 6 applied to the outputs), and
+    recovery from any M-1 of them gives the plain products."""
+    M, w = 4, 64
+    l, k, dp, _ = orc.params(M, w)
+    gen = synth.rng(24)
+    c = synth.uniform_int(gen, (M, 6, 9), -(1 << 12), 1 << 12)
+    g = synth.uniform_int(gen, (9, 5), -(1 << 12), 1 << 12)
+    e = orc.entangle(c.reshape(M, -1), w, l).reshape(c.shape)
+    D = c @ g
+    delta = orc.gemm(e, g, w)
+    for m in range(M):
+        expect = wrap_arr(D[m].astype(object) + (D[m - 1].astype(object) << l), w)
+        assert delta[m].tolist() == expect.tolist()
+    for r in range(M):
+        rec = orc.recover(delta.reshape(M, -1), w, l, r).reshape(D.shape)
+        assert np.array_equal(rec, D)
+    v = synth.uniform_int(gen, (13,), -(1 << 12), 1 << 12)
+    x = synth.uniform_int(gen, (M, 8), -(1 << 12), 1 << 12)
+    ov = orc.outer(orc.entangle(x, w, l), v, w).reshape(M, -1)
+    plain = np.stack([np.outer(x[m], v) for m in range(M)]).reshape(M, -1)
+    for r in range(M):
+        assert np.array_equal(orc.recover(ov, w, l, r), plain)
