@@ -252,6 +252,78 @@ int ne_protected_conv(const void *c, int64_t ldc, int M, int64_t N,
 /* Workspace bytes ne_protected_conv needs for (M, N, K). Host-only. */
 size_t ne_protected_conv_ws_bytes(int M, int64_t N, int K);
 
+/*
+ * ne_gemm -- stream-by-stream matrix product (Sec. IV: each stream's block
+ * times one matrix kernel; cost M R S T multiply-adds): for every stream m
+ * whose bit is set in live_mask, y_m = x_m g modulo 2^w, every entry the
+ * sum over s < S of x_m[i][s] g[s][j].  The product is Z/2^w-linear in
+ * x_m, so on entangled blocks (ne_entangle over the M blocks viewed as rows
+ * of R*S words) the outputs are entangled and recover with ne_recover.
+ *   x: M blocks of R x S words (w bits), block m at x + m*sx words, rows ldx
+ *      words apart (ldx >= S, sx >= R*ldx);
+ *   g: S x T int32 kernel, rows ldg apart (ldg >= T);
+ *   y: M blocks of R x T words, block m at y + m*sy, rows ldy apart
+ *      (ldy >= T, sy >= R*ldy); must not overlap x.  Blocks of dead streams
+ *      are not written.
+ *   [x_min, x_max]: declared range of x's values (x_min > x_max: unknown);
+ *      picks the arithmetic as in ne_conv (a span of at most 2^32 values
+ *      takes one 32x32->64 multiply-add per product).
+ * R = 0 or T = 0 is a no-op (null pointers allowed); S = 0 with R, T > 0 is
+ * NE_ERR_INVALID_ARG.  Caller owns every buffer; nothing is allocated.
+ */
+int ne_gemm(const void *x, int64_t ldx, int64_t sx, int M, int64_t R,
+            int64_t S, const int32_t *g, int64_t ldg, int64_t T, void *y,
+            int64_t ldy, int64_t sy, int w, int64_t x_min, int64_t x_max,
+            uint32_t live_mask, void *stream);
+
+/*
+ * ne_protected_gemm -- the protected matrix product: entangle-on-load of
+ * the M raw blocks (Eq. 6 applied elementwise as each block is read),
+ * ne_gemm of every entangled block with failure injection, then recovery
+ * of all M products from the M-1 delivered ones (Eq. 16-19) in place.
+ * Two launches on `stream` (the product; the recovery, which is
+ * bandwidth-bound and small next to the M R S T multiply-adds).
+ *   c: M raw blocks (ldc, sc as x of ne_gemm); g: S x T int32 (ldg);
+ *   d: M output blocks of R x T words with contiguous rows (row stride T),
+ *      block m at d + m*sd (sd >= R*T); receives the true products
+ *      D_m = c_m g; must not overlap c.
+ *   [c_min, c_max], max_abs_g: declared ranges; NE_ERR_RANGE if
+ *      S * max|c| * max_abs_g exceeds the exact output range for (M, w, l)
+ *      or max|c| (2^l + 1) does not fit w signed bits.
+ *   failed, fail_mode: as ne_protected_conv (NE_FAIL_SKIP: stream `failed`
+ *      is never computed; NE_FAIL_DROP: computed, then not read).
+ */
+int ne_protected_gemm(const void *c, int64_t ldc, int64_t sc, int M,
+                      int64_t R, int64_t S, const int32_t *g, int64_t ldg,
+                      int64_t T, int w, int l, int64_t c_min, int64_t c_max,
+                      int64_t max_abs_g, int failed, int fail_mode, void *d,
+                      int64_t sd, void *stream);
+
+/*
+ * ne_outer -- outer vector product of every live stream with the kernel
+ * vector g (Sec. I lists outer products among the sesquilinear LSB ops):
+ * y_m[i][j] = x_m[i] g[j] modulo 2^w.
+ *   x: M rows of N words (ldx >= N); g: P int32;
+ *   y: M blocks of N x P words, block m at y + m*sy, rows ldy apart
+ *      (ldy >= P, sy >= N*ldy); must not overlap x.
+ * N = 0 or P = 0 is a no-op.  Bandwidth-bound (M N P words written).
+ */
+int ne_outer(const void *x, int64_t ldx, int M, int64_t N, const int32_t *g,
+             int64_t P, void *y, int64_t ldy, int64_t sy, int w,
+             uint32_t live_mask, void *stream);
+
+/*
+ * ne_protected_outer -- entangle-on-load + ne_outer with failure injection
+ * + in-place recovery of all M outer products (Eq. 16-19).  d: M blocks of
+ * N x P words with contiguous rows, block m at d + m*sd (sd >= N*P).
+ * Ranges, failure arguments and errors as ne_protected_gemm with S = 1.
+ */
+int ne_protected_outer(const void *c, int64_t ldc, int M, int64_t N,
+                       const int32_t *g, int64_t P, int w, int l,
+                       int64_t c_min, int64_t c_max, int64_t max_abs_g,
+                       int failed, int fail_mode, void *d, int64_t sd,
+                       void *stream);
+
 /* Largest N + K - 1 that ne_protected_conv_noalloc accepts. */
 #define NE_NOALLOC_MAX_NOUT 100663296LL /* 2^25 * 3 output samples */
 

@@ -201,27 +201,6 @@ inline bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   return x < y + nb && y < x + na;
 }
 
-inline unsigned __int128 exact_limit(int M, int w, int l) {
-  const unsigned __int128 one = 1;
-  unsigned __int128 lim = ((one << (w - 1)) - 1) / ((one << l) + 1);
-  const int win_bits = (M - 1) * l - 1;
-  if (win_bits < 127) {
-    const unsigned __int128 win = (one << win_bits) - 1;
-    if (win < lim) lim = win;
-  }
-  return lim;
-}
-
-inline int choose_mode(int w, __int128 lo, __int128 hi, long long* bias) {
-  *bias = 0;
-  if (w == 32) return MODE_I32;
-  if (hi - lo > (__int128)0xffffffffLL) return MODE_SPLIT;
-  const __int128 i32min = -((__int128)1 << 31), i32max = ((__int128)1 << 31) - 1;
-  if (lo >= i32min && hi <= i32max) return MODE_WIDE;
-  *bias = (long long)(uint64_t)(unsigned __int128)(lo - i32min);
-  return MODE_WIDE;
-}
-
 template <int T>
 int set_batch_smem(size_t bytes) {
   return cudaFuncSetAttribute(batch_kernel<T>,
@@ -519,7 +498,7 @@ int ne_batch_prepare(ne_ctx* ctx, const ne_job* jobs, int n_jobs) {
     jd.Kp = (J.K + CONV_KC - 1) / CONV_KC * CONV_KC;
     jd.l = l;
     const __int128 f = ((__int128)1 << l) + 1;
-    jd.mode = choose_mode(J.w, (__int128)J.c_min * f, (__int128)J.c_max * f,
+    jd.mode = choose_mode(J.w, true, (__int128)J.c_min * f, (__int128)J.c_max * f,
                           &jd.bias);
     jd.failed = J.failed;
     jd.fail_mode = J.fail_mode;

@@ -749,35 +749,6 @@ inline size_t rows_bytes(int rows, int64_t ld, int64_t n, int wb) {
   return ((size_t)(rows - 1) * (size_t)ld + (size_t)n) * (size_t)wb;
 }
 
-// Arithmetic mode for w-bit words whose values lie in [lo, hi] (if known):
-// 32-bit words multiply-add in 32 bits; 64-bit words whose range spans at
-// most 2^32 values take one 32x32->64 multiply-add per tap after a shift by
-// *bias (0 when the range already fits 32 bits); any other 64-bit words use
-// the split operands.
-inline int choose_mode(int w, bool known, __int128 lo, __int128 hi,
-                       long long* bias) {
-  *bias = 0;
-  if (w == 32) return MODE_I32;
-  if (!known || hi - lo > (__int128)0xffffffffLL) return MODE_SPLIT;
-  const __int128 i32min = -((__int128)1 << 31), i32max = ((__int128)1 << 31) - 1;
-  if (lo >= i32min && hi <= i32max) return MODE_WIDE;
-  // x - b in [-2^31, hi - lo - 2^31]; b is used modulo 2^64
-  *bias = (long long)(uint64_t)(unsigned __int128)(lo - i32min);
-  return MODE_WIDE;
-}
-
-// Exact range limit for an arbitrary shift l (see ne_params).
-inline unsigned __int128 exact_limit(int M, int w, int l) {
-  const unsigned __int128 one = 1;
-  unsigned __int128 lim = ((one << (w - 1)) - 1) / ((one << l) + 1);
-  const int win_bits = (M - 1) * l - 1;
-  if (win_bits < 127) {
-    const unsigned __int128 win = (one << win_bits) - 1;
-    if (win < lim) lim = win;
-  }
-  return lim;
-}
-
 }  // namespace
 
 // Host reader of this translation unit's device error word.

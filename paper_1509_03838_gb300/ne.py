@@ -105,6 +105,15 @@ _SIGS = {
                    _i32),
     "ne_probe_imad_rate": ([_i32, _i32, ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double)], _i32),
+    "ne_gemm": ([_vp, _i64, _i64, _i32, _i64, _i64, _vp, _i64, _i64, _vp,
+                 _i64, _i64, _i32, _i64, _i64, _u32, _vp], _i32),
+    "ne_protected_gemm": ([_vp, _i64, _i64, _i32, _i64, _i64, _vp, _i64, _i64,
+                           _i32, _i32, _i64, _i64, _i64, _i32, _i32, _vp,
+                           _i64, _vp], _i32),
+    "ne_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _vp, _i64, _i64, _i32,
+                  _u32, _vp], _i32),
+    "ne_protected_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _i32, _i32, _i64,
+                            _i64, _i64, _i32, _i32, _vp, _i64, _vp], _i32),
 }
 
 
@@ -195,6 +204,23 @@ def _rows(t: torch.Tensor, name: str):
         raise ValueError(f"{name} must have unit stride along samples")
     ld = t2.stride(0) if t2.size(0) > 1 else max(t2.size(1), 1)
     return ctypes.c_void_p(t2.data_ptr()), t2.size(0), t2.size(1), ld
+
+
+def _blocks(t: torch.Tensor, name: str):
+    """(ptr, blocks, rows, cols, row stride, block stride) of a 3-D CUDA
+    tensor [M, rows, cols] with unit stride along cols (a 2-D tensor is one
+    block)."""
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    t3 = t.unsqueeze(0) if t.dim() == 2 else t
+    if t3.dim() != 3:
+        raise ValueError(f"{name} must be 2-D or 3-D")
+    if t3.size(2) > 1 and t3.stride(2) != 1:
+        raise ValueError(f"{name} must have unit stride along columns")
+    ld = t3.stride(1) if t3.size(1) > 1 else max(t3.size(2), 1)
+    sb = t3.stride(0) if t3.size(0) > 1 else t3.size(1) * ld
+    return (ctypes.c_void_p(t3.data_ptr()), t3.size(0), t3.size(1), t3.size(2),
+            ld, sb)
 
 
 # ---------------------------------------------------------------------------
@@ -531,3 +557,84 @@ class Batch:
                                        ctypes.byref(b), ctypes.byref(ms)),
                "ne_batch_autotune")
         return t.value, b.value, ms.value
+
+
+# ---------------------------------------------------------------------------
+# matrix products (Sec. IV stream-by-stream GEMM; Sec. I outer product)
+# ---------------------------------------------------------------------------
+
+def ne_gemm(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
+            x_range: tuple[int, int] | None = None,
+            live_mask: int = 0xFFFFFFFF, stream=None) -> torch.Tensor:
+    """y[m] = x[m] @ g (mod 2^w) for every live stream; x [M, R, S] words,
+    g [S, T] int32, y [M, R, T] words of x's width."""
+    px, M, R, S, ldx, sx = _blocks(x, "x")
+    py, My, Ry, T, ldy, sy = _blocks(y, "y")
+    if (My, Ry) != (M, R) or g.dim() != 2 or g.size(0) != S or g.size(1) != T:
+        raise ValueError("shapes of x, g and y do not match")
+    if g.dtype != torch.int32 or (T > 1 and g.stride(1) != 1):
+        raise ValueError("g must be int32 with unit column stride")
+    lo, hi = (1, 0) if x_range is None else (int(x_range[0]), int(x_range[1]))
+    _check(lib().ne_gemm(px, ldx, sx, M, R, S, ctypes.c_void_p(g.data_ptr()),
+                         g.stride(0) if S > 1 else T, T, py, ldy, sy,
+                         _word_bits(x), lo, hi, live_mask & 0xFFFFFFFF,
+                         _stream(stream)), "ne_gemm")
+    return y
+
+
+def ne_protected_gemm(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
+                      l: int, c_range: tuple[int, int], max_abs_g: int,
+                      failed: int = -1, fail_mode: int = NE_FAIL_NONE,
+                      stream=None) -> torch.Tensor:
+    """Entangle-on-load -> stream-by-stream GEMM -> recovery (d[m] = c[m] @ g);
+    d [M, R, T] with contiguous rows."""
+    pc, M, R, S, ldc, sc = _blocks(c, "c")
+    pd, Md, Rd, T, ldd, sd = _blocks(d, "d")
+    if (Md, Rd) != (M, R) or g.dim() != 2 or g.size(0) != S or g.size(1) != T:
+        raise ValueError("shapes of c, g and d do not match")
+    if R > 1 and ldd != T:
+        raise ValueError("d must have contiguous rows (row stride T)")
+    if g.dtype != torch.int32 or (T > 1 and g.stride(1) != 1):
+        raise ValueError("g must be int32 with unit column stride")
+    _check(lib().ne_protected_gemm(pc, ldc, sc, M, R, S,
+                                   ctypes.c_void_p(g.data_ptr()),
+                                   g.stride(0) if S > 1 else T, T,
+                                   _word_bits(c), l, int(c_range[0]),
+                                   int(c_range[1]), int(max_abs_g), failed,
+                                   fail_mode, pd, sd, _stream(stream)),
+           "ne_protected_gemm")
+    return d
+
+
+def ne_outer(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
+             live_mask: int = 0xFFFFFFFF, stream=None) -> torch.Tensor:
+    """y[m] = outer(x[m], g) (mod 2^w); x [M, N] words, g [P] int32,
+    y [M, N, P]."""
+    px, M, N, ldx = _rows(x, "x")
+    py, My, Ny, P, ldy, sy = _blocks(y, "y")
+    if (My, Ny) != (M, N) or g.numel() != P or g.dtype != torch.int32:
+        raise ValueError("shapes of x, g and y do not match")
+    _check(lib().ne_outer(px, ldx, M, N, ctypes.c_void_p(g.data_ptr()), P,
+                          py, ldy, sy, _word_bits(x), live_mask & 0xFFFFFFFF,
+                          _stream(stream)), "ne_outer")
+    return y
+
+
+def ne_protected_outer(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
+                       l: int, c_range: tuple[int, int], max_abs_g: int,
+                       failed: int = -1, fail_mode: int = NE_FAIL_NONE,
+                       stream=None) -> torch.Tensor:
+    """Entangle-on-load -> outer products -> recovery; d [M, N, P] with
+    contiguous rows."""
+    pc, M, N, ldc = _rows(c, "c")
+    pd, Md, Nd, P, ldd, sd = _blocks(d, "d")
+    if (Md, Nd) != (M, N) or g.numel() != P or g.dtype != torch.int32:
+        raise ValueError("shapes of c, g and d do not match")
+    if N > 1 and ldd != P:
+        raise ValueError("d must have contiguous rows (row stride P)")
+    _check(lib().ne_protected_outer(pc, ldc, M, N, ctypes.c_void_p(g.data_ptr()),
+                                    P, _word_bits(c), l, int(c_range[0]),
+                                    int(c_range[1]), int(max_abs_g), failed,
+                                    fail_mode, pd, sd, _stream(stream)),
+           "ne_protected_outer")
+    return d

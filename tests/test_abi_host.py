@@ -174,3 +174,53 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         fresh.ne_params(3, 32)
     importlib.reload(nemod)
+
+
+def test_matrix_product_argument_checks(ne):
+    """ne_gemm / ne_protected_gemm / ne_outer validate on the host before
+    any launch; empty outputs are no-ops that accept null pointers."""
+    L = ne.lib()
+    s = ctypes.c_void_p(0)
+    null = ctypes.c_void_p(0)
+    X, Y = ctypes.c_void_p(0x1000), ctypes.c_void_p(0x100000)
+    # empty output: no-op
+    assert L.ne_gemm(null, 4, 0, 3, 0, 4, null, 5, 5, null, 5, 0, 64, 1, 0,
+                     7, s) == ne.NE_OK
+    assert L.ne_gemm(null, 4, 16, 3, 4, 4, null, 0, 0, null, 0, 0, 64, 1, 0,
+                     7, s) == ne.NE_OK
+    assert L.ne_outer(null, 0, 3, 0, null, 9, null, 9, 0, 64, 7, s) == ne.NE_OK
+    # empty inner dimension with a nonempty output is not defined
+    assert L.ne_gemm(X, 4, 16, 3, 4, 0, X, 5, 5, Y, 5, 20, 64, 1, 0, 7,
+                     s) == ne.NE_ERR_INVALID_ARG
+    # strides too short
+    assert L.ne_gemm(X, 3, 16, 3, 4, 4, X, 5, 5, Y, 5, 20, 64, 1, 0, 7,
+                     s) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_gemm(X, 4, 15, 3, 4, 4, X, 5, 5, Y, 5, 20, 64, 1, 0, 7,
+                     s) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_gemm(X, 4, 16, 3, 4, 4, X, 5, 5, Y, 5, 19, 64, 1, 0, 7,
+                     s) == ne.NE_ERR_INVALID_ARG
+    # overlapping input and output
+    assert L.ne_gemm(X, 4, 16, 3, 4, 4, X, 5, 5, X, 5, 20, 64, 1, 0, 7,
+                     s) == ne.NE_ERR_INVALID_ARG
+    # word width
+    assert L.ne_outer(X, 8, 3, 8, X, 9, Y, 9, 72, 16, 7, s) == ne.NE_ERR_INVALID_ARG
+    p = ne.ne_params(4, 64)
+    # S * max|c| * max|g| beyond the exact limit
+    assert L.ne_protected_gemm(X, 1 << 20, 1 << 40, 4, 1 << 20, 1 << 20, X,
+                               64, 64, 64, p.l, -(1 << 15), 1 << 15, 1 << 15,
+                               -1, ne.NE_FAIL_NONE, Y, 1 << 26,
+                               s) == ne.NE_ERR_RANGE
+    # entangled words must fit the word
+    assert L.ne_protected_outer(X, 8, 4, 8, X, 8, 64, p.l, 0, 1 << 48, 1, -1,
+                                ne.NE_FAIL_NONE, Y, 64, s) == ne.NE_ERR_RANGE
+    # failure arguments
+    assert L.ne_protected_gemm(X, 8, 64, 4, 8, 8, X, 8, 8, 64, p.l, -9, 9, 9,
+                               4, ne.NE_FAIL_DROP, Y, 64,
+                               s) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_protected_outer(X, 8, 4, 8, X, 8, 64, p.l, -9, 9, 9, 1,
+                                ne.NE_FAIL_NONE, Y, 64,
+                                s) == ne.NE_ERR_INVALID_ARG
+    # fewer than three streams cannot be protected
+    assert L.ne_protected_gemm(X, 8, 64, 2, 8, 8, X, 8, 8, 64, p.l, -9, 9, 9,
+                               -1, ne.NE_FAIL_NONE, Y, 64,
+                               s) == ne.NE_ERR_INVALID_ARG
