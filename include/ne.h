@@ -277,12 +277,16 @@ int ne_gemm(const void *x, int64_t ldx, int64_t sx, int M, int64_t R,
             uint32_t live_mask, void *stream);
 
 /*
- * ne_protected_gemm -- the protected matrix product: entangle-on-load of
- * the M raw blocks (Eq. 6 applied elementwise as each block is read),
- * ne_gemm of every entangled block with failure injection, then recovery
- * of all M products from the M-1 delivered ones (Eq. 16-19) in place.
- * Two launches on `stream` (the product; the recovery, which is
- * bandwidth-bound and small next to the M R S T multiply-adds).
+ * ne_protected_gemm -- the protected matrix product: entanglement of the M
+ * raw blocks (Eq. 6 applied elementwise), ne_gemm of every entangled block
+ * with failure injection, then recovery of all M products from the M-1
+ * delivered ones (Eq. 16-19) in place.  With a workspace (ws of at least
+ * ne_protected_gemm_ws_bytes() bytes, c's blocks contiguous: ldc = S,
+ * sc = R*S) the blocks are entangled once into ws by a streaming pass
+ * before the product (three launches); otherwise the product entangles as
+ * it loads, which repeats the work once per 64 kernel columns (two
+ * launches).  The recovery is bandwidth-bound and small next to the
+ * M R S T multiply-adds.
  *   c: M raw blocks (ldc, sc as x of ne_gemm); g: S x T int32 (ldg);
  *   d: M output blocks of R x T words with contiguous rows (row stride T),
  *      block m at d + m*sd (sd >= R*T); receives the true products
@@ -292,12 +296,18 @@ int ne_gemm(const void *x, int64_t ldx, int64_t sx, int M, int64_t R,
  *      or max|c| (2^l + 1) does not fit w signed bits.
  *   failed, fail_mode: as ne_protected_conv (NE_FAIL_SKIP: stream `failed`
  *      is never computed; NE_FAIL_DROP: computed, then not read).
+ *   ws, ws_bytes: optional device workspace (NULL/0: entangle on load); it
+ *      must not overlap c or d, and is overwritten.
  */
 int ne_protected_gemm(const void *c, int64_t ldc, int64_t sc, int M,
                       int64_t R, int64_t S, const int32_t *g, int64_t ldg,
                       int64_t T, int w, int l, int64_t c_min, int64_t c_max,
                       int64_t max_abs_g, int failed, int fail_mode, void *d,
-                      int64_t sd, void *stream);
+                      int64_t sd, void *ws, size_t ws_bytes, void *stream);
+
+/* Workspace bytes for ne_protected_gemm's entangle-once form: M R S words
+ * of w bits (0 for an empty or invalid shape).  Host-only. */
+size_t ne_protected_gemm_ws_bytes(int M, int64_t R, int64_t S, int w);
 
 /*
  * ne_outer -- outer vector product of every live stream with the kernel

@@ -452,11 +452,16 @@ int ne_gemm(const void* x, int64_t ldx, int64_t sx, int M, int64_t R,
   return dispatch_gemm<false>(a, w, mode, vec, (cudaStream_t)stream);
 }
 
+size_t ne_protected_gemm_ws_bytes(int M, int64_t R, int64_t S, int w) {
+  if (M < 1 || R <= 0 || S <= 0 || (w != 32 && w != 64)) return 0;
+  return (size_t)M * (size_t)R * (size_t)S * (size_t)(w / 8);
+}
+
 int ne_protected_gemm(const void* c, int64_t ldc, int64_t sc, int M,
                       int64_t R, int64_t S, const int32_t* g, int64_t ldg,
                       int64_t T, int w, int l, int64_t c_min, int64_t c_max,
                       int64_t max_abs_g, int failed, int fail_mode, void* d,
-                      int64_t sd, void* stream) {
+                      int64_t sd, void* ws, size_t ws_bytes, void* stream) {
   if (M < 3 || M > 32 || R < 0 || S < 0 || T < 0 || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (fail_mode != NE_FAIL_NONE && fail_mode != NE_FAIL_SKIP &&
@@ -498,9 +503,27 @@ int ne_protected_gemm(const void* c, int64_t ldc, int64_t sc, int M,
   const __int128 f = ((__int128)1 << l) + 1;
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
-  const bool vec = rows_aligned16(c, ldc, wb) && (sc * wb) % 16 == 0;
   cudaStream_t s = (cudaStream_t)stream;
-  const int st = dispatch_gemm<true>(a, w, mode, vec, s);
+  int st;
+  const size_t need_ws = ne_protected_gemm_ws_bytes(M, R, S, w);
+  if (ws && ws_bytes >= need_ws && ldc == S && sc == R * S &&
+      !spans_overlap(ws, need_ws, c, blocks_bytes(M, R, S, ldc, sc, wb)) &&
+      !spans_overlap(ws, need_ws, d, blocks_bytes(M, R, T, T, sd, wb))) {
+    // The product re-stages each block's row panel once per 64-column tile
+    // of the kernel, so entangling as it loads would repeat the work T/64
+    // times; one streaming pass over the blocks (each a row of R*S words)
+    // entangles every word once.
+    st = ne_entangle(c, R * S, ws, R * S, M, R * S, w, l, stream);
+    if (st != NE_OK) return st;
+    a.x = ws;
+    a.ldx = S;
+    a.sx = R * S;
+    const bool vec = rows_aligned16(ws, S, wb) && ((R * S) * wb) % 16 == 0;
+    st = dispatch_gemm<false>(a, w, mode, vec, s);
+  } else {
+    const bool vec = rows_aligned16(c, ldc, wb) && (sc * wb) % 16 == 0;
+    st = dispatch_gemm<true>(a, w, mode, vec, s);
+  }
   if (st != NE_OK) return st;
   // each stream's product is R*T contiguous words: recover all M in place
   // from the M-1 that were delivered (Eq. 16-19)

@@ -109,7 +109,8 @@ _SIGS = {
                  _i64, _i64, _i32, _i64, _i64, _u32, _vp], _i32),
     "ne_protected_gemm": ([_vp, _i64, _i64, _i32, _i64, _i64, _vp, _i64, _i64,
                            _i32, _i32, _i64, _i64, _i64, _i32, _i32, _vp,
-                           _i64, _vp], _i32),
+                           _i64, _vp, ctypes.c_size_t, _vp], _i32),
+    "ne_protected_gemm_ws_bytes": ([_i32, _i64, _i64, _i32], ctypes.c_size_t),
     "ne_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _vp, _i64, _i64, _i32,
                   _u32, _vp], _i32),
     "ne_protected_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _i32, _i32, _i64,
@@ -582,12 +583,18 @@ def ne_gemm(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
     return y
 
 
+def ne_protected_gemm_ws_bytes(M: int, R: int, S: int, w: int) -> int:
+    return int(lib().ne_protected_gemm_ws_bytes(M, R, S, w))
+
+
 def ne_protected_gemm(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
                       l: int, c_range: tuple[int, int], max_abs_g: int,
                       failed: int = -1, fail_mode: int = NE_FAIL_NONE,
+                      ws: torch.Tensor | None = None,
                       stream=None) -> torch.Tensor:
-    """Entangle-on-load -> stream-by-stream GEMM -> recovery (d[m] = c[m] @ g);
-    d [M, R, T] with contiguous rows."""
+    """Entangle -> stream-by-stream GEMM -> recovery (d[m] = c[m] @ g);
+    d [M, R, T] with contiguous rows.  ws: optional workspace of
+    ne_protected_gemm_ws_bytes() bytes (entangle once instead of on load)."""
     pc, M, R, S, ldc, sc = _blocks(c, "c")
     pd, Md, Rd, T, ldd, sd = _blocks(d, "d")
     if (Md, Rd) != (M, R) or g.dim() != 2 or g.size(0) != S or g.size(1) != T:
@@ -601,7 +608,12 @@ def ne_protected_gemm(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
                                    g.stride(0) if S > 1 else T, T,
                                    _word_bits(c), l, int(c_range[0]),
                                    int(c_range[1]), int(max_abs_g), failed,
-                                   fail_mode, pd, sd, _stream(stream)),
+                                   fail_mode, pd, sd,
+                                   ctypes.c_void_p(ws.data_ptr() if ws is not None
+                                                   else 0),
+                                   ws.numel() * ws.element_size()
+                                   if ws is not None else 0,
+                                   _stream(stream)),
            "ne_protected_gemm")
     return d
 

@@ -208,19 +208,21 @@ def test_matrix_product_argument_checks(ne):
     # S * max|c| * max|g| beyond the exact limit
     assert L.ne_protected_gemm(X, 1 << 20, 1 << 40, 4, 1 << 20, 1 << 20, X,
                                64, 64, 64, p.l, -(1 << 15), 1 << 15, 1 << 15,
-                               -1, ne.NE_FAIL_NONE, Y, 1 << 26,
+                               -1, ne.NE_FAIL_NONE, Y, 1 << 26, null, 0,
                                s) == ne.NE_ERR_RANGE
     # entangled words must fit the word
     assert L.ne_protected_outer(X, 8, 4, 8, X, 8, 64, p.l, 0, 1 << 48, 1, -1,
                                 ne.NE_FAIL_NONE, Y, 64, s) == ne.NE_ERR_RANGE
     # failure arguments
     assert L.ne_protected_gemm(X, 8, 64, 4, 8, 8, X, 8, 8, 64, p.l, -9, 9, 9,
-                               4, ne.NE_FAIL_DROP, Y, 64,
+                               4, ne.NE_FAIL_DROP, Y, 64, null, 0,
                                s) == ne.NE_ERR_INVALID_ARG
     assert L.ne_protected_outer(X, 8, 4, 8, X, 8, 64, p.l, -9, 9, 9, 1,
                                 ne.NE_FAIL_NONE, Y, 64,
                                 s) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_protected_gemm_ws_bytes(4, 10, 20, 64) == 4 * 10 * 20 * 8
+    assert L.ne_protected_gemm_ws_bytes(4, 0, 20, 64) == 0
     # fewer than three streams cannot be protected
     assert L.ne_protected_gemm(X, 8, 64, 2, 8, 8, X, 8, 8, 64, p.l, -9, 9, 9,
-                               -1, ne.NE_FAIL_NONE, Y, 64,
+                               -1, ne.NE_FAIL_NONE, Y, 64, null, 0,
                                s) == ne.NE_ERR_INVALID_ARG

@@ -91,9 +91,10 @@ def test_gemm_live_mask_and_padded_output(ne, orc):
         assert (got[m, :, T:] == 11).all()  # padding untouched
 
 
+@pytest.mark.parametrize("use_ws", [False, True])
 @pytest.mark.parametrize("w,M,bits", [(64, 3, 14), (64, 4, 15), (64, 8, 14),
                                       (32, 3, 4)])
-def test_protected_gemm_every_failure(ne, orc, w, M, bits):
+def test_protected_gemm_every_failure(ne, orc, w, M, bits, use_ws):
     p = ne.ne_params(M, w)
     R, S, T = 70, 65, 66
     gen = synth.rng(M * 100 + w)
@@ -109,10 +110,15 @@ def test_protected_gemm_every_failure(ne, orc, w, M, bits):
     modes = [(ne.NE_FAIL_NONE, -1)] + [(fm, r) for fm in (ne.NE_FAIL_SKIP,
                                                           ne.NE_FAIL_DROP)
                                        for r in range(M)]
+    ws = None
+    if use_ws:  # entangle once into the workspace (contiguous blocks)
+        cd = cd.contiguous()
+        ws = torch.empty(ne.ne_protected_gemm_ws_bytes(M, R, S, w),
+                         dtype=torch.uint8, device="cuda")
     for fm, r in modes:
         d = torch.full((M, R, T), 99, dtype=dt(w), device="cuda")
         ne.ne_protected_gemm(cd, gd, d, l=p.l, c_range=(-b, b - 1),
-                             max_abs_g=gb, failed=r, fail_mode=fm)
+                             max_abs_g=gb, failed=r, fail_mode=fm, ws=ws)
         torch.cuda.synchronize()
         assert np.array_equal(host(d), plain), (fm, r)
 
@@ -193,9 +199,11 @@ def test_protected_gemm_paper_size_sampled(ne, orc, M, bits):
     g = torch.empty((N, N), dtype=torch.int32, device="cuda").random_(
         -b, b, generator=gen)
     d = torch.empty((M, N, N), dtype=torch.int64, device="cuda")
+    ws = torch.empty(ne.ne_protected_gemm_ws_bytes(M, N, N, 64),
+                     dtype=torch.uint8, device="cuda")
     r = M // 2
     ne.ne_protected_gemm(c, g, d, l=p.l, c_range=(-b, b - 1), max_abs_g=b,
-                         failed=r, fail_mode=ne.NE_FAIL_DROP)
+                         failed=r, fail_mode=ne.NE_FAIL_DROP, ws=ws)
     torch.cuda.synchronize()
     rows = np.sort(synth.rng(M).choice(N, size=8, replace=False))
     gh = g.cpu().numpy().astype(np.int64)
@@ -203,3 +211,25 @@ def test_protected_gemm_paper_size_sampled(ne, orc, M, bits):
     got = d[:, torch.from_numpy(rows).cuda(), :].cpu().numpy()
     expect = orc.gemm(ch, gh, 64)
     assert np.array_equal(got, expect)
+
+
+def test_protected_gemm_workspace_needs_contiguous_blocks(ne, orc):
+    """Padded blocks, or a workspace that is too small, fall back to
+    entangling on load; the result is the same."""
+    M, w, R, S, T = 4, 64, 20, 30, 40
+    p = ne.ne_params(M, w)
+    gen = synth.rng(31)
+    c = synth.uniform_int(gen, (M, R, S), -(1 << 15), 1 << 15)
+    g = synth.uniform_int(gen, (S, T), -(1 << 15), 1 << 15)
+    plain = orc.gemm(c, g, w)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    for cd, nbytes in ((blocks(c, w, pad_cols=2), None), (blocks(c, w), 64)):
+        need = ne.ne_protected_gemm_ws_bytes(M, R, S, w)
+        ws = torch.empty(need if nbytes is None else nbytes, dtype=torch.uint8,
+                         device="cuda")
+        d = torch.zeros((M, R, T), dtype=torch.int64, device="cuda")
+        ne.ne_protected_gemm(cd, gd, d, l=p.l, c_range=(-(1 << 15), (1 << 15) - 1),
+                             max_abs_g=1 << 15, failed=2,
+                             fail_mode=ne.NE_FAIL_SKIP, ws=ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), plain)
