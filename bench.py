@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-paper-shapes", action="store_true")
+    ap.add_argument("--no-gemm", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU oracle sample")
     return ap.parse_args()
@@ -435,6 +436,9 @@ def run_ne(args):
     del c_h, d_h, g_h
     small = bench_small(ne, synth, dev, stream)
     paper = None if args.no_paper_shapes else bench_paper_shapes(ne, dev, stream)
+    gemm = (None if args.no_gemm
+            else bench_gemm(ne, dev, stream, probe["imad_wide"] / 1e12,
+                            probe["wide_plus_imad32"] / 1e12))
     batch = None if args.no_batch else bench_batch(ne, synth, dev, stream)
     served = None if args.no_serve else bench_serve(dev)
     cpu = None
@@ -463,6 +467,7 @@ def run_ne(args):
             "clocks": clk,
             "small": small,
             "paper_shapes": paper,
+            "gemm": gemm,
             "batch": batch,
             "serve": served,
             "p99_ms_served": served["p99_ms"] if served else None,
@@ -570,6 +575,72 @@ def bench_paper_shapes(ne, dev, stream, reps=5):
                 "protected_gops": 2 * M * N * K / (res["protected"] * 1e-3) / 1e9})
             del d, dcs, ws, g
         del c, cs
+    return rows
+
+
+def bench_gemm(ne, dev, stream, peak_wide, peak_split, reps=10):
+    """Sec. IV's stream-by-stream matrix product: M blocks of N x N integers
+    times one N x N kernel (M N^3 multiply-adds), at the top of the paper's
+    N range, 64-bit words, one stream dropped per step and recovered.  Per
+    shape: the protected product (entangle once into a workspace, product,
+    recovery), the unprotected product and the checksum method (checksum
+    block, M+1 products, recovery), with overheads and the protected
+    product's fraction of the measured multiply-add peak for its
+    arithmetic (one 32x32->64 multiply-add per product, or a wide plus a
+    32-bit one)."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(13)
+    rows = []
+    for M, N, bits in ((8, 1000, 14), (4, 1024, 15), (3, 1000, 14)):
+        p = ne.ne_params(M, 64)
+        b = 1 << bits
+        f = (1 << p.l) + 1
+        c = torch.empty((M, N, N), dtype=torch.int64, device=dev).random_(
+            -b, b, generator=gen)
+        g = torch.empty((N, N), dtype=torch.int32, device=dev).random_(
+            -b, b, generator=gen)
+        d = torch.empty((M, N, N), dtype=torch.int64, device=dev)
+        ws = torch.empty(ne.ne_protected_gemm_ws_bytes(M, N, N, 64),
+                         dtype=torch.uint8, device=dev)
+        cs = torch.empty((M + 1, N, N), dtype=torch.int64, device=dev)
+        cs[:M] = c
+        dcs = torch.empty((M + 1, N, N), dtype=torch.int64, device=dev)
+
+        def prot(i):
+            ne.ne_protected_gemm(c, g, d, l=p.l, c_range=(-b, b - 1),
+                                 max_abs_g=b, failed=i % M,
+                                 fail_mode=ne.NE_FAIL_DROP, ws=ws)
+
+        def unprot(i):
+            ne.ne_gemm(c, g, d, x_range=(-b, b - 1))
+
+        def checksum(i):
+            ne.ne_checksum(cs[:M].view(M, N * N), cs[M].view(N * N))
+            ne.ne_gemm(cs, g, dcs, x_range=(-M * b, M * (b - 1)))
+            ne.ne_checksum_recover(dcs[:M].view(M, N * N), dcs[M].view(N * N),
+                                   dcs[i % M].view(N * N), f=i % M)
+
+        res = {}
+        for name, fn in (("protected", prot), ("unprotected", unprot),
+                         ("checksum", checksum)):
+            fn(0)
+            t, _ = timed(fn, reps, 1, stream)
+            res[name] = t / reps
+        macs = M * N ** 3
+        wide = (b - 1 + b) * f <= 0xFFFFFFFF
+        peak = peak_wide if wide else peak_split
+        rate = macs / (res["protected"] * 1e-3) / 1e12
+        rows.append({
+            "M": M, "N": N, "l": p.l, "data_bits": bits, "ms": res,
+            "arith": "one 32x32->64 multiply-add per product" if wide
+                     else "split 64-bit operands (wide + 32-bit multiply-add)",
+            "ne_overhead_pct": 100 * (res["protected"] / res["unprotected"] - 1),
+            "checksum_overhead_pct": 100 * (res["checksum"] / res["unprotected"] - 1),
+            "protected_tmac_per_s": rate,
+            "unprotected_tmac_per_s": macs / (res["unprotected"] * 1e-3) / 1e12,
+            "protected_frac_of_peak": rate * (1.0 if wide else 2.0) / peak})
+        del c, g, d, ws, cs, dcs
     return rows
 
 

@@ -14,6 +14,10 @@ data and taps, 64-bit words, the benchmark's workload):
                  K = 1000 shape (data and taps in [-2^14, 2^14), no
                  failure): the arrival-word form
   conv_m8        unprotected conv of the same data (declared range)
+  gemm_m8        stream-by-stream matrix product, M = 8 blocks of
+                 1000 x 1000 (data and kernel in [-2^14, 2^14))
+  gemm_prot_m8   the protected product of the same blocks (entangle once
+                 into a workspace, product, recovery; stream 3 dropped)
 """
 from __future__ import annotations
 
@@ -66,9 +70,25 @@ def main() -> int:
         ops["protected_m8"] = lambda: ne.ne_protected_conv(
             c8, g8, d8, l=l8, c_range=(-b8, b8 - 1), max_abs_g=b8, ws=ws8)
         ops["conv_m8"] = lambda: ne.ne_conv(c8, g8, d8, x_range=(-b8, b8 - 1))
+    if a.case in ("gemm_m8", "gemm_prot_m8"):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(21)
+        bg, Mg, Ng = 1 << 14, 8, 1000
+        cg = torch.empty((Mg, Ng, Ng), dtype=torch.int64, device=dev).random_(
+            -bg, bg, generator=gen)
+        gg = torch.empty((Ng, Ng), dtype=torch.int32, device=dev).random_(
+            -bg, bg, generator=gen)
+        dg = torch.empty((Mg, Ng, Ng), dtype=torch.int64, device=dev)
+        wsg = torch.empty(ne.ne_protected_gemm_ws_bytes(Mg, Ng, Ng, 64),
+                          dtype=torch.uint8, device=dev)
+        lg = ne.ne_params(Mg, 64).l
+        ops["gemm_m8"] = lambda: ne.ne_gemm(cg, gg, dg, x_range=(-bg, bg - 1))
+        ops["gemm_prot_m8"] = lambda: ne.ne_protected_gemm(
+            cg, gg, dg, l=lg, c_range=(-bg, bg - 1), max_abs_g=bg, failed=3,
+            fail_mode=ne.NE_FAIL_DROP, ws=wsg)
     if a.case not in ops:
         raise SystemExit(f"unknown case {a.case}; one of "
-                         f"{sorted(ops) + ['conv_m8', 'protected_m8']}")
+                         f"{sorted(ops) + ['conv_m8', 'protected_m8', 'gemm_m8', 'gemm_prot_m8']}")
     for _ in range(a.reps):
         ops[a.case]()
     torch.cuda.synchronize()
