@@ -305,6 +305,45 @@ int ne_protected_gemm(const void *c, int64_t ldc, int64_t sc, int M,
                       int64_t max_abs_g, int failed, int fail_mode, void *d,
                       int64_t sd, void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * Host-to-host pipeline for the protected convolution (the whole path of
+ * ne_protected_conv with its streams in host memory).  The job is cut into
+ * chunks of `chunk` output samples per stream; each chunk copies its input
+ * slice, with the K-1 samples of history its first output reads, to the
+ * device, runs ne_protected_conv on it, and copies its outputs back.  Chunks
+ * rotate over `nstreams` CUDA streams, each with its own device buffers, so
+ * host-to-device copies, the fused kernels and device-to-host copies of
+ * different chunks overlap; for transfers to overlap the host buffers must
+ * be pinned (cudaHostAlloc / cudaHostRegister).  The paper has no
+ * counterpart: it moves no data between memories.
+ *
+ * ne_pipe_create allocates the pipeline's streams, events and device
+ * buffers (M * (chunk + 2 K_max) words per stream plus arrival words); it
+ * is the only call here that allocates, and ne_pipe_destroy frees them.
+ */
+#define NE_PIPE_MAX_STREAMS 8
+typedef struct ne_pipe ne_pipe;
+int ne_pipe_create(ne_pipe **out, int M, int64_t chunk, int K_max, int w,
+                   int nstreams);
+int ne_pipe_destroy(ne_pipe *p);
+
+/*
+ * ne_pipe_protected_conv -- d_host = the M true outputs d_m = c_m * g of
+ * the protected convolution of c_host (M rows of N words, ldc), with the
+ * failure injected into every chunk, written to d_host (M rows, ldd >=
+ * N+K-1).  g: K int32 taps in DEVICE memory (K <= K_max); l, ranges and
+ * failure arguments as ne_protected_conv, all checked before anything is
+ * enqueued.  Ordered after prior work on `stream`; `stream` waits for the
+ * last chunk's copy, so d_host is complete once `stream` gets past this
+ * call.  c_host and d_host must not overlap; calls on one pipeline must not
+ * overlap either.
+ */
+int ne_pipe_protected_conv(ne_pipe *p, const void *c_host, int64_t ldc,
+                           int64_t N, const int32_t *g, int K, int l,
+                           int64_t c_min, int64_t c_max, int64_t max_abs_g,
+                           int failed, int fail_mode, void *d_host,
+                           int64_t ldd, void *stream);
+
 /* Workspace bytes for ne_protected_gemm's entangle-once form: M R S words
  * of w bits (0 for an empty or invalid shape).  Host-only. */
 size_t ne_protected_gemm_ws_bytes(int M, int64_t R, int64_t S, int w);

@@ -111,6 +111,11 @@ _SIGS = {
                            _i32, _i32, _i64, _i64, _i64, _i32, _i32, _vp,
                            _i64, _vp, ctypes.c_size_t, _vp], _i32),
     "ne_protected_gemm_ws_bytes": ([_i32, _i64, _i64, _i32], ctypes.c_size_t),
+    "ne_pipe_create": ([ctypes.POINTER(_vp), _i32, _i64, _i32, _i32, _i32],
+                       _i32),
+    "ne_pipe_destroy": ([_vp], _i32),
+    "ne_pipe_protected_conv": ([_vp, _vp, _i64, _i64, _vp, _i32, _i32, _i64,
+                                _i64, _i64, _i32, _i32, _vp, _i64, _vp], _i32),
     "ne_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _vp, _i64, _i64, _i32,
                   _u32, _vp], _i32),
     "ne_protected_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _i32, _i32, _i64,
@@ -650,3 +655,55 @@ def ne_protected_outer(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
                                     fail_mode, pd, sd, _stream(stream)),
            "ne_protected_outer")
     return d
+
+
+# ---------------------------------------------------------------------------
+# host-to-host pipeline
+# ---------------------------------------------------------------------------
+
+class Pipe:
+    """ne_pipe: protected convolutions from host memory to host memory, cut
+    into chunks that overlap their copies and kernels over several streams.
+    Host tensors should be pinned (torch.Tensor.pin_memory())."""
+
+    def __init__(self, M: int, chunk: int, K_max: int, w: int = 64,
+                 nstreams: int = 3):
+        h = _vp()
+        _check(lib().ne_pipe_create(ctypes.byref(h), M, chunk, K_max, w,
+                                    nstreams), "ne_pipe_create")
+        self._h = h
+        self.M, self.chunk, self.K_max, self.w = M, chunk, K_max, w
+
+    def protected_conv(self, c_host: torch.Tensor, g: torch.Tensor,
+                       d_host: torch.Tensor, *, l: int,
+                       c_range: tuple[int, int], max_abs_g: int,
+                       failed: int = -1, fail_mode: int = NE_FAIL_NONE,
+                       stream=None) -> torch.Tensor:
+        """d_host[m] = c_host[m] * g; c_host, d_host: 2-D host tensors of
+        w-bit words; g: int32 CUDA tensor."""
+        for t, nm in ((c_host, "c_host"), (d_host, "d_host")):
+            if t.is_cuda or t.dim() != 2 or (t.size(1) > 1 and t.stride(1) != 1):
+                raise ValueError(f"{nm} must be a 2-D host tensor with unit "
+                                 "column stride")
+        if not g.is_cuda or g.dtype != torch.int32:
+            raise ValueError("g must be an int32 CUDA tensor")
+        if c_host.size(0) != self.M or d_host.size(0) != self.M:
+            raise ValueError("row count differs from the pipeline's M")
+        _check(lib().ne_pipe_protected_conv(
+            self._h, ctypes.c_void_p(c_host.data_ptr()), c_host.stride(0),
+            c_host.size(1), ctypes.c_void_p(g.data_ptr()), g.numel(), l,
+            int(c_range[0]), int(c_range[1]), int(max_abs_g), failed,
+            fail_mode, ctypes.c_void_p(d_host.data_ptr()), d_host.stride(0),
+            _stream(stream)), "ne_pipe_protected_conv")
+        return d_host
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().ne_pipe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

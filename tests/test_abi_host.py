@@ -226,3 +226,21 @@ def test_matrix_product_argument_checks(ne):
     assert L.ne_protected_gemm(X, 8, 64, 2, 8, 8, X, 8, 8, 64, p.l, -9, 9, 9,
                                -1, ne.NE_FAIL_NONE, Y, 64, null, 0,
                                s) == ne.NE_ERR_INVALID_ARG
+
+
+def test_pipe_argument_checks(ne):
+    """ne_pipe_create and ne_pipe_protected_conv reject bad arguments before
+    touching the device."""
+    L = ne.lib()
+    h = ctypes.c_void_p()
+    for M, chunk, K, w, ns in ((2, 1000, 64, 64, 3), (4, 0, 64, 64, 3),
+                               (4, 1000, 0, 64, 3), (4, 1000, 64, 16, 3),
+                               (4, 1000, 64, 64, 0), (4, 1000, 64, 64, 9)):
+        assert L.ne_pipe_create(ctypes.byref(h), M, chunk, K, w, ns) == \
+            ne.NE_ERR_INVALID_ARG
+        assert not h.value
+    assert L.ne_pipe_destroy(None) == ne.NE_OK
+    X = ctypes.c_void_p(0x1000)
+    assert L.ne_pipe_protected_conv(None, X, 8, 8, X, 4, 16, -9, 9, 9, -1,
+                                    ne.NE_FAIL_NONE, X, 11,
+                                    ctypes.c_void_p(0)) == ne.NE_ERR_INVALID_ARG
