@@ -500,8 +500,8 @@ E2E_STREAMS = 4
 
 TRAFFIC_CAPTURE = {
     "sources_sha256":
-        "9fe898d99f8a508409983efc82f26a4704a11a82f73c60c7237bc11614ee845a",
-    "bytes": 134311936 + 86469888,  # profiles/conv_cluster_protected_M4_N2e22_K64.md
+        "59ef4e0af713753ec61fb2b6a444696f61c3a127c8e9f3e6b213d68b900606b2",
+    "bytes": 134323968 + 86639872,  # profiles/conv_cluster_protected_M4_N2e22_K64.md
 }
 CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_recover.cuh",
                 "ne_common.cuh"]
