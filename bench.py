@@ -436,13 +436,11 @@ def run_ne(args):
     t_e2e, _ = timed(e2e, args.steps, world, stream)
     t_e2e = max_over_ranks(t_e2e, world, dev)
     e2e_val = world * ops_job * args.steps / (t_e2e * 1e-3) / 1e9
+    # bytes per step: every chunk's input slice (with its K-1 samples of
+    # history) and the taps in, every output out
+    h2d, d2h = pipe.bytes_moved(N, K)
+    h2d += K * 4
     pipe.close()
-    # bytes the pipeline moves per step: every chunk's input slice (with its
-    # K-1 samples of history), the taps, and every output once
-    h2d = K * 4
-    for n0 in range(0, Nout, E2E_CHUNK):
-        n1 = min(Nout, n0 + E2E_CHUNK)
-        h2d += M * (min(N, n1) - max(0, n0 - K + 1)) * 8
 
     clk = clocks.summary(t_start, t_end)
     del c_h, d_h, g_h
@@ -474,7 +472,7 @@ def run_ne(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "GOPS",
                     "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": M * Nout * 8,
+                    "d2h_bytes_per_step": d2h,
                     "path": f"ne_pipe_protected_conv, chunks of {E2E_CHUNK} "
                             f"output samples over {E2E_STREAMS} streams"},
             "gpu_launches": args.steps,

@@ -344,6 +344,12 @@ int ne_pipe_protected_conv(ne_pipe *p, const void *c_host, int64_t ldc,
                            int failed, int fail_mode, void *d_host,
                            int64_t ldd, void *stream);
 
+/* Bytes one ne_pipe_protected_conv call on p moves for an N-sample job
+ * with K taps: *h2d (input slices, histories included) and *d2h (outputs).
+ * Host-only. */
+int ne_pipe_bytes(const ne_pipe *p, int64_t N, int K, int64_t *h2d,
+                  int64_t *d2h);
+
 /* Workspace bytes for ne_protected_gemm's entangle-once form: M R S words
  * of w bits (0 for an empty or invalid shape).  Host-only. */
 size_t ne_protected_gemm_ws_bytes(int M, int64_t R, int64_t S, int w);

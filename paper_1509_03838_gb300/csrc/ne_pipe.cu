@@ -30,6 +30,23 @@ struct ne_pipe {
 
 namespace {
 
+// Output chunks of one call: [0, chunk), [chunk, 2 chunk), ..., clipped
+// to Nout.  (Chunks that grow and shrink at the ends, to shorten the
+// pipeline's ramp, measured no faster: with both copy directions busy the
+// host link, not the ramp, bounds the call.)
+struct ChunkWalk {
+  int64_t Nout, chunk, at = 0;
+  ChunkWalk(int64_t nout, int64_t ch) : Nout(nout), chunk(ch) {}
+  // the next chunk [n0, n1); false once [0, Nout) is covered
+  bool next(int64_t& n0, int64_t& n1) {
+    if (at >= Nout) return false;
+    n0 = at;
+    n1 = std::min<int64_t>(Nout, at + chunk);
+    at = n1;
+    return true;
+  }
+};
+
 void release(ne_pipe* p) {
   for (int i = 0; i < NE_PIPE_MAX_STREAMS; ++i) {
     if (p->in[i]) cudaFree(p->in[i]);
@@ -104,6 +121,25 @@ int ne_pipe_destroy(ne_pipe* p) {
   return NE_OK;
 }
 
+int ne_pipe_bytes(const ne_pipe* p, int64_t N, int K, int64_t* h2d,
+                  int64_t* d2h) {
+  if (!p || !h2d || !d2h || N < 0 || K < 1 || K > p->K_max)
+    return NE_ERR_INVALID_ARG;
+  *h2d = 0;
+  *d2h = 0;
+  if (N == 0) return NE_OK;
+  const int64_t Nout = N + K - 1;
+  const int64_t wb = p->w / 8;
+  ChunkWalk walk(Nout, p->chunk);
+  int64_t n0 = 0, n1 = 0;
+  while (walk.next(n0, n1)) {
+    *h2d += (std::min<int64_t>(N, n1) - std::max<int64_t>(0, n0 - K + 1)) *
+            p->M * wb;
+    *d2h += (n1 - n0) * p->M * wb;
+  }
+  return NE_OK;
+}
+
 int ne_pipe_protected_conv(ne_pipe* p, const void* c_host, int64_t ldc,
                            int64_t N, const int32_t* g, int K, int l,
                            int64_t c_min, int64_t c_max, int64_t max_abs_g,
@@ -126,13 +162,12 @@ int ne_pipe_protected_conv(ne_pipe* p, const void* c_host, int64_t ldc,
   for (int i = 0; i < p->ns; ++i)
     if (cudaStreamWaitEvent(p->s[i], p->start, 0) != cudaSuccess)
       return NE_ERR_CUDA;
-  const int64_t nchunks = (Nout + p->chunk - 1) / p->chunk;
   int st = NE_OK;
-  for (int64_t cidx = 0; cidx < nchunks && st == NE_OK; ++cidx) {
+  ChunkWalk walk(Nout, p->chunk);
+  int64_t n0 = 0, n1 = 0;
+  for (int64_t cidx = 0; st == NE_OK && walk.next(n0, n1); ++cidx) {
     const int i = (int)(cidx % p->ns);
     cudaStream_t s = p->s[i];
-    const int64_t n0 = cidx * p->chunk;
-    const int64_t n1 = std::min<int64_t>(Nout, n0 + p->chunk);
     // inputs that outputs [n0, n1) read: [n0 - K + 1, n1) within [0, N)
     const int64_t s0 = std::max<int64_t>(0, n0 - K + 1);
     const int64_t s1 = std::min<int64_t>(N, n1);

@@ -114,6 +114,8 @@ _SIGS = {
     "ne_pipe_create": ([ctypes.POINTER(_vp), _i32, _i64, _i32, _i32, _i32],
                        _i32),
     "ne_pipe_destroy": ([_vp], _i32),
+    "ne_pipe_bytes": ([_vp, _i64, _i32, ctypes.POINTER(_i64),
+                       ctypes.POINTER(_i64)], _i32),
     "ne_pipe_protected_conv": ([_vp, _vp, _i64, _i64, _vp, _i32, _i32, _i64,
                                 _i64, _i64, _i32, _i32, _vp, _i64, _vp], _i32),
     "ne_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _vp, _i64, _i64, _i32,
@@ -696,6 +698,13 @@ class Pipe:
             fail_mode, ctypes.c_void_p(d_host.data_ptr()), d_host.stride(0),
             _stream(stream)), "ne_pipe_protected_conv")
         return d_host
+
+    def bytes_moved(self, N: int, K: int) -> tuple[int, int]:
+        """(host-to-device, device-to-host) bytes of one call."""
+        h, d = _i64(), _i64()
+        _check(lib().ne_pipe_bytes(self._h, N, K, ctypes.byref(h),
+                                   ctypes.byref(d)), "ne_pipe_bytes")
+        return h.value, d.value
 
     def close(self) -> None:
         if getattr(self, "_h", None):

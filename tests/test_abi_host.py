@@ -244,3 +244,9 @@ def test_pipe_argument_checks(ne):
     assert L.ne_pipe_protected_conv(None, X, 8, 8, X, 4, 16, -9, 9, 9, -1,
                                     ne.NE_FAIL_NONE, X, 11,
                                     ctypes.c_void_p(0)) == ne.NE_ERR_INVALID_ARG
+
+
+def test_pipe_bytes_needs_a_pipe(ne):
+    h, d = ctypes.c_int64(), ctypes.c_int64()
+    assert ne.lib().ne_pipe_bytes(None, 10, 3, ctypes.byref(h),
+                                  ctypes.byref(d)) == ne.NE_ERR_INVALID_ARG

@@ -102,3 +102,16 @@ def test_pipe_full_size_sampled(ne, orc):
     exp = np.stack([orc.conv_at(j.c[m], j.g, 64, pos) for m in range(j.M)])
     assert np.array_equal(got, exp)
     pipe.close()
+
+
+def test_pipe_bytes_account_for_every_chunk(ne):
+    """Every output leaves once; every input arrives once plus at most K-1
+    samples of history per chunk."""
+    M, N, K, chunk = 4, 1 << 22, 64, 1 << 20
+    pipe = ne.Pipe(M, chunk, K)
+    h2d, d2h = pipe.bytes_moved(N, K)
+    assert d2h == M * (N + K - 1) * 8
+    nchunks_max = (N + K - 1) // (chunk // 8) + 1
+    assert M * N * 8 <= h2d <= M * (N + nchunks_max * (K - 1)) * 8
+    assert pipe.bytes_moved(0, K) == (0, 0)
+    pipe.close()
