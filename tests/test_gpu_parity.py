@@ -236,6 +236,8 @@ PROT_CASES = [
     (64, 5, TILE - 1, 1024, 12, 12),     # long kernel, one tile
     (32, 4, 777, 5, 6, 6),
     (64, 3, 50, 100, 15, 15),            # N < K
+    (64, 3, 3000, 8192, 10, 10),         # maximum K, split arithmetic
+    (32, 3, 2000, 8192, 3, 3),           # maximum K, 32-bit words
 ]
 
 
@@ -252,8 +254,9 @@ def test_protected_conv_all_failures(ne, orc, case):
                                                           ne.NE_FAIL_DROP)
                                        for r in range(M)]
     for fm, r in modes:
-        # the oracle's step-by-step method gives the same result
-        if r >= 0:
+        # the oracle's step-by-step method gives the same result (checked
+        # where it runs in seconds; the plain convolution pins the rest)
+        if r >= 0 and K <= 2048:
             _, _, d_or = orc.protected_conv(c, g, w, p.l, r)
             assert np.array_equal(d_or, plain)
         d = torch.full((M, N + K - 1), 99, dtype=dt(w), device="cuda")
