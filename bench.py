@@ -5,7 +5,10 @@ Default workload: M = 4 integer streams of N = 2^22 samples, K = 64 taps,
 data and taps uniform in [-2^15, 2^15), 64-bit entangled words; each step is
 one pass of the whole protected path over the job (entangle-on-load,
 convolution of every entangled stream, fail-stop of stream r = step mod M,
-recovery of all M outputs from the other M-1) in the fused launch.
+recovery of all M outputs from the other M-1) through ne_protected_conv: on
+the tensor cores (the entangling product, then the in-place recovery) when
+the operands fit 32 bits, K <= 65 and |g| <= 2^15, as here; otherwise the
+fused multiply-add kernel.
 
 Prints ONE JSON line (rank 0).  `value` is protected GOPS (2*M*N*K integer
 ops per job) over all ranks; beside it: the unprotected and checksum-ABFT
@@ -332,6 +335,9 @@ def run_ne(args):
 
     # ---- baselines on the same data (same number of steps) ---------------
     def unprot_best(i):   # the fastest exact unprotected conv of the data
+        ne.ne_conv(c, g, d, x_range=j.c_range, max_abs_g=j.bound_g)
+
+    def unprot_imad(i):   # the same on the integer multiply-add kernel
         ne.ne_conv(c, g, d, x_range=j.c_range)
 
     def unprot_split(i):  # 64-bit words of undeclared range (context)
@@ -344,7 +350,8 @@ def run_ne(args):
     def checksum(i):      # Eq. 3-5: checksum stream, M+1 convs, recovery
         f = i % M
         ne.ne_checksum(cs[:M], cs[M])
-        ne.ne_conv(cs, g, cso, x_range=(M * j.c_range[0], M * j.c_range[1]))
+        ne.ne_conv(cs, g, cso, x_range=(M * j.c_range[0], M * j.c_range[1]),
+                   max_abs_g=j.bound_g)
         ne.ne_checksum_recover(cso[:M], cso[M], cso[f], f=f)
 
     eps = torch.empty_like(c)
@@ -356,11 +363,12 @@ def run_ne(args):
     def unfused(i):       # entangle -> conv of all M -> drop r -> recover
         r = i % M
         ne.ne_entangle(c, eps, l=p.l)
-        ne.ne_conv(eps, g, delta, x_range=eps_range)
+        ne.ne_conv(eps, g, delta, x_range=eps_range, max_abs_g=j.bound_g)
         ne.ne_recover(delta, d, l=p.l, failed=r)
 
     res = {}
     for name, fn in [("unprotected", unprot_best),
+                     ("unprotected_multiply_add", unprot_imad),
                      ("unprotected_undeclared_range", unprot_split),
                      ("checksum_abft", checksum),
                      ("protected_unfused", unfused)]:
@@ -379,41 +387,70 @@ def run_ne(args):
         "protected_vs_unprotected": pct(ms_step, res["unprotected"]),
         "checksum_abft_vs_unprotected": pct(res["checksum_abft"], res["unprotected"]),
         "unfused_protected_vs_unprotected": pct(res["protected_unfused"], res["unprotected"]),
-        "ms_per_job": {"protected_fused": ms_step, **res},
+        "ms_per_job": {"protected": ms_step, **res},
     }
 
-    # ---- roofline of the dominant kernel (integer multiply-add pipe) -------
+    # ---- roofline of the dominant kernel -----------------------------------
     probe = {}
-    for kind, nm in [(0, "imad32"), (1, "imad_wide"), (2, "wide_plus_imad32")]:
-        rate, _ = ne.ne_probe_imad_rate(kind, 2048)
+    for kind, nm in [(0, "imad32"), (1, "imad_wide"), (2, "wide_plus_imad32"),
+                     (5, "mma_sync_f16")]:
+        rate, _ = ne.ne_probe_imad_rate(kind, 2048 if kind < 5 else 512)
         probe[nm] = rate
-    # The entangled words c_m + 2^l c_{m-1} with c in [-2^15, 2^15) and
-    # l = 16 span (2^16 - 1)(2^16 + 1) = 2^32 - 1 values, so after the range
-    # shift every tap is one 32x32->64 multiply-add: M*N*K of them per job
-    # (the dropped stream's convolution runs too).  The pipe's limit for that
-    # instruction is the measured probe rate.
     span = (j.c_range[1] - j.c_range[0]) * f_ent
-    per_mac = 1.0 if span <= 0xFFFFFFFF else 2.0
-    macs = float(M) * N * K
-    achieved = macs * per_mac / (prot_ms * 1e-3) / 1e12
-    peak = (probe["imad_wide"] if per_mac == 1.0
-            else probe["wide_plus_imad32"]) / 1e12
-    traffic = (TRAFFIC_CAPTURE["bytes"]
-               if TRAFFIC_CAPTURE["sources_sha256"] == conv_sources_sha()
-               else None)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "T 32x32->64 multiply-add instr/s" if per_mac == 1.0
-                        else "T multiply-add instr/s (wide + 32-bit pairs)",
-                "frac": achieved / peak, "traffic": traffic,
-                "algorithmic_bytes": float((M * N + M * Nout) * 8),
-                "kernel": "conv_cluster_kernel<int64, MODE_WIDE> (fused "
-                          "entangle-on-load + conv + cluster exchange + "
-                          "recovery)",
-                "peak_source": "measured on this GPU by ne_probe_imad_rate "
-                               "(independent mad.wide.s32 chains, 8 per "
-                               "thread, 16 warps per scheduler)",
-                "launch_ms": prot_ms,
-                "probe_instr_per_s": probe}
+    algo_bytes = float((M * N + M * Nout) * 8)
+    tc_path = (span <= 0xFFFFFFFF and K <= 65 and j.bound_g <= 32768
+               and os.environ.get("NE_CONV_TC", "1") != "0"
+               and os.environ.get("NE_PROT_KERNEL") is None)
+    if tc_path:
+        # Exact products on the tensor cores leave the step bound by memory:
+        # c read once and d written once (algorithmic bytes) against the
+        # measured copy bandwidth.  The step is two kernels (the entangling
+        # product, then the in-place recovery), timed together.
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(peaks["hbm_gbs"])
+        achieved = algo_bytes / (prot_ms * 1e-3) / 1e9
+        mma_per_step = M * (Nout / 128.0) * 40.0  # mma.sync per 128 outputs
+        traffic = (TRAFFIC_CAPTURE["bytes"]
+                   if TRAFFIC_CAPTURE["sources_sha256"] == conv_sources_sha()
+                   else None)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                    "algorithmic_bytes": algo_bytes,
+                    "kernel": "tc_conv_kernel<int64, ENT> + recover_kernel "
+                              "(entangle-on-load tensor-core product, then "
+                              "in-place recovery; timed together)",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured "
+                                   "copy bandwidth)",
+                    "launch_ms": prot_ms,
+                    "tensor": {"mma_sync_per_s": mma_per_step / (prot_ms * 1e-3),
+                               "probe_mma_sync_per_s": probe["mma_sync_f16"],
+                               "frac": mma_per_step / (prot_ms * 1e-3)
+                                       / probe["mma_sync_f16"]},
+                    "probe_instr_per_s": probe}
+    else:
+        # The entangled words c_m + 2^l c_{m-1} with c in [-2^15, 2^15) and
+        # l = 16 span (2^16 - 1)(2^16 + 1) = 2^32 - 1 values, so after the
+        # range shift every tap is one 32x32->64 multiply-add: M*N*K of them
+        # per job.  The pipe's limit for that instruction is the measured
+        # probe rate.
+        per_mac = 1.0 if span <= 0xFFFFFFFF else 2.0
+        macs = float(M) * N * K
+        achieved = macs * per_mac / (prot_ms * 1e-3) / 1e12
+        peak = (probe["imad_wide"] if per_mac == 1.0
+                else probe["wide_plus_imad32"]) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                    "unit": "T 32x32->64 multiply-add instr/s" if per_mac == 1.0
+                            else "T multiply-add instr/s (wide + 32-bit pairs)",
+                    "frac": achieved / peak, "traffic": None,
+                    "algorithmic_bytes": algo_bytes,
+                    "kernel": "conv_cluster_kernel<int64, MODE_WIDE> (fused "
+                              "entangle-on-load + conv + cluster exchange + "
+                              "recovery)",
+                    "peak_source": "measured on this GPU by ne_probe_imad_rate "
+                                   "(independent mad.wide.s32 chains, 8 per "
+                                   "thread, 16 warps per scheduler)",
+                    "launch_ms": prot_ms,
+                    "probe_instr_per_s": probe}
 
     # ---- end to end through host buffers ----------------------------------
     # The job's streams and results live in pinned host memory; each step
@@ -475,7 +512,7 @@ def run_ne(args):
                     "d2h_bytes_per_step": d2h,
                     "path": f"ne_pipe_protected_conv, chunks of {E2E_CHUNK} "
                             f"output samples over {E2E_STREAMS} streams"},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (2 if tc_path else 1),
             "clocks": clk,
             "small": small,
             "paper_shapes": paper,
@@ -498,11 +535,13 @@ E2E_STREAMS = 4
 
 TRAFFIC_CAPTURE = {
     "sources_sha256":
-        "59ef4e0af713753ec61fb2b6a444696f61c3a127c8e9f3e6b213d68b900606b2",
-    "bytes": 134323968 + 86639872,  # profiles/conv_cluster_protected_M4_N2e22_K64.md
+        "c38f6ee921ee1b33813aa8ef7c568ea6a1a5cb969c657e85fc576231fd4c5018",
+    # tc_conv_kernel (134248448 + 84851200) + recover_kernel (100714752 +
+    # 72739328): profiles/conv_tc_protected_M4_N2e22_K64.md
+    "bytes": 134248448 + 84851200 + 100714752 + 72739328,
 }
-CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_recover.cuh",
-                "ne_common.cuh"]
+CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_conv_tc.cuh",
+                "ne_recover.cuh", "ne_common.cuh", "ne_stream_ops.cu"]
 
 
 def conv_sources_sha() -> str:
@@ -571,11 +610,12 @@ def bench_paper_shapes(ne, dev, stream, reps=5):
                                      max_abs_g=b, ws=ws)
 
             def unprot(i):
-                ne.ne_conv(c, g, d, x_range=(-b, b - 1))
+                ne.ne_conv(c, g, d, x_range=(-b, b - 1), max_abs_g=b)
 
             def checksum(i):
                 ne.ne_checksum(cs[:M], cs[M])
-                ne.ne_conv(cs, g, dcs, x_range=(-M * b, M * (b - 1)))
+                ne.ne_conv(cs, g, dcs, x_range=(-M * b, M * (b - 1)),
+                           max_abs_g=b)
                 ne.ne_checksum_recover(dcs[:M], dcs[M], dcs[0], f=0)
 
             res = {}

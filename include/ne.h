@@ -143,6 +143,23 @@ int ne_conv(const void *x, int64_t ldx, int M, int64_t N, const int32_t *g,
             int K, void *y, int64_t ldy, int w, int64_t x_min, int64_t x_max,
             uint32_t live_mask, void *stream);
 
+/*
+ * ne_conv_range -- ne_conv with the taps' range declared as well: every
+ * |g[t]| <= max_abs_g.  When the operands fit 32 bits (32-bit words, or
+ * 64-bit words whose declared range spans at most 2^32 values), K <= 65 and
+ * max_abs_g <= 32768, the convolution runs on the tensor cores, exactly:
+ * operand and taps are split into byte digits that fp16 holds exactly,
+ * every digit product and every fp32 partial sum is an exact integer
+ * below 2^24, and the outputs are assembled in 64-bit integers.  Otherwise
+ * it is ne_conv.  Same arguments, layouts and errors as ne_conv, plus
+ * NE_ERR_INVALID_ARG for max_abs_g < 0.  A tap beyond max_abs_g gives
+ * undefined outputs (no fault).
+ */
+int ne_conv_range(const void *x, int64_t ldx, int M, int64_t N,
+                  const int32_t *g, int K, int64_t max_abs_g, void *y,
+                  int64_t ldy, int w, int64_t x_min, int64_t x_max,
+                  uint32_t live_mask, void *stream);
+
 /* Kinds of ne_conv_kind (the convolution-type LSB ops of Eq. 2). */
 typedef enum {
   NE_CONV_LINEAR = 0,   /* y[n] = sum_t x[n-t] g[t], n in [0, N+K-1)        */
@@ -230,7 +247,9 @@ int ne_detect(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
  *   d: M output rows (ldd >= N+K-1), receives the true outputs d_m = c_m * g.
  *      It also serves as the landing buffer of the entangled tiles.
  *   [c_min, c_max]: caller's declared range of the inputs (c_min <= c_max);
- *   max_abs_g: bound on |g|.  With B = max(|c_min|, |c_max|) the call
+ *   max_abs_g: bound on |g| (with entangled words that fit 32 bits, K <= 65
+ *      and max_abs_g <= 32768 the product runs on the tensor cores, as in
+ *      ne_conv_range, inside the cluster form below).  With B = max(|c_min|, |c_max|) the call
  *      returns NE_ERR_RANGE if K*B*max_abs_g exceeds the exact output range
  *      for (M, w, l) or B(2^l + 1) does not fit w signed bits.  The range
  *      also picks the arithmetic: entangled words lie in

@@ -19,6 +19,9 @@ extern "C" {
  *   kind 3: mad.lo.cc.u32 + madc.hi.s32 per round, a 64-bit accumulation
  *           by carry chain (two instructions)
  *   kind 4: mad.wide.s32 + fma.rn.f32 per round (two instructions)
+ *   kind 5: mma.sync m16n8k16 with fp16 inputs and fp32 accumulation, the
+ *           tensor-core product of the exact integer convolution; counted as
+ *           warp-wide instructions (2*16*8*16 = 4096 flops each)
  * and return the best of three timed launches (after one warm-up) as
  * multiply-add instructions per second in *instr_per_s (and the launch time
  * in *elapsed_ms if non-NULL).  Unlike the compute calls of ne.h this call

@@ -574,6 +574,11 @@ constexpr int CLUSTER_K_MAX_SPLIT = 208;
 constexpr int CLUSTER_K_MIN_I32_M3 = 48;
 
 // ---------------------------------------------------------------------------
+// tensor-core convolution (32-bit operands, |taps| < 2^15, K <= 65)
+// ---------------------------------------------------------------------------
+#include "ne_conv_tc.cuh"
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 constexpr size_t kSmemBudget = 200 * 1024;  // per block, of 227 KB
@@ -732,6 +737,64 @@ int dispatch_cluster(const ConvArgs& a, int w, int mode, bool vec,
   return launch_cluster<int64_t, MODE_SPLIT>(a, vec, s);
 }
 
+// The tensor-core path: 32-bit operands (32-bit words, or 64-bit words whose
+// range spans at most 2^32 values), K <= 65, |g| <= 32768.  NE_CONV_TC=0
+// turns it off (the multiply-add kernels run instead).
+inline bool tc_enabled() {
+  static const bool off = [] {
+    const char* e = getenv("NE_CONV_TC");
+    return e && strcmp(e, "0") == 0;
+  }();
+  return !off;
+}
+
+inline bool tc_eligible(int mode, int K, long long max_abs_g) {
+  return tc_enabled() && (mode == MODE_I32 || mode == MODE_WIDE) &&
+         K <= TC_MAX_K && max_abs_g >= 0 && max_abs_g <= TC_MAX_G;
+}
+
+// Persistent tensor-core launch: the grid is the resident block count.
+template <typename Kern>
+int launch_tc_persistent(Kern kernel, size_t dyn, const ConvArgs& a,
+                         cudaStream_t s, std::once_flag& once, int& per_sm,
+                         int& attr) {
+  std::call_once(once, [&] {
+    attr = set_max_smem(kernel, dyn > 0 ? dyn : 1);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, TC_THREADS,
+                                                      dyn) == cudaSuccess &&
+        n > 0)
+      per_sm = n;
+    cudaGetLastError();
+  });
+  if (attr != NE_OK) return attr;
+  const int64_t units = a.ntiles * a.M;
+  const int64_t grid = std::min<int64_t>(units, (int64_t)sm_count() * per_sm);
+  kernel<<<(unsigned)grid, TC_THREADS, dyn, s>>>(a);
+  return status_from_cuda(cudaGetLastError());
+}
+
+template <typename W, bool VEC, bool BIAS, bool ENT>
+int launch_tc_conv_v(const ConvArgs& a, cudaStream_t s) {
+  static std::once_flag once;
+  static int per_sm = 1, attr = NE_OK;
+  return launch_tc_persistent(tc_conv_kernel<W, VEC, BIAS, ENT>, 0, a, s,
+                              once, per_sm, attr);
+}
+
+// ENT: entangle on load (x holds the raw streams, a.l the shift).
+template <bool ENT>
+int dispatch_tc_conv(const ConvArgs& a, int w, bool vec, cudaStream_t s) {
+  if (w == 32)
+    return vec ? launch_tc_conv_v<int32_t, true, false, ENT>(a, s)
+               : launch_tc_conv_v<int32_t, false, false, ENT>(a, s);
+  if (a.bias != 0)
+    return vec ? launch_tc_conv_v<int64_t, true, true, ENT>(a, s)
+               : launch_tc_conv_v<int64_t, false, true, ENT>(a, s);
+  return vec ? launch_tc_conv_v<int64_t, true, false, ENT>(a, s)
+             : launch_tc_conv_v<int64_t, false, false, ENT>(a, s);
+}
+
 template <bool PROT>
 int dispatch_conv(const ConvArgs& a, int w, int mode, bool vec,
                   cudaStream_t s) {
@@ -800,6 +863,43 @@ int ne_conv(const void* x, int64_t ldx, int M, int64_t N, const int32_t* g,
   // rows); outputs are stored through shared memory for any alignment
   const bool vec = rows_aligned16(x, ldx, wb);
   return dispatch_conv<false>(a, w, mode, vec, (cudaStream_t)stream);
+}
+
+int ne_conv_range(const void* x, int64_t ldx, int M, int64_t N,
+                  const int32_t* g, int K, int64_t max_abs_g, void* y,
+                  int64_t ldy, int w, int64_t x_min, int64_t x_max,
+                  uint32_t live_mask, void* stream) {
+  if (max_abs_g < 0) return NE_ERR_INVALID_ARG;
+  long long bias = 0;
+  const int mode = (w == 32 || w == 64)
+                       ? choose_mode(w, x_min <= x_max, (__int128)x_min,
+                                     (__int128)x_max, &bias)
+                       : MODE_SPLIT;
+  if (!tc_eligible(mode, K, max_abs_g))
+    return ne_conv(x, ldx, M, N, g, K, y, ldy, w, x_min, x_max, live_mask,
+                   stream);
+  if (M < 1 || M > 32 || N < 0 || K < 1 || ldx < N) return NE_ERR_INVALID_ARG;
+  if (N == 0) return NE_OK;
+  const int64_t Nout = N + K - 1;
+  if (!x || !y || !g || ldy < Nout) return NE_ERR_INVALID_ARG;
+  const int wb = w / 8;
+  if (overlaps(x, rows_bytes(M, ldx, N, wb), y, rows_bytes(M, ldy, Nout, wb)))
+    return NE_ERR_INVALID_ARG;
+  ConvArgs a{};
+  a.x = x;
+  a.ldx = ldx;
+  a.M = M;
+  a.N = N;
+  a.Nout = Nout;
+  a.ntiles = (Nout + TC_TILE - 1) / TC_TILE;
+  a.g = g;
+  a.K = K;
+  a.y = y;
+  a.ldy = ldy;
+  a.live_mask = M == 32 ? live_mask : (live_mask & ((1u << M) - 1u));
+  a.bias = bias;
+  return dispatch_tc_conv<false>(a, w, rows_aligned16(x, ldx, wb),
+                                 (cudaStream_t)stream);
 }
 
 int ne_conv_kind(const void* x, int64_t ldx, int M, int64_t N,
@@ -912,6 +1012,19 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
+  if (tc_eligible(mode, K, max_abs_g) && forced_form() == FORM_AUTO) {
+    // tensor cores: every computing stream's entangled product delta_m into
+    // d (entangled on load), then the recovery of all M in place
+    ConvArgs t = a;
+    t.ntiles = (Nout + TC_TILE - 1) / TC_TILE;
+    const uint32_t all = M == 32 ? 0xffffffffu : (1u << M) - 1u;
+    t.live_mask = fail_mode == NE_FAIL_SKIP ? (all & ~(1u << failed)) : all;
+    const int st = dispatch_tc_conv<true>(t, w, vec, s);
+    if (st != NE_OK) return st;
+    if (fail_mode == NE_FAIL_NONE)
+      return ne_extract(d, ldd, M, Nout, w, l, d, ldd, stream);
+    return ne_recover(d, ldd, M, Nout, w, l, failed, d, ldd, stream);
+  }
   if (use_cluster(M, K, w, mode, a.ntiles)) {
     if (dispatch_cluster(a, w, mode, vec, s) == NE_OK) return NE_OK;
     // a refused cluster launch (configuration error, not sticky): clear it

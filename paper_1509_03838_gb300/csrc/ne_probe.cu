@@ -11,6 +11,7 @@
 //   kind 3: mad.lo.cc.u32 + madc.hi.s32 per round (a 64-bit multiply-add
 //           as a carry chain; two instructions)
 //   kind 4: mad.wide.s32 + fma.rn.f32 per round (two instructions)
+//   kind 5: mma.sync m16n8k16 f16 -> f32 (warp-wide; 4096 flops each)
 #include "ne_common.cuh"
 
 namespace ne {
@@ -69,6 +70,37 @@ __global__ void __launch_bounds__(256) imad_probe_kernel(int iters, int seed,
   sink[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keep every chain live
 }
 
+// kind 5: eight independent chains of mma.sync m16n8k16 (fp16 inputs, fp32
+// accumulation) per warp, the tensor-core product of the exact integer
+// convolution.  Operands are fp16 values near 1; the accumulators feed the
+// sink so that no chain is dead.
+__global__ void __launch_bounds__(256) mma_probe_kernel(int iters, int seed,
+                                                        unsigned long long* sink) {
+  const uint32_t base = 0x3c003c00u ^ (uint32_t)(seed + threadIdx.x);
+  const uint32_t a0 = base, a1 = base ^ 0x1u, a2 = base ^ 0x2u, a3 = base ^ 0x3u;
+  const uint32_t b0 = base ^ 0x4u, b1 = base ^ 0x5u;
+  float c[8][4];
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[k][q] = 0.f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, "
+          "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+          : "+f"(c[k][0]), "+f"(c[k][1]), "+f"(c[k][2]), "+f"(c[k][3])
+          : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s += c[k][q];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = (unsigned long long)__float_as_uint(s);
+}
+
 }  // namespace
 }  // namespace ne
 
@@ -76,7 +108,7 @@ using namespace ne;
 
 extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
                                   double* elapsed_ms) {
-  if (!instr_per_s || kind < 0 || kind > 4 || iters < 1)
+  if (!instr_per_s || kind < 0 || kind > 5 || iters < 1)
     return NE_ERR_INVALID_ARG;
   const int sms = sm_count();
   const int blocks = sms * 8;
@@ -95,7 +127,8 @@ extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
     else if (kind == 1) imad_probe_kernel<1><<<blocks, 256>>>(iters, rep, sink);
     else if (kind == 2) imad_probe_kernel<2><<<blocks, 256>>>(iters, rep, sink);
     else if (kind == 3) imad_probe_kernel<3><<<blocks, 256>>>(iters, rep, sink);
-    else imad_probe_kernel<4><<<blocks, 256>>>(iters, rep, sink);
+    else if (kind == 4) imad_probe_kernel<4><<<blocks, 256>>>(iters, rep, sink);
+    else mma_probe_kernel<<<blocks, 256>>>(iters, rep, sink);
     cudaEventRecord(e1, 0);
     if (cudaEventSynchronize(e1) != cudaSuccess) { st = NE_ERR_CUDA; break; }
     float ms = 0.f;
@@ -104,7 +137,8 @@ extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
   }
   if (st == NE_OK && cudaGetLastError() != cudaSuccess) st = NE_ERR_CUDA;
   if (st == NE_OK) {
-    const double per_round = (kind >= 2) ? 16.0 : 8.0;
+    // kind 5 counts warp-wide mma.sync instructions (8 per warp per round)
+    const double per_round = kind == 5 ? 8.0 / 32.0 : (kind >= 2) ? 16.0 : 8.0;
     const double instr = (double)blocks * 256.0 * (double)iters * per_round;
     *instr_per_s = instr / (best * 1e-3);
     if (elapsed_ms) *elapsed_ms = best;

@@ -105,6 +105,8 @@ _SIGS = {
                    _i32),
     "ne_probe_imad_rate": ([_i32, _i32, ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double)], _i32),
+    "ne_conv_range": ([_vp, _i64, _i32, _i64, _vp, _i32, _i64, _vp, _i64, _i32,
+                       _i64, _i64, _u32, _vp], _i32),
     "ne_gemm": ([_vp, _i64, _i64, _i32, _i64, _i64, _vp, _i64, _i64, _vp,
                  _i64, _i64, _i32, _i64, _i64, _u32, _vp], _i32),
     "ne_protected_gemm": ([_vp, _i64, _i64, _i32, _i64, _i64, _vp, _i64, _i64,
@@ -279,10 +281,12 @@ def ne_entangle(c: torch.Tensor, eps: torch.Tensor | None = None, *, l: int,
 
 def ne_conv(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
             x_range: tuple[int, int] | None = None,
+            max_abs_g: int | None = None,
             live_mask: int = 0xFFFFFFFF, N: int | None = None,
             stream=None) -> torch.Tensor:
     """y_m = x_m * g (full linear convolution, Eq. 9) for live streams.
-    x_range = (x_min, x_max): declared range of the inputs, or None."""
+    x_range = (x_min, x_max): declared range of the inputs, or None;
+    max_abs_g: declared bound on |g| (ne_conv_range), or None (ne_conv)."""
     x_min, x_max = x_range if x_range is not None else (1, 0)
     px, M, n, ldx = _rows(x, "x")
     py, _, _, ldy = _rows(y, "y")
@@ -290,11 +294,18 @@ def ne_conv(x: torch.Tensor, g: torch.Tensor, y: torch.Tensor, *,
         raise ValueError("taps g must be an int32 CUDA tensor")
     w = _word_bits(x)
     assert _word_bits(y) == w
-    _check(lib().ne_conv(px, ldx, M, n if N is None else N,
-                         ctypes.c_void_p(g.data_ptr()), g.numel(), py, ldy, w,
-                         x_min, x_max, live_mask & 0xFFFFFFFF,
-                         _stream(stream)),
-           "ne_conv")
+    if max_abs_g is None:
+        _check(lib().ne_conv(px, ldx, M, n if N is None else N,
+                             ctypes.c_void_p(g.data_ptr()), g.numel(), py,
+                             ldy, w, x_min, x_max, live_mask & 0xFFFFFFFF,
+                             _stream(stream)),
+               "ne_conv")
+    else:
+        _check(lib().ne_conv_range(px, ldx, M, n if N is None else N,
+                                   ctypes.c_void_p(g.data_ptr()), g.numel(),
+                                   int(max_abs_g), py, ldy, w, x_min, x_max,
+                                   live_mask & 0xFFFFFFFF, _stream(stream)),
+               "ne_conv_range")
     return y
 
 

@@ -7,6 +7,7 @@ data and taps, 64-bit words, the benchmark's workload):
   protected      fused entangle-on-load + conv + extraction (stream 1 dropped)
   conv_split     plain conv, range not declared: split 64-bit operands
   conv_wide      plain conv, declared range: one 32x32->64 multiply-add/tap
+  conv_tc        plain conv, declared input and tap ranges: tensor cores
   entangle       out-of-place entanglement
   recover        recovery of all streams with stream 1 missing
   checksum       checksum stream of the ABFT baseline
@@ -53,6 +54,8 @@ def main() -> int:
             failed=1, fail_mode=ne.NE_FAIL_DROP, ws=ws),
         "conv_split": lambda: ne.ne_conv(c, g, d),
         "conv_wide": lambda: ne.ne_conv(c, g, d, x_range=j.c_range),
+        "conv_tc": lambda: ne.ne_conv(c, g, d, x_range=j.c_range,
+                                      max_abs_g=j.bound_g),
         "entangle": lambda: ne.ne_entangle(c, eps, l=p.l),
         "recover": lambda: ne.ne_recover(d, d, l=p.l, failed=1),
         "checksum": lambda: ne.ne_checksum(c, r),

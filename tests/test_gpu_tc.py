@@ -1,0 +1,153 @@
+"""GPU parity of the tensor-core convolution (exact integer products from
+byte digits on fp16 mma.sync) against the CPU oracle, bit-exact: the plain
+convolution with declared ranges (ne_conv_range) and the fused protected
+convolution, every failure mode, operands at the ends of the 32-bit window,
+the largest taps, K from 1 to 65, ragged and unaligned rows; and the same
+cases on the multiply-add kernels (NE_CONV_TC=0)."""
+import numpy as np
+import pytest
+
+from paper_1509_03838_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TT = 2048  # tensor-core tile
+
+
+@pytest.fixture(scope="module")
+def ne():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_03838_gb300 import build, ne as nemod
+    build.build()
+    return nemod
+
+
+def dt(w):
+    return torch.int32 if w == 32 else torch.int64
+
+
+def dev(a, w, ld=None):
+    a = np.asarray(a, dtype=np.int64)
+    rows, n = a.shape
+    ld = n if ld is None else ld
+    buf = torch.zeros((rows, ld), dtype=dt(w))
+    buf[:, :n] = torch.from_numpy(a.astype(np.int32 if w == 32 else np.int64))
+    return buf.cuda()[:, :n]
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.int64)
+
+
+CONV_CASES = [
+    # w, M, N, K, data range [lo, hi], declared range, max|g|, pad
+    (64, 4, 3 * TT + 11, 64, (-2**15, 2**15 - 1), (-2**15, 2**15 - 1), 32767, 0),
+    (64, 3, 2 * TT + 5, 65, (-2**31, 2**31 - 1), (-2**31, 2**31 - 1), 32767, 0),
+    (64, 3, TT + 3, 33, (2**40, 2**40 + 2**32 - 1), (2**40, 2**40 + 2**32 - 1), 32767, 0),
+    (64, 4, 5000, 64, (-2**31 - 2**15, 2**31 - 2**15 - 1),
+     (-2**31 - 2**15, 2**31 - 2**15 - 1), 32767, 0),              # shifted window
+    (64, 5, 1, 1, (-7, 7), (-7, 7), 100, 0),                       # N = 1, K = 1
+    (64, 3, 30, 64, (-2**20, 2**20), (-2**20, 2**20), 32767, 0),   # N < K
+    (64, 4, 4097, 16, (-2**15, 2**15 - 1), (-2**15, 2**15 - 1), 32767, 1),  # odd ld
+    (32, 3, 3 * TT - 1, 64, (-2**31, 2**31 - 1), (-2**31, 2**31 - 1), 32767, 0),
+    (32, 6, 777, 17, (-2**10, 2**10), (-2**10, 2**10), 5000, 3),
+    # beyond the tensor path's limits: the multiply-add kernels take over
+    (64, 3, 2000, 66, (-2**15, 2**15 - 1), (-2**15, 2**15 - 1), 32767, 0),
+    (64, 3, 2000, 40, (-2**15, 2**15 - 1), (-2**15, 2**15 - 1), 40000, 0),
+    (64, 4, 3000, 64, (-2**15, 2**15 - 1), (-2**15, 2**15 - 1), 32768, 0),  # |g| = 2^15
+    (64, 3, 2000, 40, (-2**40, 2**40), None, 32767, 0),
+]
+
+
+@pytest.mark.parametrize("case", CONV_CASES)
+def test_conv_range_matches_oracle(ne, orc, case):
+    w, M, N, K, (lo, hi), declared, gmax, pad = case
+    gen = synth.rng(N * 3 + K + gmax)
+    x = synth.uniform_int(gen, (M, N), lo, hi + 1)
+    x[:, 0] = hi
+    x[:, -1] = lo
+    if N > 8:
+        x[:, N // 2] = hi
+        x[:, N // 2 + 1] = lo
+    g = synth.uniform_int(gen, (K,), -gmax, gmax + 1)
+    g[0] = gmax
+    if K > 1:
+        g[-1] = -gmax
+    expect = orc.conv(x, g, w, strict=False)
+    y = torch.full((M, N + K - 1), 5, dtype=dt(w), device="cuda")
+    ne.ne_conv(dev(x, w, ld=N + pad), torch.from_numpy(g.astype(np.int32)).cuda(),
+               y, x_range=declared, max_abs_g=gmax)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), expect)
+
+
+def test_conv_range_live_mask(ne, orc):
+    w, M, N, K = 64, 5, 3 * TT + 100, 64
+    gen = synth.rng(12)
+    x = synth.uniform_int(gen, (M, N), -(1 << 15), 1 << 15)
+    g = synth.uniform_int(gen, (K,), -(1 << 15) + 1, 1 << 15)
+    expect = orc.conv(x, g, w)
+    y = torch.full((M, N + K - 1), -3, dtype=torch.int64, device="cuda")
+    live = 0b10101
+    ne.ne_conv(dev(x, w), torch.from_numpy(g.astype(np.int32)).cuda(), y,
+               x_range=(-(1 << 15), (1 << 15) - 1), max_abs_g=32767,
+               live_mask=live)
+    torch.cuda.synchronize()
+    got = host(y)
+    for m in range(M):
+        if (live >> m) & 1:
+            assert np.array_equal(got[m], expect[m])
+        else:
+            assert (got[m] == -3).all()
+
+
+PROT_CASES = [
+    # w, M, N, K, data bits, tap bits
+    (64, 4, 3 * TT + 7, 64, 15, 15),    # entangled span 2^32 - 1: range shift
+    (64, 8, 5000, 37, 14, 14),          # fits 32 bits without a shift
+    (64, 3, TT + 1, 65, 7, 15),         # l = 22, K = 65
+    (32, 3, 3000, 16, 7, 7),            # 32-bit words
+    (64, 5, TT, 1, 15, 15),             # K = 1, one full tile
+    (64, 4, 30, 64, 15, 15),            # N < K
+    (64, 6, 7 * TT - 5, 48, 12, 15),
+]
+
+
+@pytest.mark.parametrize("case", PROT_CASES)
+def test_protected_tc_every_failure(ne, orc, case):
+    w, M, N, K, bc, bg = case
+    p = ne.ne_params(M, w)
+    gen = synth.rng(N + K + M + w)
+    c = synth.uniform_int(gen, (M, N), -(1 << bc), 1 << bc)
+    c[:, 0] = (1 << bc) - 1
+    c[:, -1] = -(1 << bc)
+    g = synth.uniform_int(gen, (K,), -(1 << bg) + 1, 1 << bg)
+    assert K * (1 << bc) * ((1 << bg) - 1) <= p.d_max_exact
+    plain = orc.conv(c, g, w)
+    cd, gd = dev(c, w), torch.from_numpy(g.astype(np.int32)).cuda()
+    modes = [(ne.NE_FAIL_NONE, -1)] + [(fm, r) for fm in (ne.NE_FAIL_SKIP,
+                                                          ne.NE_FAIL_DROP)
+                                       for r in range(M)]
+    for fm, r in modes:
+        d = torch.full((M, N + K - 1), 77, dtype=dt(w), device="cuda")
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(1 << bc), (1 << bc) - 1),
+                             max_abs_g=(1 << bg) - 1, failed=r, fail_mode=fm)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), plain), (fm, r)
+
+
+def test_same_cases_on_the_multiply_add_kernels(ne):
+    """NE_CONV_TC=0 (read once per process, hence the child run): every case
+    above through the multiply-add kernels."""
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ, NE_CONV_TC="0")
+    out = subprocess.run(
+        [sys.executable, "-m", "pytest", __file__, "-q", "-x", "-m", "gpu",
+         "-p", "no:cacheprovider", "-k", "not multiply_add"],
+        env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout[-3000:] + out.stderr[-2000:]
+    assert " passed" in out.stdout
