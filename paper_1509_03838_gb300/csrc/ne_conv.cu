@@ -753,7 +753,8 @@ inline bool tc_eligible(int mode, int K, long long max_abs_g) {
          K <= TC_MAX_K && max_abs_g >= 0 && max_abs_g <= TC_MAX_G;
 }
 
-// Persistent tensor-core launch: the grid is the resident block count.
+// Persistent tensor-core launch: the raw-input buffers (aligned rows only)
+// are dynamic shared memory; the grid is the resident block count.
 template <typename Kern>
 int launch_tc_persistent(Kern kernel, size_t dyn, const ConvArgs& a,
                          cudaStream_t s, std::once_flag& once, int& per_sm,
@@ -778,8 +779,9 @@ template <typename W, bool VEC, bool BIAS, bool ENT>
 int launch_tc_conv_v(const ConvArgs& a, cudaStream_t s) {
   static std::once_flag once;
   static int per_sm = 1, attr = NE_OK;
-  return launch_tc_persistent(tc_conv_kernel<W, VEC, BIAS, ENT>, 0, a, s,
-                              once, per_sm, attr);
+  return launch_tc_persistent(tc_conv_kernel<W, VEC, BIAS, ENT>,
+                              VEC ? tc_raw_bytes<W, ENT>() : 0, a, s, once,
+                              per_sm, attr);
 }
 
 // ENT: entangle on load (x holds the raw streams, a.l the shift).

@@ -192,6 +192,91 @@ __device__ __forceinline__ void tc_stage(const W* __restrict__ row,
   }
 }
 
+// ---- prefetch of raw inputs (16-byte aligned rows) ------------------------
+// 16-byte cp.async of src_bytes (0, 8 or 16) from global memory, the rest
+// zero-filled; src is always a valid address.
+__device__ __forceinline__ void tc_cp16(void* dst, const void* src,
+                                        uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tc_cp_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tc_cp_wait() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Start copying the raw inputs [n0 - 64, n0 + TC_TILE) of row (and prow
+// with ENT) into raw (rawp): 16-byte chunk c to bytes [16c, 16c + 16).
+// Chunks start at multiples of 16 bytes (n0 - 64 does), so each is whole,
+// cut at N, or outside; outside words arrive as zeros.  No barrier.
+template <typename W, bool ENT>
+__device__ __forceinline__ void tc_prefetch(const W* __restrict__ row,
+                                            const W* __restrict__ prow,
+                                            int64_t N, int64_t n0, W* raw,
+                                            W* rawp) {
+  constexpr int V = 16 / (int)sizeof(W);
+  for (int c = threadIdx.x; c < TC_STAGE / V; c += TC_THREADS) {
+    const int64_t gi = n0 - TC_KP + (int64_t)c * V;
+    uint32_t bytes = 0;
+    int64_t at = 0;
+    if (gi >= 0 && gi < N) {
+      bytes = (uint32_t)(lmin(gi + V, N) - gi) * (uint32_t)sizeof(W);
+      at = gi;
+    }
+    tc_cp16(raw + c * V, row + at, bytes);
+    if constexpr (ENT) tc_cp16(rawp + c * V, prow + at, bytes);
+  }
+  tc_cp_commit();
+}
+
+// Digits of the staged raw inputs, as tc_stage but from shared memory: a
+// thread converts 16-byte chunks t, t + THREADS, ... (consecutive threads
+// read consecutive chunks and write consecutive digit pairs).  Operands
+// outside [0, N) are zero and are not shifted.  No barrier.
+template <typename W, bool ENT>
+__device__ __forceinline__ void tc_stage_raw(const W* raw, const W* rawp,
+                                             int64_t N, int64_t n0, int l,
+                                             uint32_t bias_lo, TcShared& sh) {
+  constexpr int V = 16 / (int)sizeof(W);  // words per chunk: 2 or 4
+  for (int c = threadIdx.x; c < TC_STAGE / V; c += TC_THREADS) {
+    const int64_t gi = n0 - TC_KP + (int64_t)c * V;
+    using VT = typename Vec<W>::T;
+    const VT x = *reinterpret_cast<const VT*>(raw + c * V);
+    const W* px = reinterpret_cast<const W*>(&x);
+    W py[V];
+    if constexpr (ENT) {
+      const VT y = *reinterpret_cast<const VT*>(rawp + c * V);
+#pragma unroll
+      for (int e = 0; e < V; ++e) py[e] = reinterpret_cast<const W*>(&y)[e];
+    }
+    uint32_t v[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      uint32_t o = (uint32_t)px[e];
+      if constexpr (ENT) o += l < 32 ? (uint32_t)py[e] << l : 0u;
+      v[e] = (gi + e >= 0 && gi + e < N) ? o - bias_lo : 0u;
+    }
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) {
+      const int j = tc_pad(c * V + 2 * h);
+      *reinterpret_cast<uint32_t*>(&sh.d[0][j]) = tc_digit_pair<0>(v[2 * h], v[2 * h + 1]);
+      *reinterpret_cast<uint32_t*>(&sh.d[1][j]) = tc_digit_pair<1>(v[2 * h], v[2 * h + 1]);
+      *reinterpret_cast<uint32_t*>(&sh.d[2][j]) = tc_digit_pair<2>(v[2 * h], v[2 * h + 1]);
+      *reinterpret_cast<uint32_t*>(&sh.d[3][j]) = tc_digit_pair<3>(v[2 * h], v[2 * h + 1]);
+    }
+  }
+}
+
+// Bytes of dynamic shared memory of the raw buffers.
+template <typename W, bool ENT>
+__host__ __device__ constexpr size_t tc_raw_bytes() {
+  return (size_t)TC_STAGE * sizeof(W) * (ENT ? 2 : 1);
+}
+
 __device__ __forceinline__ void tc_mma(float (&c)[4], const uint32_t (&a)[4],
                                        uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -227,10 +312,14 @@ __device__ __forceinline__ void tc_ntile(uint32_t sbase, int ob, int lane,
       asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                    : "=r"(b0), "=r"(b1), "=r"(b2), "=r"(b3)
                    : "r"(addr));
+      // the two tap digits feed different accumulators: alternate them so
+      // that no product waits on the one issued just before it
 #pragma unroll
-      for (int jg = 0; jg < TC_NG; ++jg) {
-        tc_mma(c[i + jg], a[jg][kk], b0, b1);
-        if (kk + 1 < TC_KS) tc_mma(c[i + jg], a[jg][kk + 1], b2, b3);
+      for (int jg = 0; jg < TC_NG; ++jg) tc_mma(c[i + jg], a[jg][kk], b0, b1);
+      if (kk + 1 < TC_KS) {
+#pragma unroll
+        for (int jg = 0; jg < TC_NG; ++jg)
+          tc_mma(c[i + jg], a[jg][kk + 1], b2, b3);
       }
     }
   }
@@ -290,6 +379,9 @@ template <typename W, bool VEC, bool BIAS, bool ENT = false>
 __global__ void __launch_bounds__(TC_THREADS, 4)
 tc_conv_kernel(const ConvArgs p) {
   __shared__ __align__(16) TcShared sh;
+  extern __shared__ int4 tc_dyn[];  // raw inputs (VEC): row, then prow
+  W* raw = reinterpret_cast<W*>(tc_dyn);
+  W* rawp = raw + TC_STAGE;
   const unsigned long long shift_c = tc_block_setup<BIAS>(p, sh);
   uint32_t a[TC_NG][TC_KS][4];
   tc_a_fragments(sh, threadIdx.x & 31, a);
@@ -298,17 +390,53 @@ tc_conv_kernel(const ConvArgs p) {
   const int64_t total = p.ntiles * p.M;
   // units tile by tile: the M streams of a tile run close together, so the
   // neighbouring stream's rows an entangling load reads are still in L2
-#pragma unroll 1
-  for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+  auto live = [&](int64_t u) {
+    return ((p.live_mask >> (int)(u % p.M)) & 1u) != 0;
+  };
+  auto next = [&](int64_t u) {
+    while (u < total && !live(u)) u += gridDim.x;
+    return u;
+  };
+  auto unit = [&](int64_t u, const W*& row, const W*& prow, int64_t& n0,
+                  int& m) {
     const int64_t tile = u / p.M;
-    const int m = (int)(u - tile * p.M);
-    if (!((p.live_mask >> m) & 1u)) continue;  // uniform over the block
-    const int64_t n0 = tile * TC_TILE;
-    const W* row = reinterpret_cast<const W*>(p.x) + (int64_t)m * p.ldx;
-    const W* prow = reinterpret_cast<const W*>(p.x) +
-                    (int64_t)(m == 0 ? p.M - 1 : m - 1) * p.ldx;
-    tc_stage<W, ENT, VEC>(row, prow, p.N, n0, p.l, (uint32_t)p.bias, sh);
-    __syncthreads();
+    m = (int)(u - tile * p.M);
+    n0 = tile * TC_TILE;
+    row = reinterpret_cast<const W*>(p.x) + (int64_t)m * p.ldx;
+    prow = reinterpret_cast<const W*>(p.x) +
+           (int64_t)(m == 0 ? p.M - 1 : m - 1) * p.ldx;
+  };
+  int64_t u = next(blockIdx.x);
+  if (VEC && u < total) {
+    const W *row, *prow;
+    int64_t n0;
+    int m;
+    unit(u, row, prow, n0, m);
+    tc_prefetch<W, ENT>(row, prow, p.N, n0, raw, rawp);
+  }
+#pragma unroll 1
+  while (u < total) {
+    const W *row, *prow;
+    int64_t n0;
+    int m;
+    unit(u, row, prow, n0, m);
+    const int64_t un = next(u + gridDim.x);
+    if constexpr (VEC) {
+      tc_cp_wait();
+      __syncthreads();  // this unit's raw inputs have landed
+      tc_stage_raw<W, ENT>(raw, rawp, p.N, n0, p.l, (uint32_t)p.bias, sh);
+      __syncthreads();  // digits ready; the raw buffers are free
+      if (un < total) {  // the next unit's inputs arrive during this product
+        const W *nr, *np;
+        int64_t nn0;
+        int nm;
+        unit(un, nr, np, nn0, nm);
+        tc_prefetch<W, ENT>(nr, np, p.N, nn0, raw, rawp);
+      }
+    } else {
+      tc_stage<W, ENT, false>(row, prow, p.N, n0, p.l, (uint32_t)p.bias, sh);
+      __syncthreads();
+    }
     const bool edge = n0 < (int64_t)p.K - 1 || n0 + TC_TILE > p.N;
     W* yrow = reinterpret_cast<W*>(p.y) + (int64_t)m * p.ldy;
 #pragma unroll 1
@@ -323,6 +451,7 @@ tc_conv_kernel(const ConvArgs p) {
           yrow[n] = (W)(out[q] + tc_shift<BIAS>(p, sh, edge, shift_c, n));
       }
     }
-    __syncthreads();  // the next tile's digits overwrite these
+    __syncthreads();  // the next unit's digits overwrite these
+    u = un;
   }
 }
