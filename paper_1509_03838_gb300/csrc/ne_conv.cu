@@ -577,6 +577,7 @@ constexpr int CLUSTER_K_MIN_I32_M3 = 48;
 // tensor-core convolution (32-bit operands, |taps| < 2^15, K <= 65)
 // ---------------------------------------------------------------------------
 #include "ne_conv_tc.cuh"
+#include "ne_conv_tc5.cuh"
 
 // ---------------------------------------------------------------------------
 // host launchers
@@ -703,15 +704,17 @@ int launch_cluster(const ConvArgs& a, bool vec, cudaStream_t s) {
 // blocks all fit on the device at once (at most 4 per SM) takes clusters
 // whatever K is: nothing waits to be co-scheduled, and the arrival words'
 // workspace clear would be a second launch on a latency-bound call.
-// NE_PROT_KERNEL=cluster or =arrival forces one form (clusters only for
-// 3 <= M <= 8).
-enum ProtForm { FORM_AUTO, FORM_CLUSTER, FORM_ARRIVAL };
+// NE_PROT_KERNEL=cluster or =arrival forces one multiply-add form (clusters
+// only for 3 <= M <= 8); =twopass forces the tensor-core two-pass form
+// (products, then a recovery pass) where the fused one would run.
+enum ProtForm { FORM_AUTO, FORM_CLUSTER, FORM_ARRIVAL, FORM_TWOPASS };
 
 inline ProtForm forced_form() {
   static const ProtForm f = [] {
     const char* e = getenv("NE_PROT_KERNEL");
     if (e && strcmp(e, "arrival") == 0) return FORM_ARRIVAL;
     if (e && strcmp(e, "cluster") == 0) return FORM_CLUSTER;
+    if (e && strcmp(e, "twopass") == 0) return FORM_TWOPASS;
     return FORM_AUTO;
   }();
   return f;
@@ -743,6 +746,15 @@ int dispatch_cluster(const ConvArgs& a, int w, int mode, bool vec,
 inline bool tc_enabled() {
   static const bool off = [] {
     const char* e = getenv("NE_CONV_TC");
+    return e && strcmp(e, "0") == 0;
+  }();
+  return !off;
+}
+
+// NE_CONV_TC5=0 keeps the mma.sync kernels where the tcgen05 ones would run.
+inline bool tc5_enabled() {
+  static const bool off = [] {
+    const char* e = getenv("NE_CONV_TC5");
     return e && strcmp(e, "0") == 0;
   }();
   return !off;
@@ -780,7 +792,7 @@ int launch_tc_conv_v(const ConvArgs& a, cudaStream_t s) {
   static std::once_flag once;
   static int per_sm = 1, attr = NE_OK;
   return launch_tc_persistent(tc_conv_kernel<W, VEC, BIAS, ENT>,
-                              VEC ? tc_raw_bytes<W, ENT>() : 0, a, s, once,
+                              VEC ? (size_t)TC_STAGE * sizeof(W) * (ENT ? 2 : 1) : 0, a, s, once,
                               per_sm, attr);
 }
 
@@ -795,6 +807,77 @@ int dispatch_tc_conv(const ConvArgs& a, int w, bool vec, cudaStream_t s) {
                : launch_tc_conv_v<int64_t, false, true, ENT>(a, s);
   return vec ? launch_tc_conv_v<int64_t, true, false, ENT>(a, s)
              : launch_tc_conv_v<int64_t, false, false, ENT>(a, s);
+}
+
+// Fused protected tensor-core launch: dynamic shared memory and the
+// resident block count depend on M (the tile is 128 floor(32 / M)).
+template <typename W, bool VEC, bool BIAS>
+int launch_tc_prot_v(const ConvArgs& a, bool vec_out, cudaStream_t s) {
+  static std::once_flag once;
+  static int attr = NE_OK;
+  static int per_sm[TCP_MAX_M + 1] = {};
+  std::call_once(once, [] {
+    size_t most = 0;
+    for (int M = TCP_MIN_M; M <= TCP_MAX_M; ++M)
+      most = std::max(most, tcp_smem_bytes<W>(M, VEC));
+    attr = set_max_smem(tc_prot_kernel<W, VEC, BIAS>, most);
+    for (int M = TCP_MIN_M; M <= TCP_MAX_M; ++M) {
+      int n = 0;
+      per_sm[M] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                      &n, tc_prot_kernel<W, VEC, BIAS>, TCP_THREADS,
+                      tcp_smem_bytes<W>(M, VEC)) == cudaSuccess && n > 0
+                      ? n
+                      : 1;
+    }
+    cudaGetLastError();
+  });
+  if (attr != NE_OK) return attr;
+  const int64_t grid =
+      std::min<int64_t>(a.ntiles, (int64_t)sm_count() * per_sm[a.M]);
+  tc_prot_kernel<W, VEC, BIAS>
+      <<<(unsigned)grid, TCP_THREADS, tcp_smem_bytes<W>(a.M, VEC), s>>>(
+          a, vec_out);
+  return status_from_cuda(cudaGetLastError());
+}
+
+// Fused protected tcgen05 launch: one warp-specialised block per SM (its
+// shared memory keeps a second off; it takes all of the SM's tensor
+// memory), at most one per tile.
+template <typename W, bool BIAS, int MM>
+int launch_tc5_prot_v(const ConvArgs& a, bool, cudaStream_t s) {
+  static std::once_flag once;
+  static int attr = NE_OK;
+  std::call_once(once, [] {
+    attr = set_max_smem(tc5p_prot_kernel<W, BIAS, MM>, t5p_smem_bytes<W>(MM));
+  });
+  if (attr != NE_OK) return attr;
+  const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)sm_count());
+  tc5p_prot_kernel<W, BIAS, MM>
+      <<<(unsigned)grid, T5P_THREADS, t5p_smem_bytes<W>(MM), s>>>(a);
+  return status_from_cuda(cudaGetLastError());
+}
+
+int dispatch_tc5_prot(const ConvArgs& a, int w, bool vec_out, cudaStream_t s) {
+  if (w == 32)
+    return a.M == 3 ? launch_tc5_prot_v<int32_t, false, 3>(a, vec_out, s)
+                    : launch_tc5_prot_v<int32_t, false, 4>(a, vec_out, s);
+  if (a.bias != 0)
+    return a.M == 3 ? launch_tc5_prot_v<int64_t, true, 3>(a, vec_out, s)
+                    : launch_tc5_prot_v<int64_t, true, 4>(a, vec_out, s);
+  return a.M == 3 ? launch_tc5_prot_v<int64_t, false, 3>(a, vec_out, s)
+                  : launch_tc5_prot_v<int64_t, false, 4>(a, vec_out, s);
+}
+
+int dispatch_tc_prot(const ConvArgs& a, int w, bool vec, bool vec_out,
+                     cudaStream_t s) {
+  if (w == 32)
+    return vec ? launch_tc_prot_v<int32_t, true, false>(a, vec_out, s)
+               : launch_tc_prot_v<int32_t, false, false>(a, vec_out, s);
+  if (a.bias != 0)
+    return vec ? launch_tc_prot_v<int64_t, true, true>(a, vec_out, s)
+               : launch_tc_prot_v<int64_t, false, true>(a, vec_out, s);
+  return vec ? launch_tc_prot_v<int64_t, true, false>(a, vec_out, s)
+             : launch_tc_prot_v<int64_t, false, false>(a, vec_out, s);
 }
 
 template <bool PROT>
@@ -1014,9 +1097,27 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
-  if (tc_eligible(mode, K, max_abs_g) && forced_form() == FORM_AUTO) {
-    // tensor cores: every computing stream's entangled product delta_m into
-    // d (entangled on load), then the recovery of all M in place
+  const ProtForm form = forced_form();
+  if (tc_eligible(mode, K, max_abs_g) && form == FORM_AUTO &&
+      M <= T5_MAX_M && vec && tc5_enabled()) {
+    // fifth-generation tensor cores, fused: products in tensor memory,
+    // recovery in the epilogue's registers
+    ConvArgs t = a;
+    t.ntiles = (Nout + T5_TILE - 1) / T5_TILE;
+    return dispatch_tc5_prot(t, w, rows_aligned16(d, ldd, wb), s);
+  }
+  if (tc_eligible(mode, K, max_abs_g) && form == FORM_AUTO &&
+      M <= TCP_MAX_M) {
+    // tensor cores, fused: products and recovery tile by tile in one kernel
+    ConvArgs t = a;
+    t.ntiles = (Nout + tcp_tile(M) - 1) / tcp_tile(M);
+    return dispatch_tc_prot(t, w, vec, rows_aligned16(d, ldd, wb), s);
+  }
+  if (tc_eligible(mode, K, max_abs_g) &&
+      (form == FORM_AUTO || form == FORM_TWOPASS)) {
+    // tensor cores, two passes: every computing stream's entangled product
+    // delta_m into d (entangled on load), then the recovery of all M in
+    // place
     ConvArgs t = a;
     t.ntiles = (Nout + TC_TILE - 1) / TC_TILE;
     const uint32_t all = M == 32 ? 0xffffffffu : (1u << M) - 1u;

@@ -20,15 +20,31 @@
 // ldmatrix.  One warp covers 128 outputs with 4 x 2 x 5 = 40 mma.sync per
 // N-tile (operand digit x tap digit x k-step).
 //
-// Shared-memory layout of the staged digits: word j at j + 8 (j / 64), so
-// that the eight windows of an ldmatrix (32 bytes apart) fall in distinct
-// banks; each window's 8 words stay within one 64-word group.
+// Shared-memory layout of the staged digits: one array of S halves per
+// digit (S a multiple of 64, arrays 128-byte aligned); word j sits at
+// j ^ ((j >> 3) & 8), i.e. in every second group of eight 16-byte chunks
+// the chunks swap in pairs.  The eight rows of an ldmatrix matrix are
+// chunks c, c + 2, ..., c + 14; after the swap they fall in eight distinct
+// 16-byte bank groups, with no padding.
+//
+// Two kernels:
+//   tc_conv_kernel  one (tile, stream) unit at a time: the plain product,
+//                   or (ENT) the entangled products delta_m of the
+//                   protected path's two-pass form (recovery follows as a
+//                   separate pass);
+//   tc_prot_kernel  the fused protected convolution: one output tile of
+//                   every stream per unit, entangled from the raw rows in
+//                   shared memory (Eq. 6), the products delta_m kept in
+//                   shared memory and all M outputs recovered from M - 1 of
+//                   them (Eq. 16-19) before the tile is written.
 //
 // Included by ne_conv.cu inside its anonymous namespace (it uses ConvArgs
 // and the tap-prefix helpers).
 #pragma once
 
 #include <cuda_fp16.h>
+
+#include <type_traits>
 
 constexpr int TC_THREADS = 128;
 constexpr int TC_WARPS = TC_THREADS / 32;
@@ -43,18 +59,45 @@ constexpr int TC_MAX_K = TC_KP + 1;
 constexpr long long TC_MAX_G = 32768;  // |g| <= 2^15: digits in [-128, 128]
 constexpr int TC_RT = 98;                       // reversed tap digits per copy
 constexpr int TC_TAPS = 80;                     // taps kept for the range shift
-__host__ __device__ constexpr int tc_pad(int j) { return j + ((j >> 6) << 3); }
 constexpr int TC_STAGE = TC_TILE + TC_KP;       // staged inputs per tile
-constexpr int TC_STAGE_P = tc_pad(TC_STAGE) + 8;
-static_assert(TC_STAGE % 8 == 0, "staging runs of 8");
+static_assert(TC_STAGE % 64 == 0, "digit arrays of whole 128-byte groups");
 
-struct TcShared {
-  uint16_t d[TC_ND][TC_STAGE_P];    // staged digits (fp16)
+// Fused protected kernel: 8 warps, two blocks per SM; a unit is T outputs
+// of each of the M streams, T = 128 floor(32 / M), so that a unit holds
+// about 32 N-tiles (four per warp) whatever M.
+constexpr int TCP_THREADS = 256;
+constexpr int TCP_WARPS = TCP_THREADS / 32;
+constexpr int TCP_MIN_M = 3;
+constexpr int TCP_MAX_M = 8;
+__host__ __device__ constexpr int tcp_tile(int M) { return 128 * (32 / M); }
+
+__host__ __device__ constexpr int tc_swz(int j) { return j ^ ((j >> 3) & 8); }
+
+// Slot of product word j in a stream's row of the fused kernel's product
+// tile: 32 bytes of padding after every 32 words, so that the strided
+// stores of an mma fragment (8 consecutive words at 4 offsets 32 apart)
+// spread over all banks.
+template <typename W>
+__host__ __device__ constexpr int tcp_dpad(int j) {
+  return j + (j >> 5) * (32 / (int)sizeof(W));
+}
+
+struct TcTaps {
   uint16_t rt[TC_NG][2][TC_RT];     // reversed tap digits, two parity copies
   int taps[TC_TAPS];
   long long pref[TC_TAPS];
-  long long warp_sums[TC_THREADS / 32];
+  long long warp_sums[16];           // one per warp of a block (<= 16)
 };
+
+// Bytes of the fused kernel's dynamic shared memory: digits of M streams,
+// their products, the raw rows (vec: the prefetch buffer) and the taps.
+template <typename W>
+__host__ __device__ constexpr size_t tcp_smem_bytes(int M, bool vec) {
+  return (size_t)M * TC_ND * (tcp_tile(M) + TC_KP) * 2 +
+         (size_t)M * tcp_dpad<W>(tcp_tile(M)) * sizeof(W) +
+         (vec ? (size_t)M * (tcp_tile(M) + TC_KP) * sizeof(W) : 0) +
+         sizeof(TcTaps);
+}
 
 __device__ __forceinline__ uint16_t tc_half(int v) {
   return __half_as_ushort(__int2half_rn(v));
@@ -81,14 +124,26 @@ __device__ __forceinline__ uint32_t tc_digit_pair(uint32_t a, uint32_t b) {
   return h;
 }
 
+// The digits of operands a, b (words j, j + 1 of a stream, j even) into the
+// four digit arrays dg + i S (SWZ: at the swizzled slot of j; else at j).
+template <bool SWZ = true>
+__device__ __forceinline__ void tc_put_pair(uint16_t* dg, int S, int j,
+                                            uint32_t a, uint32_t b) {
+  const int js = SWZ ? tc_swz(j) : j;
+  *reinterpret_cast<uint32_t*>(dg + js) = tc_digit_pair<0>(a, b);
+  *reinterpret_cast<uint32_t*>(dg + S + js) = tc_digit_pair<1>(a, b);
+  *reinterpret_cast<uint32_t*>(dg + 2 * S + js) = tc_digit_pair<2>(a, b);
+  *reinterpret_cast<uint32_t*>(dg + 3 * S + js) = tc_digit_pair<3>(a, b);
+}
+
 // Taps: reversed digits R_j[u] = digit_j(g[79 - u]) (zero outside [0, K)),
 // copy c stored from position c on, so that every pair (R[u], R[u + 1]) an
 // A fragment needs is one aligned 32-bit word of one copy.  With BIAS also
 // the taps themselves for the range shift.  Contains no barrier.
 template <bool BIAS>
 __device__ __forceinline__ void tc_load_taps(const int32_t* __restrict__ g,
-                                             int K, TcShared& sh) {
-  for (int idx = threadIdx.x; idx < TC_NG * 2 * TC_RT; idx += TC_THREADS) {
+                                             int K, TcTaps& tt) {
+  for (int idx = threadIdx.x; idx < TC_NG * 2 * TC_RT; idx += blockDim.x) {
     const int jg = idx / (2 * TC_RT);
     const int rem = idx - jg * 2 * TC_RT;
     const int cp = rem / TC_RT;
@@ -101,16 +156,16 @@ __device__ __forceinline__ void tc_load_taps(const int32_t* __restrict__ g,
       const int g0 = (int)(int8_t)(gv & 0xff);
       v = jg == 0 ? g0 : (gv - g0) >> 8;
     }
-    sh.rt[jg][cp][pos] = tc_half(v);
+    tt.rt[jg][cp][pos] = tc_half(v);
   }
   if constexpr (BIAS) {
-    for (int t = threadIdx.x; t < TC_TAPS; t += TC_THREADS)
-      sh.taps[t] = t < K ? __ldg(g + t) : 0;
+    for (int t = threadIdx.x; t < TC_TAPS; t += blockDim.x)
+      tt.taps[t] = t < K ? __ldg(g + t) : 0;
   }
 }
 
 // This thread's A fragments: H_j[o][k] = R_j[15 - o + 16 kk + k].
-__device__ __forceinline__ void tc_a_fragments(const TcShared& sh, int lane,
+__device__ __forceinline__ void tc_a_fragments(const TcTaps& tt, int lane,
                                                uint32_t (&a)[TC_NG][TC_KS][4]) {
   const int gq = lane >> 2, tq = lane & 3;
   // 15 - o is even for odd o: copy 0; else copy 1 (shifted by one)
@@ -124,77 +179,44 @@ __device__ __forceinline__ void tc_a_fragments(const TcShared& sh, int lane,
         const int o = gq + 8 * (r & 1);
         const int k = 2 * tq + 8 * (r >> 1);
         const int pos = 15 - o + 16 * kk + k + cp;
-        a[jg][kk][r] = *reinterpret_cast<const uint32_t*>(&sh.rt[jg][cp][pos]);
+        a[jg][kk][r] = *reinterpret_cast<const uint32_t*>(&tt.rt[jg][cp][pos]);
       }
 }
 
-// Stage the digits of the inputs [n0 - 64, n0 + TC_TILE) of one stream: the
-// operand is the low 32 bits of (row + (prow << l) with ENT) minus the range
-// shift; inputs outside [0, N) are zero and are not shifted.  Runs of 8
-// inputs per thread, one 16-byte store per digit.  Contains no barrier.
-template <typename W, bool ENT, bool VEC>
-__device__ __forceinline__ void tc_stage(const W* __restrict__ row,
-                                         const W* __restrict__ prow, int64_t N,
-                                         int64_t n0, int l, uint32_t bias_lo,
-                                         TcShared& sh) {
-  for (int r = threadIdx.x; r < TC_STAGE / 8; r += TC_THREADS) {
+// Stage, straight from global memory, the digits of the inputs
+// [n0 - 64, n0 + S - 64) of one stream (rows without 16-byte alignment):
+// the operand is the low 32 bits of row (+ prow << l with ENT) minus the
+// range shift; inputs outside [0, N) are zero and are not shifted.  Thread
+// tid of NT takes runs of 8 inputs tid, tid + NT, ...  Contains no barrier.
+template <typename W, bool ENT>
+__device__ __forceinline__ void tc_stage_global(const W* __restrict__ row,
+                                                const W* __restrict__ prow,
+                                                int64_t N, int64_t n0, int l,
+                                                uint32_t bias_lo, uint16_t* dg,
+                                                int S, int tid, int NT) {
+  for (int r = tid; r < S / 8; r += NT) {
     const int64_t gi = n0 - TC_KP + 8 * r;
     uint32_t v[8];
-    if (VEC && gi >= 0 && gi + 8 <= N) {
-      using VT = typename Vec<W>::T;
-      constexpr int V = Vec<W>::n;
 #pragma unroll
-      for (int q = 0; q < 8 / V; ++q) {
-        const VT x = __ldg(reinterpret_cast<const VT*>(row + gi) + q);
-        const W* px = reinterpret_cast<const W*>(&x);
-        W xp[V];
-        if constexpr (ENT) {
-          const VT y = __ldg(reinterpret_cast<const VT*>(prow + gi) + q);
-          const W* py = reinterpret_cast<const W*>(&y);
-#pragma unroll
-          for (int e = 0; e < V; ++e) xp[e] = py[e];
-        }
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-          uint32_t o = (uint32_t)px[e];
-          if constexpr (ENT) o += l < 32 ? (uint32_t)xp[e] << l : 0u;
-          v[q * V + e] = o - bias_lo;
-        }
+    for (int e = 0; e < 8; ++e) {
+      const int64_t gq = gi + e;
+      uint32_t o = 0;
+      if (gq >= 0 && gq < N) {
+        o = (uint32_t)__ldg(row + gq);
+        if constexpr (ENT) o += l < 32 ? (uint32_t)__ldg(prow + gq) << l : 0u;
+        o -= bias_lo;
       }
-    } else {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int64_t gq = gi + e;
-        uint32_t o = 0;
-        if (gq >= 0 && gq < N) {
-          o = (uint32_t)__ldg(row + gq);
-          if constexpr (ENT)
-            o += l < 32 ? (uint32_t)__ldg(prow + gq) << l : 0u;
-          o -= bias_lo;
-        }
-        v[e] = o;
-      }
+      v[e] = o;
     }
-    const int jo = tc_pad(8 * r);
-    uint4 q0, q1, q2, q3;
-    q0.x = tc_digit_pair<0>(v[0], v[1]); q0.y = tc_digit_pair<0>(v[2], v[3]);
-    q0.z = tc_digit_pair<0>(v[4], v[5]); q0.w = tc_digit_pair<0>(v[6], v[7]);
-    q1.x = tc_digit_pair<1>(v[0], v[1]); q1.y = tc_digit_pair<1>(v[2], v[3]);
-    q1.z = tc_digit_pair<1>(v[4], v[5]); q1.w = tc_digit_pair<1>(v[6], v[7]);
-    q2.x = tc_digit_pair<2>(v[0], v[1]); q2.y = tc_digit_pair<2>(v[2], v[3]);
-    q2.z = tc_digit_pair<2>(v[4], v[5]); q2.w = tc_digit_pair<2>(v[6], v[7]);
-    q3.x = tc_digit_pair<3>(v[0], v[1]); q3.y = tc_digit_pair<3>(v[2], v[3]);
-    q3.z = tc_digit_pair<3>(v[4], v[5]); q3.w = tc_digit_pair<3>(v[6], v[7]);
-    *reinterpret_cast<uint4*>(&sh.d[0][jo]) = q0;
-    *reinterpret_cast<uint4*>(&sh.d[1][jo]) = q1;
-    *reinterpret_cast<uint4*>(&sh.d[2][jo]) = q2;
-    *reinterpret_cast<uint4*>(&sh.d[3][jo]) = q3;
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      tc_put_pair(dg, S, 8 * r + 2 * h, v[2 * h], v[2 * h + 1]);
   }
 }
 
 // ---- prefetch of raw inputs (16-byte aligned rows) ------------------------
-// 16-byte cp.async of src_bytes (0, 8 or 16) from global memory, the rest
-// zero-filled; src is always a valid address.
+// 16-byte cp.async of src_bytes (0, 4, 8, 12 or 16) from global memory, the
+// rest zero-filled; src is always a valid address.
 __device__ __forceinline__ void tc_cp16(void* dst, const void* src,
                                         uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
@@ -209,72 +231,55 @@ __device__ __forceinline__ void tc_cp_wait() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-// Start copying the raw inputs [n0 - 64, n0 + TC_TILE) of row (and prow
-// with ENT) into raw (rawp): 16-byte chunk c to bytes [16c, 16c + 16).
-// Chunks start at multiples of 16 bytes (n0 - 64 does), so each is whole,
-// cut at N, or outside; outside words arrive as zeros.  No barrier.
-template <typename W, bool ENT>
-__device__ __forceinline__ void tc_prefetch(const W* __restrict__ row,
-                                            const W* __restrict__ prow,
-                                            int64_t N, int64_t n0, W* raw,
-                                            W* rawp) {
+// Start copying 16-byte chunk c of the raw inputs [n0 - 64, n0 + S - 64) of
+// row into raw + c V (V words per chunk).  Chunks start at multiples of 16
+// bytes (n0 - 64 does), so each is whole, cut at N, or outside; outside
+// words arrive as zeros.
+template <typename W>
+__device__ __forceinline__ void tc_prefetch_chunk(const W* __restrict__ row,
+                                                  int64_t N, int64_t n0, int c,
+                                                  W* raw) {
   constexpr int V = 16 / (int)sizeof(W);
-  for (int c = threadIdx.x; c < TC_STAGE / V; c += TC_THREADS) {
-    const int64_t gi = n0 - TC_KP + (int64_t)c * V;
-    uint32_t bytes = 0;
-    int64_t at = 0;
-    if (gi >= 0 && gi < N) {
-      bytes = (uint32_t)(lmin(gi + V, N) - gi) * (uint32_t)sizeof(W);
-      at = gi;
-    }
-    tc_cp16(raw + c * V, row + at, bytes);
-    if constexpr (ENT) tc_cp16(rawp + c * V, prow + at, bytes);
+  const int64_t gi = n0 - TC_KP + (int64_t)c * V;
+  uint32_t bytes = 0;
+  int64_t at = 0;
+  if (gi >= 0 && gi < N) {
+    bytes = (uint32_t)(lmin(gi + V, N) - gi) * (uint32_t)sizeof(W);
+    at = gi;
   }
-  tc_cp_commit();
+  tc_cp16(raw + c * V, row + at, bytes);
 }
 
-// Digits of the staged raw inputs, as tc_stage but from shared memory: a
-// thread converts 16-byte chunks t, t + THREADS, ... (consecutive threads
-// read consecutive chunks and write consecutive digit pairs).  Operands
-// outside [0, N) are zero and are not shifted.  No barrier.
-template <typename W, bool ENT>
-__device__ __forceinline__ void tc_stage_raw(const W* raw, const W* rawp,
-                                             int64_t N, int64_t n0, int l,
-                                             uint32_t bias_lo, TcShared& sh) {
+// Digits of staged raw chunk c: operand = low 32 bits of x (+ xp << l with
+// ENT) minus the range shift, zero outside [0, N) (CHECK = false: the whole
+// staged window lies inside).  Consecutive threads on consecutive chunks
+// read and write shared memory without bank conflicts.
+template <typename W, bool ENT, bool CHECK = true, bool SWZ = true>
+__device__ __forceinline__ void tc_stage_chunk(const W* raw, const W* rawp,
+                                               int64_t N, int64_t n0, int c,
+                                               int l, uint32_t bias_lo,
+                                               uint16_t* dg, int S) {
   constexpr int V = 16 / (int)sizeof(W);  // words per chunk: 2 or 4
-  for (int c = threadIdx.x; c < TC_STAGE / V; c += TC_THREADS) {
-    const int64_t gi = n0 - TC_KP + (int64_t)c * V;
-    using VT = typename Vec<W>::T;
-    const VT x = *reinterpret_cast<const VT*>(raw + c * V);
-    const W* px = reinterpret_cast<const W*>(&x);
-    W py[V];
-    if constexpr (ENT) {
-      const VT y = *reinterpret_cast<const VT*>(rawp + c * V);
+  using VT = typename Vec<W>::T;
+  const int64_t gi = n0 - TC_KP + (int64_t)c * V;
+  const VT x = *reinterpret_cast<const VT*>(raw + c * V);
+  const W* px = reinterpret_cast<const W*>(&x);
+  W py[V];
+  if constexpr (ENT) {
+    const VT y = *reinterpret_cast<const VT*>(rawp + c * V);
 #pragma unroll
-      for (int e = 0; e < V; ++e) py[e] = reinterpret_cast<const W*>(&y)[e];
-    }
-    uint32_t v[V];
-#pragma unroll
-    for (int e = 0; e < V; ++e) {
-      uint32_t o = (uint32_t)px[e];
-      if constexpr (ENT) o += l < 32 ? (uint32_t)py[e] << l : 0u;
-      v[e] = (gi + e >= 0 && gi + e < N) ? o - bias_lo : 0u;
-    }
-#pragma unroll
-    for (int h = 0; h < V / 2; ++h) {
-      const int j = tc_pad(c * V + 2 * h);
-      *reinterpret_cast<uint32_t*>(&sh.d[0][j]) = tc_digit_pair<0>(v[2 * h], v[2 * h + 1]);
-      *reinterpret_cast<uint32_t*>(&sh.d[1][j]) = tc_digit_pair<1>(v[2 * h], v[2 * h + 1]);
-      *reinterpret_cast<uint32_t*>(&sh.d[2][j]) = tc_digit_pair<2>(v[2 * h], v[2 * h + 1]);
-      *reinterpret_cast<uint32_t*>(&sh.d[3][j]) = tc_digit_pair<3>(v[2 * h], v[2 * h + 1]);
-    }
+    for (int e = 0; e < V; ++e) py[e] = reinterpret_cast<const W*>(&y)[e];
   }
-}
-
-// Bytes of dynamic shared memory of the raw buffers.
-template <typename W, bool ENT>
-__host__ __device__ constexpr size_t tc_raw_bytes() {
-  return (size_t)TC_STAGE * sizeof(W) * (ENT ? 2 : 1);
+  uint32_t v[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    uint32_t o = (uint32_t)px[e];
+    if constexpr (ENT) o += l < 32 ? (uint32_t)py[e] << l : 0u;
+    v[e] = (!CHECK || (gi + e >= 0 && gi + e < N)) ? o - bias_lo : 0u;
+  }
+#pragma unroll
+  for (int h = 0; h < V / 2; ++h)
+    tc_put_pair<SWZ>(dg, S, c * V + 2 * h, v[2 * h], v[2 * h + 1]);
 }
 
 __device__ __forceinline__ void tc_mma(float (&c)[4], const uint32_t (&a)[4],
@@ -286,10 +291,12 @@ __device__ __forceinline__ void tc_mma(float (&c)[4], const uint32_t (&a)[4],
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// The 128 outputs [ob, ob + 128) of the staged tile (local indices): this
-// thread's four, at local ob + 16 n + o for (n, o) = (2tq, gq),
-// (2tq + 1, gq), (2tq, gq + 8), (2tq + 1, gq + 8), as 64-bit integers.
-__device__ __forceinline__ void tc_ntile(uint32_t sbase, int ob, int lane,
+// The 128 outputs [ob, ob + 128) of a staged tile (local indices; digit
+// arrays at shared address sbase, S halves apart): this thread's four, at
+// local ob + 16 n + o for (n, o) = (2tq, gq), (2tq + 1, gq), (2tq, gq + 8),
+// (2tq + 1, gq + 8), as 64-bit integers.
+__device__ __forceinline__ void tc_ntile(uint32_t sbase, int S, int ob,
+                                         int lane,
                                          const uint32_t (&a)[TC_NG][TC_KS][4],
                                          long long (&out)[4]) {
   float c[TC_NL][4];
@@ -300,14 +307,14 @@ __device__ __forceinline__ void tc_ntile(uint32_t sbase, int ob, int lane,
   const int q8 = lane >> 3, n8 = lane & 7;
 #pragma unroll
   for (int i = 0; i < TC_ND; ++i) {
-    const uint32_t dbase = sbase + (uint32_t)(i * TC_STAGE_P) * 2u;
+    const uint32_t dbase = sbase + (uint32_t)(i * S) * 2u;
 #pragma unroll
     for (int kk = 0; kk < TC_KS; kk += 2) {
       // matrix q8 of the ldmatrix: k-step kk + q8/2 (the last odd step
       // loads step kk twice and uses one), half q8 % 2; row n8
       const int kq = (kk + (q8 >> 1)) < TC_KS ? kk + (q8 >> 1) : kk;
       const int j = ob + 16 * n8 + 16 * kq + 8 * (q8 & 1);
-      const uint32_t addr = dbase + (uint32_t)tc_pad(j) * 2u;
+      const uint32_t addr = dbase + (uint32_t)tc_swz(j) * 2u;
       uint32_t b0, b1, b2, b3;
       asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                    : "=r"(b0), "=r"(b1), "=r"(b2), "=r"(b3)
@@ -342,30 +349,30 @@ __device__ __forceinline__ int tc_local(int ob, int lane, int q) {
 // the tiles at either end: b G(n) from the prefix sums).
 template <bool BIAS>
 __device__ __forceinline__ long long tc_shift(const ConvArgs& p,
-                                              const TcShared& sh, bool edge,
+                                              const TcTaps& tt, bool edge,
                                               unsigned long long shift_c,
                                               int64_t n) {
   if constexpr (!BIAS) {
     return 0;
   } else {
-    return (long long)(edge ? shift_correction(p.bias, sh.pref, n, p.N, p.K)
+    return (long long)(edge ? shift_correction(p.bias, tt.pref, n, p.N, p.K)
                             : shift_c);
   }
 }
 
-// Taps and (BIAS) the range shift's sums, once per block; the caller loads
-// its A fragments from sh afterwards.  Contains barriers: every thread must
-// call it.
-template <bool BIAS>
+// Taps and (BIAS) the range shift's sums, once per block of NT threads; the
+// caller loads its A fragments from tt afterwards.  Contains barriers: every
+// thread must call it.
+template <bool BIAS, int NT>
 __device__ __forceinline__ unsigned long long tc_block_setup(const ConvArgs& p,
-                                                             TcShared& sh) {
-  tc_load_taps<BIAS>(p.g, p.K, sh);
+                                                             TcTaps& tt) {
+  tc_load_taps<BIAS>(p.g, p.K, tt);
   __syncthreads();
   unsigned long long shift_c = 0;
   if constexpr (BIAS) {
     shift_c = (unsigned long long)p.bias *
-              (unsigned long long)tap_total(sh.taps, p.K, sh.warp_sums);
-    tap_prefix(sh.taps, p.K, sh.pref, sh.warp_sums);
+              (unsigned long long)tap_total<NT>(tt.taps, p.K, tt.warp_sums);
+    tap_prefix<NT>(tt.taps, p.K, tt.pref, tt.warp_sums);
   }
   return shift_c;
 }
@@ -378,15 +385,17 @@ __device__ __forceinline__ unsigned long long tc_block_setup(const ConvArgs& p,
 template <typename W, bool VEC, bool BIAS, bool ENT = false>
 __global__ void __launch_bounds__(TC_THREADS, 4)
 tc_conv_kernel(const ConvArgs p) {
-  __shared__ __align__(16) TcShared sh;
+  __shared__ TcTaps tt;
+  __shared__ __align__(128) uint16_t dg[TC_ND * TC_STAGE];
   extern __shared__ int4 tc_dyn[];  // raw inputs (VEC): row, then prow
   W* raw = reinterpret_cast<W*>(tc_dyn);
   W* rawp = raw + TC_STAGE;
-  const unsigned long long shift_c = tc_block_setup<BIAS>(p, sh);
+  constexpr int CPS = TC_STAGE * (int)sizeof(W) / 16;  // chunks per row
+  const unsigned long long shift_c = tc_block_setup<BIAS, TC_THREADS>(p, tt);
   uint32_t a[TC_NG][TC_KS][4];
-  tc_a_fragments(sh, threadIdx.x & 31, a);
+  tc_a_fragments(tt, threadIdx.x & 31, a);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(&sh.d[0][0]);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(dg);
   const int64_t total = p.ntiles * p.M;
   // units tile by tile: the M streams of a tile run close together, so the
   // neighbouring stream's rows an entangling load reads are still in L2
@@ -406,14 +415,19 @@ tc_conv_kernel(const ConvArgs p) {
     prow = reinterpret_cast<const W*>(p.x) +
            (int64_t)(m == 0 ? p.M - 1 : m - 1) * p.ldx;
   };
-  int64_t u = next(blockIdx.x);
-  if (VEC && u < total) {
+  auto prefetch = [&](int64_t u) {
     const W *row, *prow;
     int64_t n0;
     int m;
     unit(u, row, prow, n0, m);
-    tc_prefetch<W, ENT>(row, prow, p.N, n0, raw, rawp);
-  }
+    for (int c = threadIdx.x; c < CPS; c += TC_THREADS) {
+      tc_prefetch_chunk<W>(row, p.N, n0, c, raw);
+      if constexpr (ENT) tc_prefetch_chunk<W>(prow, p.N, n0, c, rawp);
+    }
+    tc_cp_commit();
+  };
+  int64_t u = next(blockIdx.x);
+  if (VEC && u < total) prefetch(u);
 #pragma unroll 1
   while (u < total) {
     const W *row, *prow;
@@ -424,17 +438,21 @@ tc_conv_kernel(const ConvArgs p) {
     if constexpr (VEC) {
       tc_cp_wait();
       __syncthreads();  // this unit's raw inputs have landed
-      tc_stage_raw<W, ENT>(raw, rawp, p.N, n0, p.l, (uint32_t)p.bias, sh);
-      __syncthreads();  // digits ready; the raw buffers are free
-      if (un < total) {  // the next unit's inputs arrive during this product
-        const W *nr, *np;
-        int64_t nn0;
-        int nm;
-        unit(un, nr, np, nn0, nm);
-        tc_prefetch<W, ENT>(nr, np, p.N, nn0, raw, rawp);
+      if (n0 >= TC_KP && n0 + TC_TILE <= p.N) {
+        for (int c = threadIdx.x; c < CPS; c += TC_THREADS)
+          tc_stage_chunk<W, ENT, false>(raw, rawp, p.N, n0, c, p.l,
+                                        (uint32_t)p.bias, dg, TC_STAGE);
+      } else {
+        for (int c = threadIdx.x; c < CPS; c += TC_THREADS)
+          tc_stage_chunk<W, ENT>(raw, rawp, p.N, n0, c, p.l, (uint32_t)p.bias,
+                                 dg, TC_STAGE);
       }
+      __syncthreads();  // digits ready; the raw buffers are free
+      // the next unit's inputs arrive during this product
+      if (un < total) prefetch(un);
     } else {
-      tc_stage<W, ENT, false>(row, prow, p.N, n0, p.l, (uint32_t)p.bias, sh);
+      tc_stage_global<W, ENT>(row, prow, p.N, n0, p.l, (uint32_t)p.bias, dg,
+                              TC_STAGE, threadIdx.x, TC_THREADS);
       __syncthreads();
     }
     const bool edge = n0 < (int64_t)p.K - 1 || n0 + TC_TILE > p.N;
@@ -443,15 +461,223 @@ tc_conv_kernel(const ConvArgs p) {
     for (int nt = 0; nt < TC_NTW; ++nt) {
       const int ob = (warp * TC_NTW + nt) * 128;
       long long out[4];
-      tc_ntile(sbase, ob, lane, a, out);
+      tc_ntile(sbase, TC_STAGE, ob, lane, a, out);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int64_t n = n0 + tc_local(ob, lane, q);
         if (n < p.Nout)
-          yrow[n] = (W)(out[q] + tc_shift<BIAS>(p, sh, edge, shift_c, n));
+          yrow[n] = (W)(out[q] + tc_shift<BIAS>(p, tt, edge, shift_c, n));
       }
     }
     __syncthreads();  // the next unit's digits overwrite these
     u = un;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Recovery of a tile of the fused kernel: outputs [n0, n0 + T) of all M
+// streams from the products in shared memory (row m of dl, slot
+// tcp_dpad(j)), failed stream r; each thread takes V consecutive outputs at
+// a time.  Product q is row (r + 1 + q) mod M, q < M - 1; the Horner sum of
+// Eq. 16 over them gives d_{r-1} (Eq. 17), and the backward chain
+// d_{j-1} = (delta_j - d_j) >> l the rest (Eq. 18-19, reached around the
+// cycle the other way).  Shared memory serves both passes, so no product
+// row is held in registers.  vec_out: d's rows are 16-byte aligned.
+// ---------------------------------------------------------------------------
+template <typename W, int MM>
+__device__ __forceinline__ void tcp_recover_tile(const W* dl, int dlen, int T,
+                                                 int r, int l, W* y,
+                                                 int64_t ldy, int64_t n0,
+                                                 int64_t Nout, bool vec_out) {
+  constexpr int V = 16 / (int)sizeof(W);
+  using VT = typename Vec<W>::T;
+  int prow[MM - 1];  // row of product q
+#pragma unroll
+  for (int q = 0; q < MM - 1; ++q) {
+    const int row = r + 1 + q;
+    prow[q] = row >= MM ? row - MM : row;
+  }
+#pragma unroll 1
+  for (int j = threadIdx.x * V; j < T; j += TCP_THREADS * V) {
+    const int64_t n = n0 + j;
+    if (n >= Nout) break;
+    auto product = [&](int q, W (&v)[V]) {
+      const VT t = *reinterpret_cast<const VT*>(dl + prow[q] * dlen +
+                                                tcp_dpad<W>(j));
+#pragma unroll
+      for (int e = 0; e < V; ++e) v[e] = reinterpret_cast<const W*>(&t)[e];
+    };
+    W t[V];
+    product(0, t);
+#pragma unroll
+    for (int q = 1; q < MM - 1; ++q) {
+      W v[V];
+      product(q, v);
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        t[e] = (q & 1) ? wsub<W>(shl<W>(t[e], l), v[e])
+                       : wadd<W>(shl<W>(t[e], l), v[e]);
+    }
+    W dcur[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      dcur[e] = sext_low<W>((MM & 1) ? wsub<W>((W)0, t[e]) : t[e], (MM - 1) * l);
+    const bool whole = vec_out && n + V <= Nout;
+    auto store = [&](int orow, const W (&vals)[V]) {
+      W* o = y + (int64_t)orow * ldy + n;
+      if (whole) {
+        VT v;
+#pragma unroll
+        for (int e = 0; e < V; ++e) reinterpret_cast<W*>(&v)[e] = vals[e];
+        *reinterpret_cast<VT*>(o) = v;
+      } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+          if (n + e < Nout) o[e] = vals[e];
+      }
+    };
+    // d_{r-1} (the row of product M - 2) first, then down the chain to d_r
+#pragma unroll
+    for (int q = MM - 2; q >= 0; --q) {
+      store(prow[q], dcur);
+      W v[V];
+      product(q, v);
+#pragma unroll
+      for (int e = 0; e < V; ++e) dcur[e] = wsub<W>(v[e], dcur[e]) >> l;
+    }
+    store(r, dcur);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused protected convolution (3 <= M <= 8).  Persistent blocks walk the
+// output tiles [n0, n0 + T); per tile:
+//   1. the raw rows c_m[n0 - 64, n0 + T) of all M streams (prefetched with
+//      cp.async during the previous tile when the rows are 16-byte aligned)
+//      become the digits of eps_m = c_m + 2^l c_{m-1} (Eq. 6) minus the
+//      range shift, for every stream that computes (all but r with SKIP);
+//   2. the warps share the tile's N-tiles (T / 128 per computing stream);
+//      each product delta_m (Eq. 8), range shift undone, goes to the
+//      stream's row of a shared product tile;
+//   3. all M outputs are recovered from the M - 1 products other than r's
+//      (r = M - 1 without a failure) and written straight to d.
+// vec_out: d's rows are 16-byte aligned (vector stores).
+// ---------------------------------------------------------------------------
+template <typename W, bool VEC, bool BIAS>
+__global__ void __launch_bounds__(TCP_THREADS, 2)
+tc_prot_kernel(const ConvArgs p, const bool vec_out) {
+  extern __shared__ __align__(128) int4 tcp_dyn[];
+  constexpr int V = 16 / (int)sizeof(W);  // words per 16-byte chunk
+  const int M = p.M;
+  const int T = tcp_tile(M);
+  const int S = T + TC_KP;            // staged inputs per stream
+  const int CPS = S / V;              // raw chunks per stream
+  const int dlen = tcp_dpad<W>(T);    // product slots per stream
+  uint16_t* dg = reinterpret_cast<uint16_t*>(tcp_dyn);
+  W* dl = reinterpret_cast<W*>(dg + (size_t)M * TC_ND * S);
+  W* raw = dl + (size_t)M * dlen;
+  TcTaps& tt = *reinterpret_cast<TcTaps*>(raw + (VEC ? (size_t)M * S : 0));
+  const unsigned long long shift_c = tc_block_setup<BIAS, TCP_THREADS>(p, tt);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t a[TC_NG][TC_KS][4];
+  tc_a_fragments(tt, lane, a);
+  const int r = p.fail_mode == NE_FAIL_NONE ? M - 1 : p.failed;
+  const bool skip = p.fail_mode == NE_FAIL_SKIP;  // stream r computes nothing
+  const int per = T / 128;                        // N-tiles per stream
+  const int ntl = (skip ? M - 1 : M) * per;       // N-tiles per tile
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(dg);
+  const W* x = reinterpret_cast<const W*>(p.x);
+  W* y = reinterpret_cast<W*>(p.y);
+  const uint32_t bias_lo = (uint32_t)p.bias;
+  // chunk k of the M rows laid end to end: stream k / CPS, chunk k % CPS
+  auto prefetch = [&](int64_t n0) {
+    int m = 0, cc = threadIdx.x;
+    while (cc >= CPS) cc -= CPS, ++m;
+    while (m < M) {
+      tc_prefetch_chunk<W>(x + (int64_t)m * p.ldx, p.N, n0, cc,
+                           raw + (size_t)m * S);
+      cc += TCP_THREADS;
+      while (cc >= CPS) cc -= CPS, ++m;
+    }
+    tc_cp_commit();
+  };
+  auto stage = [&](int64_t n0, auto check_tag) {
+    constexpr bool CHECK = decltype(check_tag)::value;
+    int m = 0, cc = threadIdx.x;
+    while (cc >= CPS) cc -= CPS, ++m;
+    while (m < M) {
+      if (!(skip && m == r)) {
+        const int mp = m == 0 ? M - 1 : m - 1;
+        tc_stage_chunk<W, true, CHECK>(raw + (size_t)m * S,
+                                       raw + (size_t)mp * S, p.N, n0, cc, p.l,
+                                       bias_lo, dg + (size_t)m * TC_ND * S, S);
+      }
+      cc += TCP_THREADS;
+      while (cc >= CPS) cc -= CPS, ++m;
+    }
+  };
+  auto products = [&](int64_t n0, auto edge_tag) {
+    constexpr bool EDGE = decltype(edge_tag)::value;
+#pragma unroll 1
+    for (int k = warp; k < ntl; k += TCP_WARPS) {
+      const int si = k / per;
+      const int m = (skip && si >= r) ? si + 1 : si;
+      const int ob = (k - si * per) * 128;
+      long long out[4];
+      tc_ntile(sbase + (uint32_t)(m * TC_ND * S) * 2u, S, ob, lane, a, out);
+      W* drow = dl + (size_t)m * dlen;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = tc_local(ob, lane, q);
+        long long v = out[q];
+        if constexpr (BIAS)
+          v += EDGE ? (long long)shift_correction(p.bias, tt.pref, n0 + j,
+                                                  p.N, p.K)
+                    : (long long)shift_c;
+        drow[tcp_dpad<W>(j)] = (W)v;
+      }
+    }
+  };
+  int64_t tile = blockIdx.x;
+  if (VEC && tile < p.ntiles) prefetch(tile * T);
+#pragma unroll 1
+  for (; tile < p.ntiles; tile += gridDim.x) {
+    const int64_t n0 = tile * T;
+    // 1. the digits of the entangled inputs
+    if constexpr (VEC) {
+      tc_cp_wait();
+      __syncthreads();  // this tile's raw rows have landed
+      if (n0 >= TC_KP && n0 + T <= p.N)
+        stage(n0, std::false_type{});
+      else
+        stage(n0, std::true_type{});
+      __syncthreads();  // digits ready; the raw rows are free
+      if (tile + gridDim.x < p.ntiles) prefetch((tile + gridDim.x) * T);
+    } else {
+      for (int m = 0; m < M; ++m) {
+        if (skip && m == r) continue;
+        const int mp = m == 0 ? M - 1 : m - 1;
+        tc_stage_global<W, true>(x + (int64_t)m * p.ldx,
+                                 x + (int64_t)mp * p.ldx, p.N, n0, p.l, bias_lo,
+                                 dg + (size_t)m * TC_ND * S, S, threadIdx.x,
+                                 TCP_THREADS);
+      }
+      __syncthreads();
+    }
+    // 2. the products
+    if (BIAS && (n0 < (int64_t)p.K - 1 || n0 + T > p.N))
+      products(n0, std::true_type{});
+    else
+      products(n0, std::false_type{});
+    __syncthreads();  // every product of the tile is in place
+    // 3. the recovery
+    switch (M) {
+      case 3: tcp_recover_tile<W, 3>(dl, dlen, T, r, p.l, y, p.ldy, n0, p.Nout, vec_out); break;
+      case 4: tcp_recover_tile<W, 4>(dl, dlen, T, r, p.l, y, p.ldy, n0, p.Nout, vec_out); break;
+      case 5: tcp_recover_tile<W, 5>(dl, dlen, T, r, p.l, y, p.ldy, n0, p.Nout, vec_out); break;
+      case 6: tcp_recover_tile<W, 6>(dl, dlen, T, r, p.l, y, p.ldy, n0, p.Nout, vec_out); break;
+      case 7: tcp_recover_tile<W, 7>(dl, dlen, T, r, p.l, y, p.ldy, n0, p.Nout, vec_out); break;
+      default: tcp_recover_tile<W, 8>(dl, dlen, T, r, p.l, y, p.ldy, n0, p.Nout, vec_out); break;
+    }
   }
 }

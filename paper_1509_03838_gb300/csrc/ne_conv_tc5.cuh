@@ -1,0 +1,493 @@
+// Exact integer convolution on the fifth-generation tensor cores
+// (tcgen05.mma, kind::f16, fp32 accumulators in tensor memory), for the
+// same operands as the mma.sync kernels of ne_conv_tc.cuh: values that fit
+// 32 bits (after the range shift), taps with |g| <= 2^15, K <= 65, split
+// into the same fp16 byte digits (4 operand digits, 2 tap digits).
+//
+// The product as a GEMM.  Output block a of a tile holds the 8 outputs
+// y[n0 + 8a + o], o < 8, and reads the 80 inputs x[n0 - 64 + 8a + k],
+// k < 80, so
+//     y[n0 + 8a + o] = sum_k A[a][k] B[k][o],  A[a][k] = x[n0 - 64 + 8a + k],
+//                                              B[k][o] = g[o + 64 - k].
+// A is a Hankel matrix: its rows are the staged digit row itself, 16 bytes
+// (8 fp16 digits) apart.  The tensor cores read a K-major operand without
+// swizzling as 8-row x 16-byte core matrices, element (row, k) at
+// start + SBO (row / 8) + 16 (row % 8) + LBO (k / 8) + 2 (k % 8); with
+// SBO = 128 and LBO = 16 that is start + 16 row + 2 k, exactly the digit
+// row, so A needs no copy.  One instruction (M = 128 blocks, N = 16,
+// K = 16) covers 1024 outputs; the 80-wide window takes 5 of them per
+// operand digit.  B's 16 columns are (output offset o, tap digit j), laid
+// out so that columns 8h .. 8h + 7 hold offsets 4h .. 4h + 3 of both tap
+// digits.  Operand digit i accumulates in its own 16 fp32 columns, each an
+// exact integer below 2^23 (80 products of at most 2^15).
+//
+// Fused protected convolution (tc5_prot_kernel, 3 <= M <= 4): per output
+// tile [n0, n0 + 1024), all M entangled streams are staged as digits
+// (Eq. 6), one thread issues every stream's products (Eq. 8) into tensor
+// memory, and each thread of the epilogue reads back 4 output positions of
+// every stream, so that the recovery of Eq. 16-19 runs in its registers.
+//
+// Included by ne_conv.cu inside its anonymous namespace, after
+// ne_conv_tc.cuh (digits, taps, cp.async helpers).
+#pragma once
+
+constexpr int T5_TILE = 1024;              // outputs per stream per tile
+constexpr int T5_STAGE = T5_TILE + 80;     // staged inputs per stream
+constexpr int T5_THREADS = 256;
+constexpr int T5_KS = 5;                   // k-steps of 16
+constexpr int T5_N = 16;                   // B columns
+constexpr int T5_BSTEP = T5_N * 16 * 2;    // bytes of B per k-step
+constexpr int T5_ACC = TC_ND * T5_N;       // tensor-memory columns per stream
+constexpr int T5_MAX_M = 4;
+static_assert(T5_STAGE % 8 == 0, "whole 16-byte chunks");
+
+// ---- tcgen05 / tensor-memory helpers --------------------------------------
+// Shared-memory matrix descriptor: start, leading and stride byte offsets
+// (all >> 4), descriptor version 1, no swizzling.
+__device__ __forceinline__ uint64_t t5_sdesc(uint32_t addr, uint32_t lbo,
+                                             uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) |
+         ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: fp32 accumulator, fp16 A and B,
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t t5_idesc(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void t5_mma(uint32_t d, uint64_t a, uint64_t b,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+// Arrive on the mbarrier once every tcgen05.mma issued so far completes.
+__device__ __forceinline__ void t5_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+      "[%0];" ::"r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void t5_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void t5_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Whole warp: allocate ncols columns (a power of two >= 32); the base
+// address lands in *dst.
+__device__ __forceinline__ void t5_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile(
+      "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::
+          "r"(smem_addr(dst)),
+      "r"(ncols)
+      : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ void t5_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(
+                   taddr),
+               "r"(ncols)
+               : "memory");
+}
+// This warp's 32 lanes x 8 consecutive 32-bit columns from taddr.
+__device__ __forceinline__ void t5_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+        "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void t5_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Byte offset of B element (k, n) in the canonical K-major layout without
+// swizzling: per k-step of 16 a 512-byte block of four core matrices,
+// column groups of 8 at 256 bytes, the two 8-wide k halves at 128.
+__device__ __forceinline__ int t5_boff(int k, int n) {
+  return (k >> 4) * T5_BSTEP + (n >> 3) * 256 + ((k >> 3) & 1) * 128 +
+         16 * (n & 7) + 2 * (k & 7);
+}
+// Column n of B: offset o = 4 (n / 8) + n % 4 of tap digit (n / 4) % 2.
+__device__ __forceinline__ void t5_col(int n, int& o, int& jg) {
+  o = 4 * (n >> 3) + (n & 3);
+  jg = (n >> 2) & 1;
+}
+
+// ---- mbarrier helpers of the pipelined kernel ------------------------------
+__device__ __forceinline__ void t5_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+// Bounded wait for the phase of parity `parity`; gives up (false) when the
+// block's abort word is set, or after the limit (then sets it and flags the
+// library's device error word).
+__device__ __forceinline__ bool t5_wait(uint64_t* bar, uint32_t parity,
+                                        volatile int* abort) {
+  constexpr uint32_t limit = 1u << 24;
+  for (uint32_t it = 0; it < limit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 1023u) == 1023u && *abort) return false;
+  }
+  *abort = 1;
+  atomicOr(&g_ne_device_error, 1u);
+  return false;
+}
+// Named barrier 1 over the 256 epilogue threads, with an AND vote.
+__device__ __forceinline__ bool t5_epi_vote(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, 256, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(ok ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void t5_epi_sync() {
+  asm volatile("bar.sync 2, 256;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Fused protected convolution on tcgen05, warp-specialised (MM = M in
+// {3, 4}; rows of c 16-byte aligned).  One persistent block of 448 threads
+// per SM walks the tiles [n0, n0 + 1024), four stages overlapped through
+// double-buffered shared memory and tensor memory:
+//   loader (warp 12)      raw rows c_m[n0 - 64, n0 + 1040) of all M streams
+//                         by bulk copies (cp.async with zero fill at the
+//                         ends of the rows);
+//   staging (warps 8-11)  the byte digits of eps_m = c_m + 2^l c_{m-1}
+//                         (Eq. 6) minus the range shift, stream m's four
+//                         digit rows side by side, for every computing
+//                         stream;
+//   MMA (warp 13, lane 0) 20 tcgen05.mma per computing stream (4 operand
+//                         digits x 5 k-steps) into columns
+//                         [64 m, 64 m + 64) of the tile's accumulator
+//                         buffer, committed to mbarriers;
+//   epilogue (warps 0-7)  warp w reads lanes 32 (w % 4) .. + 31 (output
+//                         blocks a) and columns 8 (w / 4) .. + 7 of each
+//                         digit's accumulator: outputs n0 + 8a + 4 (w / 4)
+//                         + (0..3) of every stream.  It assembles the
+//                         products delta_m (Eq. 8, range shift undone),
+//                         recovers all M outputs from the M - 1 products
+//                         other than r's (r = M - 1 without a failure;
+//                         Horner sum of Eq. 16 for d_{r-1} (Eq. 17), then
+//                         the chain d_{j-1} = (delta_j - d_j) >> l of
+//                         Eq. 18-19 the other way round), parks them in a
+//                         swizzled shared tile and writes the tile to d
+//                         with coalesced stores.
+// Every wait is bounded; a wait that expires sets the block's abort word,
+// every role then leaves its loop, and the block frees its tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int T5P_THREADS = 448;
+constexpr int T5P_WSTG = 8;     // first staging warp
+constexpr int T5P_WLOAD = 12;   // loader warp
+constexpr int T5P_WMMA = 13;    // MMA warp (allocates tensor memory)
+constexpr int T5P_TMEM = 512;   // tensor-memory columns: 2 x M x 64 <= 512
+
+struct T5PBars {
+  uint64_t raw_full[2], raw_empty[2], dig_full[2], dig_empty[2];
+  uint64_t acc_full[2], acc_empty[2];
+  uint32_t tbase;
+  int abort;
+};
+
+// Slot (16-byte chunk) of chunk c of a row of the output tile: chunks swap
+// within their group of 8 so that the epilogue's strided writes (4 outputs
+// per thread, 64 or 32 bytes apart) and the row-wise reads both spread
+// over all banks.
+template <typename W>
+__device__ __forceinline__ int t5_oswz(int c) {
+  return c ^ ((c >> (sizeof(W) == 8 ? 2 : 1)) & 7);
+}
+
+// Dynamic shared memory of the pipelined kernel.
+template <typename W>
+__host__ __device__ constexpr size_t t5p_smem_bytes(int M) {
+  return 2 * (size_t)M * TC_ND * T5_STAGE * 2 +        // digits, 2 stages
+         2 * (size_t)M * T5_STAGE * sizeof(W) +        // raw rows, 2 stages
+         (size_t)M * T5_TILE * sizeof(W) +             // output tile
+         T5_KS * T5_BSTEP + sizeof(TcTaps) + sizeof(T5PBars) + 256;
+}
+
+template <typename W, bool BIAS, int MM>
+__global__ void __launch_bounds__(T5P_THREADS, 1)
+tc5p_prot_kernel(const ConvArgs p) {
+  extern __shared__ __align__(128) int4 t5_dyn[];
+  constexpr int V = 16 / (int)sizeof(W);     // words per 16-byte chunk
+  constexpr int CPS = T5_STAGE / V;          // raw chunks per stream
+  constexpr int DIG = MM * TC_ND * T5_STAGE; // digits per stage (halves)
+  constexpr int RAW = MM * T5_STAGE;         // raw words per stage
+  constexpr int ACC = MM * T5_ACC;           // accumulator columns per stage
+  constexpr uint32_t RAW_BYTES = RAW * sizeof(W);
+  uint16_t* dig = reinterpret_cast<uint16_t*>(t5_dyn);
+  W* raw = reinterpret_cast<W*>(dig + 2 * DIG);
+  W* outb = raw + 2 * RAW;
+  unsigned char* bmat = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(outb + MM * T5_TILE) + 127) &
+      ~(uintptr_t)127);
+  TcTaps& tt = *reinterpret_cast<TcTaps*>(bmat + T5_KS * T5_BSTEP);
+  T5PBars& bars = *reinterpret_cast<T5PBars*>(
+      (reinterpret_cast<uintptr_t>(&tt + 1) + 7) & ~(uintptr_t)7);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = p.fail_mode == NE_FAIL_NONE ? MM - 1 : p.failed;
+  const bool skip = p.fail_mode == NE_FAIL_SKIP;  // stream r computes nothing
+  const W* x = reinterpret_cast<const W*>(p.x);
+  W* y = reinterpret_cast<W*>(p.y);
+
+  // ---- setup: B (taps), range-shift sums, barriers, tensor memory --------
+  for (int idx = threadIdx.x; idx < 80 * T5_N; idx += T5P_THREADS) {
+    const int k = idx / T5_N, n = idx - k * T5_N;
+    int o, jg;
+    t5_col(n, o, jg);
+    const int t = o + 64 - k;
+    int v = 0;
+    if (t >= 0 && t < p.K) {
+      const int gv = __ldg(p.g + t);
+      const int g0 = (int)(int8_t)(gv & 0xff);
+      v = jg == 0 ? g0 : (gv - g0) >> 8;
+    }
+    *reinterpret_cast<uint16_t*>(bmat + t5_boff(k, n)) = tc_half(v);
+  }
+  if constexpr (BIAS) {
+    for (int t = threadIdx.x; t < TC_TAPS; t += T5P_THREADS)
+      tt.taps[t] = t < p.K ? __ldg(p.g + t) : 0;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&bars.raw_full[s], 1);
+      mbar_init(&bars.raw_empty[s], 128);
+      mbar_init(&bars.dig_full[s], 128);
+      mbar_init(&bars.dig_empty[s], 1);
+      mbar_init(&bars.acc_full[s], 1);
+      mbar_init(&bars.acc_empty[s], 256);
+    }
+    bars.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == T5P_WMMA) t5_alloc(&bars.tbase, T5P_TMEM);
+  fence_proxy_async_smem();  // B, written by ordinary stores, is read by MMA
+  t5_fence_before();
+  __syncthreads();
+  t5_fence_after();
+  unsigned long long shift_c = 0;
+  if constexpr (BIAS) {
+    shift_c = (unsigned long long)p.bias *
+              (unsigned long long)tap_total<T5P_THREADS>(tt.taps, p.K,
+                                                         tt.warp_sums);
+    tap_prefix<T5P_THREADS>(tt.taps, p.K, tt.pref, tt.warp_sums);
+  }
+  const uint32_t tb = bars.tbase;
+  volatile int* abort = &bars.abort;
+  const int my_n = (int64_t)blockIdx.x < p.ntiles
+                       ? (int)((p.ntiles - 1 - blockIdx.x) / gridDim.x + 1)
+                       : 0;
+  auto tile_n0 = [&](int i) {
+    return ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * T5_TILE;
+  };
+  // the whole staged window lies inside the rows
+  auto interior = [&](int64_t n0) {
+    return n0 >= TC_KP && n0 - TC_KP + T5_STAGE <= p.N;
+  };
+
+  if (warp == T5P_WLOAD) {
+    // ---- loader ----------------------------------------------------------
+#pragma unroll 1
+    for (int i = 0; i < my_n; ++i) {
+      const int s = i & 1;
+      const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+      if (!t5_wait(&bars.raw_empty[s], ph ^ 1u, abort)) break;
+      const int64_t n0 = tile_n0(i);
+      W* rs = raw + s * RAW;
+      if (interior(n0)) {
+        if (lane == 0) {
+          mbar_arrive_expect_tx(&bars.raw_full[s], RAW_BYTES);
+          for (int m = 0; m < MM; ++m)
+            bulk_copy_g2s(rs + m * T5_STAGE, x + (int64_t)m * p.ldx + n0 - TC_KP,
+                          (uint32_t)(T5_STAGE * sizeof(W)), &bars.raw_full[s]);
+        }
+      } else {
+        for (int k = lane; k < MM * CPS; k += 32) {
+          const int m = k / CPS, cc = k - m * CPS;
+          tc_prefetch_chunk<W>(x + (int64_t)m * p.ldx, p.N, n0, cc,
+                               rs + m * T5_STAGE);
+        }
+        tc_cp_commit();
+        tc_cp_wait();
+        __syncwarp();
+        if (lane == 0) t5_arrive(&bars.raw_full[s]);
+      }
+    }
+  } else if (warp >= T5P_WSTG && warp < T5P_WSTG + 4) {
+    // ---- staging ---------------------------------------------------------
+    const int ts = threadIdx.x - T5P_WSTG * 32;
+    const uint32_t bias_lo = (uint32_t)p.bias;
+#pragma unroll 1
+    for (int i = 0; i < my_n; ++i) {
+      const int s = i & 1;
+      const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+      if (!t5_wait(&bars.raw_full[s], ph, abort)) break;
+      if (!t5_wait(&bars.dig_empty[s], ph ^ 1u, abort)) break;
+      const int64_t n0 = tile_n0(i);
+      const W* rs = raw + s * RAW;
+      uint16_t* ds = dig + s * DIG;
+      auto stage = [&](auto check_tag) {
+        constexpr bool CHECK = decltype(check_tag)::value;
+        for (int k = ts; k < MM * CPS; k += 128) {
+          const int m = k / CPS, cc = k - m * CPS;
+          if (skip && m == r) continue;
+          const int mp = m == 0 ? MM - 1 : m - 1;
+          tc_stage_chunk<W, true, CHECK, false>(
+              rs + m * T5_STAGE, rs + mp * T5_STAGE, p.N, n0, cc, p.l, bias_lo,
+              ds + m * TC_ND * T5_STAGE, T5_STAGE);
+        }
+      };
+      if (interior(n0))
+        stage(std::false_type{});
+      else
+        stage(std::true_type{});
+      fence_proxy_async_smem();  // digits are read by the tensor cores
+      t5_arrive(&bars.raw_empty[s]);
+      t5_arrive(&bars.dig_full[s]);
+    }
+  } else if (warp == T5P_WMMA) {
+    // ---- MMA issue -------------------------------------------------------
+    if (lane == 0) {
+      const uint32_t dig_addr = smem_addr(dig), b_addr = smem_addr(bmat);
+#pragma unroll 1
+      for (int i = 0; i < my_n; ++i) {
+        const int s = i & 1;
+        const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+        if (!t5_wait(&bars.dig_full[s], ph, abort)) break;
+        if (!t5_wait(&bars.acc_empty[s], ph ^ 1u, abort)) break;
+        t5_fence_after();
+#pragma unroll 1
+        for (int m = 0; m < MM; ++m) {
+          if (skip && m == r) continue;
+#pragma unroll
+          for (int d = 0; d < TC_ND; ++d)
+#pragma unroll
+            for (int kk = 0; kk < T5_KS; ++kk)
+              t5_mma(tb + s * ACC + m * T5_ACC + d * T5_N,
+                     t5_sdesc(dig_addr +
+                                  (uint32_t)((s * DIG + (m * TC_ND + d) * T5_STAGE +
+                                              16 * kk) * 2),
+                              16, 128),
+                     t5_sdesc(b_addr + kk * T5_BSTEP, 128, 256),
+                     t5_idesc(128, T5_N), kk > 0);
+        }
+        t5_commit(&bars.dig_empty[s]);
+        t5_commit(&bars.acc_full[s]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue (warps 0-7) --------------------------------------------
+    const int h = warp >> 2;                 // column half
+    const int a = 32 * (warp & 3) + lane;    // output block (TMEM lane)
+    const uint32_t tl = tb + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll 1
+    for (int i = 0; i < my_n; ++i) {
+      const int s = i & 1;
+      const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+      if (!t5_epi_vote(t5_wait(&bars.acc_full[s], ph, abort))) break;
+      t5_fence_after();
+      const int64_t n0 = tile_n0(i);
+      const bool edge = n0 < (int64_t)p.K - 1 || n0 + T5_TILE > p.N;
+      const int64_t nb = n0 + 8 * a + 4 * h;  // this thread's 4 outputs
+      W dl[MM - 1][4];                         // product q: row (r+1+q) mod M
+#pragma unroll
+      for (int q = 0; q < MM - 1; ++q) {
+        const int m = r + 1 + q >= MM ? r + 1 + q - MM : r + 1 + q;
+        uint32_t c[TC_ND][8];
+#pragma unroll
+        for (int d = 0; d < TC_ND; ++d)
+          t5_ld8(tl + s * ACC + m * T5_ACC + d * T5_N + 8 * h, c[d]);
+        t5_wait_ld();
+        long long v[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < TC_ND; ++d)
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            v[e] += ((long long)__float2int_rn(__uint_as_float(c[d][e])) +
+                     ((long long)__float2int_rn(__uint_as_float(c[d][4 + e]))
+                      << 8))
+                    << (8 * d);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if constexpr (BIAS)
+            v[e] += edge ? (long long)shift_correction(p.bias, tt.pref, nb + e,
+                                                       p.N, p.K)
+                         : (long long)shift_c;
+          dl[q][e] = (W)v[e];
+        }
+      }
+      t5_fence_before();
+      t5_arrive(&bars.acc_empty[s]);  // this buffer's columns are read
+      // recovery, 4 positions side by side; each row is parked as soon as
+      // the chain reaches it
+      auto park = [&](int m, const W (&vals)[4]) {
+        W* row = outb + m * T5_TILE;
+        const int j = 8 * a + 4 * h;  // local index, a multiple of 4
+        if constexpr (sizeof(W) == 8) {
+          *reinterpret_cast<longlong2*>(row + t5_oswz<W>(j / 2) * 2) =
+              make_longlong2(vals[0], vals[1]);
+          *reinterpret_cast<longlong2*>(row + t5_oswz<W>(j / 2 + 1) * 2) =
+              make_longlong2(vals[2], vals[3]);
+        } else {
+          *reinterpret_cast<int4*>(row + t5_oswz<W>(j / 4) * 4) =
+              make_int4(vals[0], vals[1], vals[2], vals[3]);
+        }
+      };
+      W dcur[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        W t = dl[0][e];
+#pragma unroll
+        for (int q = 1; q < MM - 1; ++q)
+          t = (q & 1) ? wsub<W>(shl<W>(t, p.l), dl[q][e])
+                      : wadd<W>(shl<W>(t, p.l), dl[q][e]);
+        dcur[e] = sext_low<W>((MM & 1) ? wsub<W>((W)0, t) : t, (MM - 1) * p.l);
+      }
+#pragma unroll
+      for (int q = MM - 2; q >= 0; --q) {
+        park(r + 1 + q >= MM ? r + 1 + q - MM : r + 1 + q, dcur);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dcur[e] = wsub<W>(dl[q][e], dcur[e]) >> p.l;
+      }
+      park(r, dcur);
+      t5_epi_sync();  // the output tile is complete
+      // coalesced stores: thread t takes 16-byte chunks t, t + 256, ...
+      const int nv = (int)lmin((int64_t)T5_TILE, p.Nout - n0);  // valid
+#pragma unroll
+      for (int m = 0; m < MM; ++m) {
+        const W* row = outb + m * T5_TILE;
+        W* drow = y + (int64_t)m * p.ldy + n0;
+        if ((reinterpret_cast<uintptr_t>(drow) & 15) == 0 && nv == T5_TILE) {
+          // 16-byte row: chunk c to thread c mod 256
+          for (int c = threadIdx.x; c < T5_TILE / V; c += 256)
+            *reinterpret_cast<typename Vec<W>::T*>(drow + c * V) =
+                *reinterpret_cast<const typename Vec<W>::T*>(
+                    row + t5_oswz<W>(c) * V);
+        } else {
+          // word j to thread j mod 256
+          for (int j = threadIdx.x; j < nv; j += 256)
+            drow[j] = row[t5_oswz<W>(j / V) * V + j % V];
+        }
+      }
+      t5_epi_sync();  // the output tile may be overwritten
+    }
+  }
+  // ---- teardown ------------------------------------------------------------
+  if (warp == T5P_WLOAD) tc_cp_wait();
+  t5_fence_before();
+  __syncthreads();
+  if (warp == T5P_WMMA) {
+    t5_fence_after();
+    t5_dealloc(tb, T5P_TMEM);
+  }
+}

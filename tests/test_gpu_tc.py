@@ -1,9 +1,12 @@
 """GPU parity of the tensor-core convolution (exact integer products from
 byte digits on fp16 mma.sync) against the CPU oracle, bit-exact: the plain
-convolution with declared ranges (ne_conv_range) and the fused protected
-convolution, every failure mode, operands at the ends of the 32-bit window,
-the largest taps, K from 1 to 65, ragged and unaligned rows; and the same
-cases on the multiply-add kernels (NE_CONV_TC=0)."""
+convolution with declared ranges (ne_conv_range) and the protected
+convolution (the fused tcgen05 kernel for 3 <= M <= 4 with aligned rows,
+the fused mma.sync kernel for the rest up to M = 8, every tile size),
+every failure mode, operands at the ends of the 32-bit window, the largest
+taps, K from 1 to 65, ragged and unaligned rows; and the same cases on the
+two-pass form (NE_PROT_KERNEL=twopass), on the mma.sync kernels alone
+(NE_CONV_TC5=0) and on the multiply-add kernels (NE_CONV_TC=0)."""
 import numpy as np
 import pytest
 
@@ -104,20 +107,28 @@ def test_conv_range_live_mask(ne, orc):
 
 
 PROT_CASES = [
-    # w, M, N, K, data bits, tap bits
-    (64, 4, 3 * TT + 7, 64, 15, 15),    # entangled span 2^32 - 1: range shift
-    (64, 8, 5000, 37, 14, 14),          # fits 32 bits without a shift
-    (64, 3, TT + 1, 65, 7, 15),         # l = 22, K = 65
-    (32, 3, 3000, 16, 7, 7),            # 32-bit words
-    (64, 5, TT, 1, 15, 15),             # K = 1, one full tile
-    (64, 4, 30, 64, 15, 15),            # N < K
-    (64, 6, 7 * TT - 5, 48, 12, 15),
+    # w, M, N, K, data bits, tap bits, row padding of c, of d
+    (64, 4, 3 * TT + 7, 64, 15, 15, 0, 0),    # range shift; odd rows, scalar
+    (64, 4, 1 << 14, 64, 15, 15, 0, 1),       # 16-byte rows in and out
+    (64, 4, 5000, 64, 15, 15, 2, 0),          # 16-byte rows in, odd rows out
+    (64, 8, 5000, 37, 14, 14, 0, 0),          # fits 32 bits without a shift
+    (64, 3, TT + 1, 65, 7, 15, 1, 0),         # l = 22, K = 65, tile 1280
+    (32, 3, 3000, 16, 7, 7, 0, 0),            # 32-bit words
+    (32, 8, 3001, 33, 6, 7, 3, 1),            # 32-bit words, tile 512
+    (64, 5, 3 * 768 - 1, 65, 15, 15, 1, 0),   # tile 768, ragged last tile
+    (64, 5, TT, 1, 15, 15, 0, 0),             # K = 1
+    (64, 4, 30, 64, 15, 15, 0, 0),            # N < K
+    (64, 6, 7 * TT - 5, 48, 12, 15, 0, 0),    # tile 640
+    (64, 7, 5 * 512 + 3, 64, 15, 15, 1, 0),   # tile 512, 7 streams
+    (64, 3, 5000, 64, 8, 15, 0, 0),           # tcgen05, M = 3, 64-bit
+    (64, 4, 1024 - 63, 64, 15, 15, 1, 0),     # tcgen05, one whole tile
+    (32, 4, 4096, 65, 6, 7, 0, 0),            # tcgen05, 32-bit words
 ]
 
 
 @pytest.mark.parametrize("case", PROT_CASES)
 def test_protected_tc_every_failure(ne, orc, case):
-    w, M, N, K, bc, bg = case
+    w, M, N, K, bc, bg, padc, padd = case
     p = ne.ne_params(M, w)
     gen = synth.rng(N + K + M + w)
     c = synth.uniform_int(gen, (M, N), -(1 << bc), 1 << bc)
@@ -126,28 +137,50 @@ def test_protected_tc_every_failure(ne, orc, case):
     g = synth.uniform_int(gen, (K,), -(1 << bg) + 1, 1 << bg)
     assert K * (1 << bc) * ((1 << bg) - 1) <= p.d_max_exact
     plain = orc.conv(c, g, w)
-    cd, gd = dev(c, w), torch.from_numpy(g.astype(np.int32)).cuda()
+    Nout = N + K - 1
+    cd, gd = dev(c, w, ld=N + padc), torch.from_numpy(g.astype(np.int32)).cuda()
     modes = [(ne.NE_FAIL_NONE, -1)] + [(fm, r) for fm in (ne.NE_FAIL_SKIP,
                                                           ne.NE_FAIL_DROP)
                                        for r in range(M)]
     for fm, r in modes:
-        d = torch.full((M, N + K - 1), 77, dtype=dt(w), device="cuda")
+        dfull = torch.full((M, Nout + padd), 77, dtype=dt(w), device="cuda")
+        d = dfull[:, :Nout]
         ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(1 << bc), (1 << bc) - 1),
                              max_abs_g=(1 << bg) - 1, failed=r, fail_mode=fm)
         torch.cuda.synchronize()
         assert np.array_equal(host(d), plain), (fm, r)
+        if padd:  # nothing written past the end of a row
+            assert (dfull[:, Nout:] == 77).all(), (fm, r)
+
+
+def _child_run(env_extra, select):
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ, **env_extra)
+    out = subprocess.run(
+        [sys.executable, "-m", "pytest", __file__, "-q", "-x", "-m", "gpu",
+         "-p", "no:cacheprovider", "-k", select],
+        env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout[-3000:] + out.stderr[-2000:]
+    assert " passed" in out.stdout
+
+
+def test_same_cases_on_the_two_pass_form(ne):
+    """NE_PROT_KERNEL=twopass (read once per process, hence the child run):
+    the protected cases through the tensor-core products and a separate
+    recovery pass instead of the fused kernel."""
+    _child_run({"NE_PROT_KERNEL": "twopass"}, "protected_tc")
+
+
+def test_same_cases_on_the_mma_sync_kernels(ne):
+    """NE_CONV_TC5=0: the protected cases through the mma.sync kernels where
+    the tcgen05 one would run (3 <= M <= 4, aligned rows)."""
+    _child_run({"NE_CONV_TC5": "0"}, "protected_tc")
 
 
 def test_same_cases_on_the_multiply_add_kernels(ne):
     """NE_CONV_TC=0 (read once per process, hence the child run): every case
     above through the multiply-add kernels."""
-    import os
-    import subprocess
-    import sys
-    env = dict(os.environ, NE_CONV_TC="0")
-    out = subprocess.run(
-        [sys.executable, "-m", "pytest", __file__, "-q", "-x", "-m", "gpu",
-         "-p", "no:cacheprovider", "-k", "not multiply_add"],
-        env=env, capture_output=True, text=True, timeout=600)
-    assert out.returncode == 0, out.stdout[-3000:] + out.stderr[-2000:]
-    assert " passed" in out.stdout
+    _child_run({"NE_CONV_TC": "0"},
+               "not multiply_add and not two_pass and not mma_sync")
