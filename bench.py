@@ -393,39 +393,43 @@ def run_ne(args):
     # ---- roofline of the dominant kernel -----------------------------------
     probe = {}
     for kind, nm in [(0, "imad32"), (1, "imad_wide"), (2, "wide_plus_imad32"),
-                     (5, "mma_sync_f16")]:
+                     (5, "mma_sync_f16"), (6, "tcgen05_f16_n16")]:
         rate, _ = ne.ne_probe_imad_rate(kind, 2048 if kind < 5 else 512)
         probe[nm] = rate
     span = (j.c_range[1] - j.c_range[0]) * f_ent
     algo_bytes = float((M * N + M * Nout) * 8)
-    tc_path = (span <= 0xFFFFFFFF and K <= 65 and j.bound_g <= 32768
+    tc_path = (span <= 0xFFFFFFFF and K <= 65 and j.bound_g <= 32768 and M <= 4
                and os.environ.get("NE_CONV_TC", "1") != "0"
+               and os.environ.get("NE_CONV_TC5", "1") != "0"
                and os.environ.get("NE_PROT_KERNEL") is None)
     if tc_path:
         # Exact products on the tensor cores leave the step bound by memory:
         # c read once and d written once (algorithmic bytes) against the
-        # measured copy bandwidth.  The step is two kernels (the entangling
-        # product, then the in-place recovery), timed together.
+        # measured copy bandwidth.  The step is one kernel (M <= 4, 16-byte
+        # rows): tcgen05 products in tensor memory, recovery in its epilogue.
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         hbm = float(peaks["hbm_gbs"])
         achieved = algo_bytes / (prot_ms * 1e-3) / 1e9
-        mma_per_step = M * (Nout / 128.0) * 40.0  # mma.sync per 128 outputs
+        # 20 tcgen05.mma (4 operand digits x 5 k-steps) per stream per
+        # 1024-output tile; every stream computes (the failure drops one)
+        mma_per_step = M * float((Nout + 1023) // 1024) * 20.0
         traffic = (TRAFFIC_CAPTURE["bytes"]
                    if TRAFFIC_CAPTURE["sources_sha256"] == conv_sources_sha()
                    else None)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm,
                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                     "algorithmic_bytes": algo_bytes,
-                    "kernel": "tc_conv_kernel<int64, ENT> + recover_kernel "
-                              "(entangle-on-load tensor-core product, then "
-                              "in-place recovery; timed together)",
+                    "kernel": "tc5p_prot_kernel<int64, BIAS, 4> (fused, "
+                              "warp-specialised: bulk-copy loads, entangled "
+                              "digit staging, tcgen05.mma into tensor memory, "
+                              "recovery in the epilogue)",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured "
                                    "copy bandwidth)",
                     "launch_ms": prot_ms,
-                    "tensor": {"mma_sync_per_s": mma_per_step / (prot_ms * 1e-3),
-                               "probe_mma_sync_per_s": probe["mma_sync_f16"],
+                    "tensor": {"tcgen05_mma_per_s": mma_per_step / (prot_ms * 1e-3),
+                               "probe_tcgen05_mma_per_s": probe["tcgen05_f16_n16"],
                                "frac": mma_per_step / (prot_ms * 1e-3)
-                                       / probe["mma_sync_f16"]},
+                                       / probe["tcgen05_f16_n16"]},
                     "probe_instr_per_s": probe}
     else:
         # The entangled words c_m + 2^l c_{m-1} with c in [-2^15, 2^15) and
@@ -512,7 +516,7 @@ def run_ne(args):
                     "d2h_bytes_per_step": d2h,
                     "path": f"ne_pipe_protected_conv, chunks of {E2E_CHUNK} "
                             f"output samples over {E2E_STREAMS} streams"},
-            "gpu_launches": args.steps * (2 if tc_path else 1),
+            "gpu_launches": args.steps,
             "clocks": clk,
             "small": small,
             "paper_shapes": paper,
@@ -535,13 +539,15 @@ E2E_STREAMS = 4
 
 TRAFFIC_CAPTURE = {
     "sources_sha256":
-        "c38f6ee921ee1b33813aa8ef7c568ea6a1a5cb969c657e85fc576231fd4c5018",
-    # tc_conv_kernel (134248448 + 84851200) + recover_kernel (100714752 +
-    # 72739328): profiles/conv_tc_protected_M4_N2e22_K64.md
-    "bytes": 134248448 + 84851200 + 100714752 + 72739328,
+        "96b75dbbac40283d73eea5c6c18f3db11d08b88e2a788153590c4790b71f4a52",
+    # tc5p_prot_kernel<int64, BIAS, 4>, second of three captured launches:
+    # 134305536 bytes read + 76547840 written (the rest of d is still in L2
+    # when the launch ends); profiles/conv_tc5_protected_M4_N2e22_K64.md
+    "bytes": 134305536 + 76547840,
 }
 CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_conv_tc.cuh",
-                "ne_recover.cuh", "ne_common.cuh", "ne_stream_ops.cu"]
+                "ne_conv_tc5.cuh", "ne_tc5.cuh", "ne_recover.cuh",
+                "ne_common.cuh", "ne_stream_ops.cu"]
 
 
 def conv_sources_sha() -> str:

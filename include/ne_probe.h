@@ -22,6 +22,11 @@ extern "C" {
  *   kind 5: mma.sync m16n8k16 with fp16 inputs and fp32 accumulation, the
  *           tensor-core product of the exact integer convolution; counted as
  *           warp-wide instructions (2*16*8*16 = 4096 flops each)
+ *   kind 6: tcgen05.mma kind::f16 with M = 128, N = 16, K = 16 (fp16 inputs,
+ *           fp32 accumulators in tensor memory), the instruction of the
+ *           fifth-generation tensor-core convolution; one block per SM,
+ *           one thread issuing, 20 instructions per round (2*128*16*16 =
+ *           65536 flops each)
  * and return the best of three timed launches (after one warm-up) as
  * multiply-add instructions per second in *instr_per_s (and the launch time
  * in *elapsed_ms if non-NULL).  Unlike the compute calls of ne.h this call

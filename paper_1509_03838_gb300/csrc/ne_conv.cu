@@ -25,6 +25,7 @@
 #include <mutex>
 
 #include "ne_conv_core.cuh"
+#include "ne_tc5.cuh"
 
 namespace ne {
 

@@ -41,69 +41,6 @@ constexpr int T5_ACC = TC_ND * T5_N;       // tensor-memory columns per stream
 constexpr int T5_MAX_M = 4;
 static_assert(T5_STAGE % 8 == 0, "whole 16-byte chunks");
 
-// ---- tcgen05 / tensor-memory helpers --------------------------------------
-// Shared-memory matrix descriptor: start, leading and stride byte offsets
-// (all >> 4), descriptor version 1, no swizzling.
-__device__ __forceinline__ uint64_t t5_sdesc(uint32_t addr, uint32_t lbo,
-                                             uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) |
-         ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-// Instruction descriptor of kind::f16: fp32 accumulator, fp16 A and B,
-// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t t5_idesc(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void t5_mma(uint32_t d, uint64_t a, uint64_t b,
-                                       uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-// Arrive on the mbarrier once every tcgen05.mma issued so far completes.
-__device__ __forceinline__ void t5_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
-      "[%0];" ::"r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ void t5_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void t5_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// Whole warp: allocate ncols columns (a power of two >= 32); the base
-// address lands in *dst.
-__device__ __forceinline__ void t5_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile(
-      "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::
-          "r"(smem_addr(dst)),
-      "r"(ncols)
-      : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::
-                   : "memory");
-}
-__device__ __forceinline__ void t5_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(
-                   taddr),
-               "r"(ncols)
-               : "memory");
-}
-// This warp's 32 lanes x 8 consecutive 32-bit columns from taddr.
-__device__ __forceinline__ void t5_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
-        "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void t5_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // Byte offset of B element (k, n) in the canonical K-major layout without
 // swizzling: per k-step of 16 a 512-byte block of four core matrices,
 // column groups of 8 at 256 bytes, the two 8-wide k halves at 128.
@@ -118,10 +55,6 @@ __device__ __forceinline__ void t5_col(int n, int& o, int& jg) {
 }
 
 // ---- mbarrier helpers of the pipelined kernel ------------------------------
-__device__ __forceinline__ void t5_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar))
-               : "memory");
-}
 // Bounded wait for the phase of parity `parity`; gives up (false) when the
 // block's abort word is set, or after the limit (then sets it and flags the
 // library's device error word).
@@ -357,7 +290,14 @@ tc5p_prot_kernel(const ConvArgs p) {
   } else if (warp == T5P_WMMA) {
     // ---- MMA issue -------------------------------------------------------
     if (lane == 0) {
-      const uint32_t dig_addr = smem_addr(dig), b_addr = smem_addr(bmat);
+      // descriptors as 32-bit halves: the start address (>> 4) sits in the
+      // low 14 bits, far from overflowing for addresses below 256 KB, so
+      // moving an operand is one add on the low half
+      const uint64_t a0 = t5_sdesc(smem_addr(dig), 16, 128);
+      const uint64_t b0 = t5_sdesc(smem_addr(bmat), 128, 256);
+      const uint32_t a_hi = (uint32_t)(a0 >> 32), b_hi = (uint32_t)(b0 >> 32);
+      const uint32_t b_lo = (uint32_t)b0;
+      constexpr uint32_t idesc = t5_idesc(128, T5_N);
 #pragma unroll 1
       for (int i = 0; i < my_n; ++i) {
         const int s = i & 1;
@@ -365,20 +305,22 @@ tc5p_prot_kernel(const ConvArgs p) {
         if (!t5_wait(&bars.dig_full[s], ph, abort)) break;
         if (!t5_wait(&bars.acc_empty[s], ph ^ 1u, abort)) break;
         t5_fence_after();
-#pragma unroll 1
+        const uint32_t a_lo = (uint32_t)a0 + (uint32_t)(s * DIG * 2 / 16);
+        const uint32_t dcol = tb + s * ACC;
+#pragma unroll
         for (int m = 0; m < MM; ++m) {
           if (skip && m == r) continue;
 #pragma unroll
-          for (int d = 0; d < TC_ND; ++d)
+          for (int d = 0; d < TC_ND; ++d) {
+            constexpr int ROW = T5_STAGE * 2 / 16;  // 16-byte units per row
+            const uint32_t al = a_lo + (uint32_t)((m * TC_ND + d) * ROW);
+            const uint32_t dc = dcol + m * T5_ACC + d * T5_N;
+            t5_mma_lh<false>(dc, al, a_hi, b_lo, b_hi, idesc);
 #pragma unroll
-            for (int kk = 0; kk < T5_KS; ++kk)
-              t5_mma(tb + s * ACC + m * T5_ACC + d * T5_N,
-                     t5_sdesc(dig_addr +
-                                  (uint32_t)((s * DIG + (m * TC_ND + d) * T5_STAGE +
-                                              16 * kk) * 2),
-                              16, 128),
-                     t5_sdesc(b_addr + kk * T5_BSTEP, 128, 256),
-                     t5_idesc(128, T5_N), kk > 0);
+            for (int kk = 1; kk < T5_KS; ++kk)
+              t5_mma_lh<true>(dc, al + 2 * kk, a_hi,
+                              b_lo + kk * (T5_BSTEP / 16), b_hi, idesc);
+          }
         }
         t5_commit(&bars.dig_empty[s]);
         t5_commit(&bars.acc_full[s]);
@@ -408,15 +350,19 @@ tc5p_prot_kernel(const ConvArgs p) {
         for (int d = 0; d < TC_ND; ++d)
           t5_ld8(tl + s * ACC + m * T5_ACC + d * T5_N + 8 * h, c[d]);
         t5_wait_ld();
-        long long v[4] = {0, 0, 0, 0};
+        // digit d's two tap-digit sums (each below 2^22 in magnitude)
+        // combine exactly in 32 bits; the four digits in 64 bits
+        long long v[4];
 #pragma unroll
-        for (int d = 0; d < TC_ND; ++d)
+        for (int e = 0; e < 4; ++e) {
+          int t[TC_ND];
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            v[e] += ((long long)__float2int_rn(__uint_as_float(c[d][e])) +
-                     ((long long)__float2int_rn(__uint_as_float(c[d][4 + e]))
-                      << 8))
-                    << (8 * d);
+          for (int d = 0; d < TC_ND; ++d)
+            t[d] = __float2int_rn(__uint_as_float(c[d][e])) +
+                   __float2int_rn(__uint_as_float(c[d][4 + e])) * 256;
+          v[e] = (long long)t[0] + (long long)t[1] * 256 +
+                 (long long)t[2] * 65536 + (long long)t[3] * 16777216;
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           if constexpr (BIAS)

@@ -12,7 +12,10 @@
 //           as a carry chain; two instructions)
 //   kind 4: mad.wide.s32 + fma.rn.f32 per round (two instructions)
 //   kind 5: mma.sync m16n8k16 f16 -> f32 (warp-wide; 4096 flops each)
+//   kind 6: tcgen05.mma kind::f16, M = 128, N = 16, K = 16 (one thread per
+//           SM issues them into tensor memory; 65536 flops each)
 #include "ne_common.cuh"
+#include "ne_tc5.cuh"
 
 namespace ne {
 namespace {
@@ -101,6 +104,70 @@ __global__ void __launch_bounds__(256) mma_probe_kernel(int iters, int seed,
   sink[blockIdx.x * blockDim.x + threadIdx.x] = (unsigned long long)__float_as_uint(s);
 }
 
+// kind 6: one block per SM; thread 0 issues `iters` rounds of 20
+// tcgen05.mma (M = 128, N = 16, K = 16, fp16 -> fp32), four accumulators
+// of five k-steps each, every accumulator reading its own 2208-byte row of
+// A through the Hankel descriptor of the convolution kernels (16-byte
+// leading offset, 128-byte stride), then commits and waits (bounded).
+constexpr int P6_ROW = 1104;  // fp16 per A row
+__global__ void __launch_bounds__(128) tc5_probe_kernel(int iters,
+                                                        unsigned long long* sink) {
+  __shared__ __align__(128) uint16_t a_rows[4 * P6_ROW];
+  __shared__ __align__(128) uint16_t b_mat[5 * 256];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tbase;
+  for (int i = threadIdx.x; i < 4 * P6_ROW; i += 128)
+    a_rows[i] = (uint16_t)(0x3C00u * ((i * 7) % 3 == 0));  // 0 or 1.0
+  for (int i = threadIdx.x; i < 5 * 256; i += 128)
+    b_mat[i] = (uint16_t)(0x3C00u * ((i * 5) % 4 == 0));
+  if (threadIdx.x < 32) t5_alloc(&tbase, 64);
+  if (threadIdx.x == 0) {
+    t5_mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  t5_fence_before();
+  __syncthreads();
+  t5_fence_after();
+  const uint32_t tb = tbase;
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    const uint64_t a0 = t5_sdesc(t5_saddr(a_rows), 16, 128);
+    const uint64_t b0 = t5_sdesc(t5_saddr(b_mat), 128, 256);
+    const uint32_t a_hi = (uint32_t)(a0 >> 32), b_hi = (uint32_t)(b0 >> 32);
+    constexpr uint32_t idesc = t5_idesc(128, 16);
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        const uint32_t al = (uint32_t)a0 + (uint32_t)(d * P6_ROW * 2 / 16);
+        t5_mma_lh<false>(tb + 16 * d, al, a_hi, (uint32_t)b0, b_hi, idesc);
+#pragma unroll
+        for (int kk = 1; kk < 5; ++kk)
+          t5_mma_lh<true>(tb + 16 * d, al + 2 * kk, a_hi,
+                          (uint32_t)b0 + 32 * kk, b_hi, idesc);
+      }
+    }
+    t5_commit(&bar);
+  }
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    if (t5_mbar_try_wait(&bar, 0)) break;
+    if (it + 1 == (1u << 26)) ok = false;
+  }
+  t5_fence_after();
+  uint32_t r[8];
+  t5_ld8(tb + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16), r);
+  t5_wait_ld();
+  sink[blockIdx.x * blockDim.x + threadIdx.x] =
+      ok ? (unsigned long long)(r[0] ^ r[7]) : ~0ull;
+  t5_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    t5_fence_after();
+    t5_dealloc(tb, 64);
+  }
+}
+
 }  // namespace
 }  // namespace ne
 
@@ -108,7 +175,7 @@ using namespace ne;
 
 extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
                                   double* elapsed_ms) {
-  if (!instr_per_s || kind < 0 || kind > 5 || iters < 1)
+  if (!instr_per_s || kind < 0 || kind > 6 || iters < 1)
     return NE_ERR_INVALID_ARG;
   const int sms = sm_count();
   const int blocks = sms * 8;
@@ -128,7 +195,8 @@ extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
     else if (kind == 2) imad_probe_kernel<2><<<blocks, 256>>>(iters, rep, sink);
     else if (kind == 3) imad_probe_kernel<3><<<blocks, 256>>>(iters, rep, sink);
     else if (kind == 4) imad_probe_kernel<4><<<blocks, 256>>>(iters, rep, sink);
-    else mma_probe_kernel<<<blocks, 256>>>(iters, rep, sink);
+    else if (kind == 5) mma_probe_kernel<<<blocks, 256>>>(iters, rep, sink);
+    else tc5_probe_kernel<<<sms, 128>>>(iters, sink);
     cudaEventRecord(e1, 0);
     if (cudaEventSynchronize(e1) != cudaSuccess) { st = NE_ERR_CUDA; break; }
     float ms = 0.f;
@@ -137,9 +205,12 @@ extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
   }
   if (st == NE_OK && cudaGetLastError() != cudaSuccess) st = NE_ERR_CUDA;
   if (st == NE_OK) {
-    // kind 5 counts warp-wide mma.sync instructions (8 per warp per round)
+    // kind 5 counts warp-wide mma.sync instructions (8 per warp per round),
+    // kind 6 tcgen05.mma (20 per block per round, one block per SM)
     const double per_round = kind == 5 ? 8.0 / 32.0 : (kind >= 2) ? 16.0 : 8.0;
-    const double instr = (double)blocks * 256.0 * (double)iters * per_round;
+    const double instr = kind == 6
+                             ? (double)sms * 20.0 * (double)iters
+                             : (double)blocks * 256.0 * (double)iters * per_round;
     *instr_per_s = instr / (best * 1e-3);
     if (elapsed_ms) *elapsed_ms = best;
   }

@@ -127,6 +127,17 @@ def test_argument_errors_return_before_launch(ne):
     assert L.ne_recover(DUMMY, 8, 4, 8, 32, 11, 0, DUMMY, 8, s) == ne.NE_ERR_INVALID_ARG
 
 
+def test_probe_kind_and_iteration_checks(ne):
+    """The rate probe (kinds 0-6) rejects an unknown kind or no rounds
+    before it touches a GPU."""
+    L = ne.lib()
+    rate, ms = ctypes.c_double(0), ctypes.c_double(0)
+    for kind, iters in [(-1, 8), (7, 8), (6, 0), (0, -3)]:
+        assert L.ne_probe_imad_rate(kind, iters, ctypes.byref(rate),
+                                    ctypes.byref(ms)) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_probe_imad_rate(6, 8, None, None) == ne.NE_ERR_INVALID_ARG
+
+
 def test_protected_conv_range_and_failure_checks(ne):
     L = ne.lib()
     s = ctypes.c_void_p(0)
