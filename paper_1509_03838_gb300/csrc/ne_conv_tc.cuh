@@ -617,7 +617,7 @@ tc_prot_kernel(const ConvArgs p, const bool vec_out) {
     }
   };
   auto products = [&](int64_t n0, auto edge_tag) {
-    constexpr bool EDGE = decltype(edge_tag)::value;
+    [[maybe_unused]] constexpr bool EDGE = decltype(edge_tag)::value;
 #pragma unroll 1
     for (int k = warp; k < ntl; k += TCP_WARPS) {
       const int si = k / per;

@@ -21,11 +21,13 @@
 // digits.  Operand digit i accumulates in its own 16 fp32 columns, each an
 // exact integer below 2^23 (80 products of at most 2^15).
 //
-// Fused protected convolution (tc5_prot_kernel, 3 <= M <= 4): per output
+// Fused protected convolution (tc5p_prot_kernel, 3 <= M <= 4): per output
 // tile [n0, n0 + 1024), all M entangled streams are staged as digits
 // (Eq. 6), one thread issues every stream's products (Eq. 8) into tensor
 // memory, and each thread of the epilogue reads back 4 output positions of
 // every stream, so that the recovery of Eq. 16-19 runs in its registers.
+// Loading, staging, the products and the epilogue run in separate warps,
+// connected by mbarrier rings.
 //
 // Included by ne_conv.cu inside its anonymous namespace, after
 // ne_conv_tc.cuh (digits, taps, cp.async helpers).
@@ -33,7 +35,6 @@
 
 constexpr int T5_TILE = 1024;              // outputs per stream per tile
 constexpr int T5_STAGE = T5_TILE + 80;     // staged inputs per stream
-constexpr int T5_THREADS = 256;
 constexpr int T5_KS = 5;                   // k-steps of 16
 constexpr int T5_N = 16;                   // B columns
 constexpr int T5_BSTEP = T5_N * 16 * 2;    // bytes of B per k-step
@@ -81,13 +82,10 @@ __device__ __forceinline__ bool t5_epi_vote(bool ok) {
       : "memory");
   return r != 0;
 }
-__device__ __forceinline__ void t5_epi_sync() {
-  asm volatile("bar.sync 2, 256;" ::: "memory");
-}
 
 // ---------------------------------------------------------------------------
 // Fused protected convolution on tcgen05, warp-specialised (MM = M in
-// {3, 4}; rows of c 16-byte aligned).  One persistent block of 448 threads
+// {3, 4}; rows of c 16-byte aligned).  One persistent block of 480 threads
 // per SM walks the tiles [n0, n0 + 1024), four stages overlapped through
 // double-buffered shared memory and tensor memory:
 //   loader (warp 12)      raw rows c_m[n0 - 64, n0 + 1040) of all M streams
@@ -96,11 +94,13 @@ __device__ __forceinline__ void t5_epi_sync() {
 //   staging (warps 8-11)  the byte digits of eps_m = c_m + 2^l c_{m-1}
 //                         (Eq. 6) minus the range shift, stream m's four
 //                         digit rows side by side, for every computing
-//                         stream;
-//   MMA (warp 13, lane 0) 20 tcgen05.mma per computing stream (4 operand
-//                         digits x 5 k-steps) into columns
+//                         stream; then the coalesced stores of the
+//                         outputs the epilogue parked two tiles earlier;
+//   MMA (warps 13, 14;    20 tcgen05.mma per computing stream (4 operand
+//   lane 0 of each)       digits x 5 k-steps) into columns
 //                         [64 m, 64 m + 64) of the tile's accumulator
-//                         buffer, committed to mbarriers;
+//                         buffer, committed to mbarriers; warp 13 issues
+//                         the even streams, warp 14 the odd ones;
 //   epilogue (warps 0-7)  warp w reads lanes 32 (w % 4) .. + 31 (output
 //                         blocks a) and columns 8 (w / 4) .. + 7 of each
 //                         digit's accumulator: outputs n0 + 8a + 4 (w / 4)
@@ -110,21 +110,20 @@ __device__ __forceinline__ void t5_epi_sync() {
 //                         other than r's (r = M - 1 without a failure;
 //                         Horner sum of Eq. 16 for d_{r-1} (Eq. 17), then
 //                         the chain d_{j-1} = (delta_j - d_j) >> l of
-//                         Eq. 18-19 the other way round), parks them in a
-//                         swizzled shared tile and writes the tile to d
-//                         with coalesced stores.
+//                         Eq. 18-19 the other way round) and parks them in
+//                         a swizzled shared output tile (two buffers).
 // Every wait is bounded; a wait that expires sets the block's abort word,
 // every role then leaves its loop, and the block frees its tensor memory.
 // ---------------------------------------------------------------------------
-constexpr int T5P_THREADS = 448;
+constexpr int T5P_THREADS = 480;
 constexpr int T5P_WSTG = 8;     // first staging warp
 constexpr int T5P_WLOAD = 12;   // loader warp
-constexpr int T5P_WMMA = 13;    // MMA warp (allocates tensor memory)
+constexpr int T5P_WMMA = 13;    // MMA warps 13 and 14 (13 allocates tensor memory)
 constexpr int T5P_TMEM = 512;   // tensor-memory columns: 2 x M x 64 <= 512
 
 struct T5PBars {
   uint64_t raw_full[2], raw_empty[2], dig_full[2], dig_empty[2];
-  uint64_t acc_full[2], acc_empty[2];
+  uint64_t acc_full[2], acc_empty[2], out_full[2], out_empty[2];
   uint32_t tbase;
   int abort;
 };
@@ -143,7 +142,7 @@ template <typename W>
 __host__ __device__ constexpr size_t t5p_smem_bytes(int M) {
   return 2 * (size_t)M * TC_ND * T5_STAGE * 2 +        // digits, 2 stages
          2 * (size_t)M * T5_STAGE * sizeof(W) +        // raw rows, 2 stages
-         (size_t)M * T5_TILE * sizeof(W) +             // output tile
+         2 * (size_t)M * T5_TILE * sizeof(W) +         // output tiles, 2
          T5_KS * T5_BSTEP + sizeof(TcTaps) + sizeof(T5PBars) + 256;
 }
 
@@ -161,7 +160,7 @@ tc5p_prot_kernel(const ConvArgs p) {
   W* raw = reinterpret_cast<W*>(dig + 2 * DIG);
   W* outb = raw + 2 * RAW;
   unsigned char* bmat = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(outb + MM * T5_TILE) + 127) &
+      (reinterpret_cast<uintptr_t>(outb + 2 * MM * T5_TILE) + 127) &
       ~(uintptr_t)127);
   TcTaps& tt = *reinterpret_cast<TcTaps*>(bmat + T5_KS * T5_BSTEP);
   T5PBars& bars = *reinterpret_cast<T5PBars*>(
@@ -195,9 +194,11 @@ tc5p_prot_kernel(const ConvArgs p) {
       mbar_init(&bars.raw_full[s], 1);
       mbar_init(&bars.raw_empty[s], 128);
       mbar_init(&bars.dig_full[s], 128);
-      mbar_init(&bars.dig_empty[s], 1);
-      mbar_init(&bars.acc_full[s], 1);
+      mbar_init(&bars.dig_empty[s], 2);  // one commit per MMA warp
+      mbar_init(&bars.acc_full[s], 2);
       mbar_init(&bars.acc_empty[s], 256);
+      mbar_init(&bars.out_full[s], 256);
+      mbar_init(&bars.out_empty[s], 128);
     }
     bars.abort = 0;
     fence_mbar_init();
@@ -221,6 +222,41 @@ tc5p_prot_kernel(const ConvArgs p) {
                        : 0;
   auto tile_n0 = [&](int i) {
     return ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * T5_TILE;
+  };
+  // Coalesced stores of rows [m0, m1) of a parked output tile (swizzled
+  // 16-byte chunks): thread t of nt takes chunks t, t + nt, ... of a
+  // 16-byte-aligned whole row, else words t, t + nt, ...
+  auto store_rows = [&](const W* ob, int64_t n0, int m0, int m1, int t,
+                        int nt) {
+    const int nv = (int)lmin((int64_t)T5_TILE, p.Nout - n0);  // valid
+#pragma unroll 1
+    for (int m = m0; m < m1; ++m) {
+      const W* row = ob + m * T5_TILE;
+      W* drow = y + (int64_t)m * p.ldy + n0;
+      const uintptr_t mis = reinterpret_cast<uintptr_t>(drow) & 15;
+      if (mis == 0 && nv == T5_TILE) {
+        for (int c = t; c < T5_TILE / V; c += nt)
+          *reinterpret_cast<typename Vec<W>::T*>(drow + c * V) =
+              *reinterpret_cast<const typename Vec<W>::T*>(
+                  row + t5_oswz<W>(c) * V);
+      } else if (sizeof(W) == 8 && mis == 8 && nv == T5_TILE) {
+        // a 64-bit row 8 bytes past a 16-byte boundary: words 0 and 1023
+        // alone, words (1 + 2c, 2 + 2c) as one 16-byte store
+        if (t == 0) {
+          drow[0] = row[t5_oswz<W>(0) * 2];
+          drow[T5_TILE - 1] = row[t5_oswz<W>(T5_TILE / 2 - 1) * 2 + 1];
+        }
+        for (int c = t; c < T5_TILE / 2 - 1; c += nt) {
+          const long long lo = (long long)row[t5_oswz<W>(c) * 2 + 1];
+          const long long hi = (long long)row[t5_oswz<W>(c + 1) * 2];
+          *reinterpret_cast<longlong2*>(drow + 1 + 2 * c) =
+              make_longlong2(lo, hi);
+        }
+      } else {
+        for (int jj = t; jj < nv; jj += nt)
+          drow[jj] = row[t5_oswz<W>(jj / V) * V + jj % V];
+      }
+    }
   };
   // the whole staged window lies inside the rows
   auto interior = [&](int64_t n0) {
@@ -259,6 +295,17 @@ tc5p_prot_kernel(const ConvArgs p) {
     // ---- staging ---------------------------------------------------------
     const int ts = threadIdx.x - T5P_WSTG * 32;
     const uint32_t bias_lo = (uint32_t)p.bias;
+    int done = 0;  // tiles staged
+    // tile j's recovered outputs, parked by the epilogue in output buffer
+    // j % 2
+    auto store_tile = [&](int j) {
+      const int so = j & 1;
+      if (!t5_wait(&bars.out_full[so], (uint32_t)(j >> 1) & 1u, abort))
+        return false;
+      store_rows(outb + so * MM * T5_TILE, tile_n0(j), 0, MM, ts, 128);
+      t5_arrive(&bars.out_empty[so]);
+      return true;
+    };
 #pragma unroll 1
     for (int i = 0; i < my_n; ++i) {
       const int s = i & 1;
@@ -268,15 +315,36 @@ tc5p_prot_kernel(const ConvArgs p) {
       const int64_t n0 = tile_n0(i);
       const W* rs = raw + s * RAW;
       uint16_t* ds = dig + s * DIG;
+      // chunk column cc of all MM rows at once: each raw chunk is read
+      // once (it is stream m's input and stream m+1's neighbour), and the
+      // MM loads are independent
       auto stage = [&](auto check_tag) {
         constexpr bool CHECK = decltype(check_tag)::value;
-        for (int k = ts; k < MM * CPS; k += 128) {
-          const int m = k / CPS, cc = k - m * CPS;
-          if (skip && m == r) continue;
-          const int mp = m == 0 ? MM - 1 : m - 1;
-          tc_stage_chunk<W, true, CHECK, false>(
-              rs + m * T5_STAGE, rs + mp * T5_STAGE, p.N, n0, cc, p.l, bias_lo,
-              ds + m * TC_ND * T5_STAGE, T5_STAGE);
+        using VT = typename Vec<W>::T;
+        for (int cc = ts; cc < CPS; cc += 128) {
+          const int64_t gi = n0 - TC_KP + (int64_t)cc * V;
+          VT rv[MM];
+#pragma unroll
+          for (int m = 0; m < MM; ++m)
+            rv[m] = *reinterpret_cast<const VT*>(rs + m * T5_STAGE + cc * V);
+#pragma unroll
+          for (int m = 0; m < MM; ++m) {
+            if (skip && m == r) continue;
+            const W* px = reinterpret_cast<const W*>(&rv[m]);
+            const W* py = reinterpret_cast<const W*>(&rv[m == 0 ? MM - 1 : m - 1]);
+            uint32_t v[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+              const uint32_t o = (uint32_t)px[e] +
+                                 (p.l < 32 ? (uint32_t)py[e] << p.l : 0u);
+              v[e] = (!CHECK || (gi + e >= 0 && gi + e < p.N)) ? o - bias_lo
+                                                               : 0u;
+            }
+#pragma unroll
+            for (int hh = 0; hh < V / 2; ++hh)
+              tc_put_pair<false>(ds + m * TC_ND * T5_STAGE, T5_STAGE,
+                                 cc * V + 2 * hh, v[2 * hh], v[2 * hh + 1]);
+          }
         }
       };
       if (interior(n0))
@@ -286,9 +354,16 @@ tc5p_prot_kernel(const ConvArgs p) {
       fence_proxy_async_smem();  // digits are read by the tensor cores
       t5_arrive(&bars.raw_empty[s]);
       t5_arrive(&bars.dig_full[s]);
+      if (i >= 2 && !store_tile(i - 2)) break;
+      done = i + 1;
     }
-  } else if (warp == T5P_WMMA) {
-    // ---- MMA issue -------------------------------------------------------
+    // the last two tiles' outputs
+    for (int j = done >= 2 ? done - 2 : 0; j < done; ++j)
+      if (!store_tile(j)) break;
+  } else if (warp == T5P_WMMA || warp == T5P_WMMA + 1) {
+    // ---- MMA issue: warp 13 takes the even streams, warp 14 the odd ones,
+    // from different schedulers ---------------------------------------------
+    const int parity = warp - T5P_WMMA;
     if (lane == 0) {
       // descriptors as 32-bit halves: the start address (>> 4) sits in the
       // low 14 bits, far from overflowing for addresses below 256 KB, so
@@ -309,7 +384,7 @@ tc5p_prot_kernel(const ConvArgs p) {
         const uint32_t dcol = tb + s * ACC;
 #pragma unroll
         for (int m = 0; m < MM; ++m) {
-          if (skip && m == r) continue;
+          if ((m & 1) != parity || (skip && m == r)) continue;
 #pragma unroll
           for (int d = 0; d < TC_ND; ++d) {
             constexpr int ROW = T5_STAGE * 2 / 16;  // 16-byte units per row
@@ -374,10 +449,14 @@ tc5p_prot_kernel(const ConvArgs p) {
       }
       t5_fence_before();
       t5_arrive(&bars.acc_empty[s]);  // this buffer's columns are read
+      // the output tile buffer s is free once the staging warps have
+      // stored tile i - 2 from it
+      if (!t5_epi_vote(t5_wait(&bars.out_empty[s], ph ^ 1u, abort))) break;
+      W* ob = outb + s * MM * T5_TILE;
       // recovery, 4 positions side by side; each row is parked as soon as
       // the chain reaches it
       auto park = [&](int m, const W (&vals)[4]) {
-        W* row = outb + m * T5_TILE;
+        W* row = ob + m * T5_TILE;
         const int j = 8 * a + 4 * h;  // local index, a multiple of 4
         if constexpr (sizeof(W) == 8) {
           *reinterpret_cast<longlong2*>(row + t5_oswz<W>(j / 2) * 2) =
@@ -406,26 +485,7 @@ tc5p_prot_kernel(const ConvArgs p) {
         for (int e = 0; e < 4; ++e) dcur[e] = wsub<W>(dl[q][e], dcur[e]) >> p.l;
       }
       park(r, dcur);
-      t5_epi_sync();  // the output tile is complete
-      // coalesced stores: thread t takes 16-byte chunks t, t + 256, ...
-      const int nv = (int)lmin((int64_t)T5_TILE, p.Nout - n0);  // valid
-#pragma unroll
-      for (int m = 0; m < MM; ++m) {
-        const W* row = outb + m * T5_TILE;
-        W* drow = y + (int64_t)m * p.ldy + n0;
-        if ((reinterpret_cast<uintptr_t>(drow) & 15) == 0 && nv == T5_TILE) {
-          // 16-byte row: chunk c to thread c mod 256
-          for (int c = threadIdx.x; c < T5_TILE / V; c += 256)
-            *reinterpret_cast<typename Vec<W>::T*>(drow + c * V) =
-                *reinterpret_cast<const typename Vec<W>::T*>(
-                    row + t5_oswz<W>(c) * V);
-        } else {
-          // word j to thread j mod 256
-          for (int j = threadIdx.x; j < nv; j += 256)
-            drow[j] = row[t5_oswz<W>(j / V) * V + j % V];
-        }
-      }
-      t5_epi_sync();  // the output tile may be overwritten
+      t5_arrive(&bars.out_full[s]);  // the staging warps store it
     }
   }
   // ---- teardown ------------------------------------------------------------
