@@ -382,9 +382,11 @@ tc5p_prot_kernel(const ConvArgs p) {
         t5_fence_after();
         const uint32_t a_lo = (uint32_t)a0 + (uint32_t)(s * DIG * 2 / 16);
         const uint32_t dcol = tb + s * ACC;
-#pragma unroll
-        for (int m = 0; m < MM; ++m) {
-          if ((m & 1) != parity || (skip && m == r)) continue;
+        // a rolled loop: the unrolled form costs instruction fetch more
+        // than it saves
+#pragma unroll 1
+        for (int m = parity; m < MM; m += 2) {
+          if (skip && m == r) continue;
 #pragma unroll
           for (int d = 0; d < TC_ND; ++d) {
             constexpr int ROW = T5_STAGE * 2 / 16;  // 16-byte units per row
