@@ -123,6 +123,9 @@ PROT_CASES = [
     (64, 3, 5000, 64, 8, 15, 0, 0),           # tcgen05, M = 3, 64-bit
     (64, 4, 1024 - 63, 64, 15, 15, 1, 0),     # tcgen05, one whole tile
     (32, 4, 4096, 65, 6, 7, 0, 0),            # tcgen05, 32-bit words
+    (64, 4, 40, 17, 15, 15, 0, 0),            # tcgen05, N shorter than the history
+    (64, 3, 2048, 65, 8, 15, 0, 2),           # tcgen05, K = 65, two input tiles
+    (32, 3, 5 * 1024, 64, 7, 7, 0, 0),        # tcgen05, 32-bit words, M = 3
 ]
 
 
@@ -151,6 +154,32 @@ def test_protected_tc_every_failure(ne, orc, case):
         assert np.array_equal(host(d), plain), (fm, r)
         if padd:  # nothing written past the end of a row
             assert (dfull[:, Nout:] == 77).all(), (fm, r)
+
+
+def test_protected_tc_extreme_taps(ne, orc):
+    """The declared tap bound 2^15 (the bench job's): taps at -2^15 and
+    2^15 - 1, whose top balanced digit reaches -128 and 128, and data at
+    both ends of [-2^15, 2^15), through the fused kernel, every failure."""
+    w, M, N, K = 64, 4, 3 * 1024 + 2, 64
+    p = ne.ne_params(M, w)
+    gen = synth.rng(4242)
+    c = synth.uniform_int(gen, (M, N), -(1 << 15), 1 << 15)
+    c[:, ::7] = (1 << 15) - 1
+    c[:, 3::7] = -(1 << 15)
+    g = synth.uniform_int(gen, (K,), -(1 << 15), 1 << 15)
+    g[::3] = -(1 << 15)
+    g[1::3] = (1 << 15) - 1
+    assert K * (1 << 15) * (1 << 15) <= p.d_max_exact
+    plain = orc.conv(c, g, w)
+    cd, gd = dev(c, w), torch.from_numpy(g.astype(np.int32)).cuda()
+    for fm, r in [(ne.NE_FAIL_NONE, -1)] + [(fm, r) for fm in (ne.NE_FAIL_SKIP,
+                                                               ne.NE_FAIL_DROP)
+                                            for r in range(M)]:
+        d = torch.full((M, N + K - 1), 5, dtype=torch.int64, device="cuda")
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(1 << 15), (1 << 15) - 1),
+                             max_abs_g=1 << 15, failed=r, fail_mode=fm)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), plain), (fm, r)
 
 
 def test_tensor_core_rate_probes(ne):
