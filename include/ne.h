@@ -83,8 +83,9 @@ int ne_version(void);
 /*
  * ne_get_device_error -- synchronise the current device and report the
  * library's device-side error word in *out: 0, or bit 0 set if a kernel's
- * bounded wait for one of its own bulk copies expired (the kernel then
- * stopped early and its outputs are incomplete).  clear != 0 resets it.
+ * bounded wait (for one of its own bulk copies, or for its tensor-core
+ * products or another warp's stage) expired; the kernel then stopped early
+ * and its outputs are incomplete.  clear != 0 resets it.
  * Blocks the host.  Returns NE_OK, NE_ERR_INVALID_ARG or NE_ERR_CUDA.
  */
 int ne_get_device_error(uint32_t *out, int clear);
@@ -237,30 +238,39 @@ int ne_detect(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
               int64_t *positions, int max_positions, void *stream);
 
 /*
- * ne_protected_conv -- the whole protected path in one launch:
+ * ne_protected_conv -- the whole protected path in one call:
  * entangle-on-load (Sec. II-B: entanglement applied as each input stream is
- * read) -> convolution of each entangled stream as independent units of
- * work (Eq. 9) -> per output tile, the (M-1)-th stream to deliver extracts
- * all M outputs from the M-1 delivered entangled tiles (Eq. 16-19; results
+ * read) -> convolution of each entangled stream (Eq. 9) -> per output tile,
+ * all M outputs recovered from M-1 entangled outputs (Eq. 16-19; results
  * are disentangled as soon as any M-1 output streams are available, Sec. V).
  *   c: M raw input rows of N words (ldc); g: K int32 taps;
  *   d: M output rows (ldd >= N+K-1), receives the true outputs d_m = c_m * g.
- *      It also serves as the landing buffer of the entangled tiles.
  *   [c_min, c_max]: caller's declared range of the inputs (c_min <= c_max);
- *   max_abs_g: bound on |g| (with entangled words that fit 32 bits, K <= 65
- *      and max_abs_g <= 32768 the product runs on the tensor cores, as in
- *      ne_conv_range, inside the cluster form below).  With B = max(|c_min|, |c_max|) the call
+ *   max_abs_g: bound on |g|.  With B = max(|c_min|, |c_max|) the call
  *      returns NE_ERR_RANGE if K*B*max_abs_g exceeds the exact output range
  *      for (M, w, l) or B(2^l + 1) does not fit w signed bits.  The range
  *      also picks the arithmetic: entangled words lie in
- *      [c_min(2^l+1), c_max(2^l+1)], and a span of at most 2^32 values
- *      takes one 32x32->64 multiply-add per tap (see ne_conv).
+ *      [c_min(2^l+1), c_max(2^l+1)].
  *   failed, fail_mode: failure injection (failed in [0, M) or -1 with
  *      NE_FAIL_NONE).
  *   ws: device workspace of ne_protected_conv_ws_bytes() bytes (per-tile
- *      arrival words; zeroed by this call on `stream`); ws_bytes its size.
- * No device-side waiting: the tile extractor is whichever stream arrives
- * (M-1)-th; a late M-th stream discards its result.
+ *      arrival words of the multiply-add form; zeroed by this call on
+ *      `stream` when that form runs); ws_bytes its size.
+ * Kernels.  When the entangled words fit 32 bits (a span of at most 2^32
+ * values, after the range shift), K <= 65 and max_abs_g <= 32768, the
+ * products run on the tensor cores, exactly (as in ne_conv_range):
+ *   3 <= M <= 4 and 16-byte-aligned rows of c: one warp-specialised tcgen05
+ *      kernel; the products stay in tensor memory and the recovery runs in
+ *      its epilogue; d is written once;
+ *   M <= 8 otherwise: one mma.sync kernel per output tile of all streams,
+ *      products in shared memory;
+ *   M > 8: an entangling product into d, then the recovery in place.
+ * Other jobs run on the integer multiply-add kernels (one 32x32->64
+ * multiply-add per tap for a span of at most 2^32 values, see ne_conv): a
+ * cluster per tile for short tiles, else per-tile arrival words, where d
+ * is also the landing buffer of the entangled tiles and a late M-th stream
+ * discards its result.  Waits inside a kernel are bounded; if one expires
+ * the outputs are incomplete and ne_get_device_error reports it.
  */
 int ne_protected_conv(const void *c, int64_t ldc, int M, int64_t N,
                       const int32_t *g, int K, int w, int l, int64_t c_min,
