@@ -423,10 +423,12 @@ int ne_protected_outer(const void *c, int64_t ldc, int M, int64_t N,
  * (512 KiB; every GPU that loads the library holds it until the process
  * exits).  Larger jobs return NE_ERR_NOMEM before any launch.
  *   - No cudaMalloc, cudaFree or other allocating call is made.  The array
- *     keeps the last call's contents; each call clears the words it uses
- *     (an asynchronous memset on `stream`) before its launch.
- *   - All calls share the one array per device: calls whose launches can
- *     overlap on the GPU (different streams, or different host threads)
+ *     keeps the last call's contents; each call that uses it clears the
+ *     words it uses (an asynchronous memset on `stream`) before its launch.
+ *   - Jobs in the tensor-core window (see ne_protected_conv) run the same
+ *     tensor-core kernels as ne_protected_conv and never touch the array.
+ *   - All other calls share the one array per device: calls whose launches
+ *     can overlap on the GPU (different streams, or different host threads)
  *     race and give wrong results.  Order them on one stream.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current) and caches it; make

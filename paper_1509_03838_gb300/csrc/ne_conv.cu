@@ -898,6 +898,49 @@ inline size_t rows_bytes(int rows, int64_t ld, int64_t n, int wb) {
   return ((size_t)(rows - 1) * (size_t)ld + (size_t)n) * (size_t)wb;
 }
 
+// The tensor-core forms of the protected convolution; none needs a
+// workspace.  a describes the job (a.ntiles unset); returns the status of
+// the form that ran, or kNotTaken when the job is outside the tensor-core
+// window (operands beyond 32 bits after the range shift, K > 65,
+// |g| > 2^15) or another form is forced.
+constexpr int kNotTaken = 1 << 30;
+int protected_tc(const ConvArgs& a, int mode, int64_t max_abs_g, int w,
+                 bool vec, cudaStream_t s) {
+  if (!tc_eligible(mode, a.K, max_abs_g)) return kNotTaken;
+  const ProtForm form = forced_form();
+  const int M = a.M, wb = w / 8;
+  const bool vec_out = rows_aligned16(a.y, a.ldy, wb);
+  if (form == FORM_AUTO && M <= T5_MAX_M && vec && tc5_enabled()) {
+    // fifth-generation tensor cores, fused: products in tensor memory,
+    // recovery in the epilogue's registers
+    ConvArgs t = a;
+    t.ntiles = (a.Nout + T5_TILE - 1) / T5_TILE;
+    return dispatch_tc5_prot(t, w, vec_out, s);
+  }
+  if (form == FORM_AUTO && M <= TCP_MAX_M) {
+    // tensor cores, fused: products and recovery tile by tile in one kernel
+    ConvArgs t = a;
+    t.ntiles = (a.Nout + tcp_tile(M) - 1) / tcp_tile(M);
+    return dispatch_tc_prot(t, w, vec, vec_out, s);
+  }
+  if (form == FORM_AUTO || form == FORM_TWOPASS) {
+    // tensor cores, two passes: every computing stream's entangled product
+    // delta_m into d (entangled on load), then the recovery of all M in
+    // place
+    ConvArgs t = a;
+    t.ntiles = (a.Nout + TC_TILE - 1) / TC_TILE;
+    const uint32_t all = M == 32 ? 0xffffffffu : (1u << M) - 1u;
+    t.live_mask =
+        a.fail_mode == NE_FAIL_SKIP ? (all & ~(1u << a.failed)) : all;
+    const int st = dispatch_tc_conv<true>(t, w, vec, s);
+    if (st != NE_OK) return st;
+    if (a.fail_mode == NE_FAIL_NONE)
+      return ne_extract(a.y, a.ldy, M, a.Nout, w, a.l, a.y, a.ldy, s);
+    return ne_recover(a.y, a.ldy, M, a.Nout, w, a.l, a.failed, a.y, a.ldy, s);
+  }
+  return kNotTaken;
+}
+
 }  // namespace
 
 // Host reader of this translation unit's device error word.
@@ -1098,37 +1141,8 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
-  const ProtForm form = forced_form();
-  if (tc_eligible(mode, K, max_abs_g) && form == FORM_AUTO &&
-      M <= T5_MAX_M && vec && tc5_enabled()) {
-    // fifth-generation tensor cores, fused: products in tensor memory,
-    // recovery in the epilogue's registers
-    ConvArgs t = a;
-    t.ntiles = (Nout + T5_TILE - 1) / T5_TILE;
-    return dispatch_tc5_prot(t, w, rows_aligned16(d, ldd, wb), s);
-  }
-  if (tc_eligible(mode, K, max_abs_g) && form == FORM_AUTO &&
-      M <= TCP_MAX_M) {
-    // tensor cores, fused: products and recovery tile by tile in one kernel
-    ConvArgs t = a;
-    t.ntiles = (Nout + tcp_tile(M) - 1) / tcp_tile(M);
-    return dispatch_tc_prot(t, w, vec, rows_aligned16(d, ldd, wb), s);
-  }
-  if (tc_eligible(mode, K, max_abs_g) &&
-      (form == FORM_AUTO || form == FORM_TWOPASS)) {
-    // tensor cores, two passes: every computing stream's entangled product
-    // delta_m into d (entangled on load), then the recovery of all M in
-    // place
-    ConvArgs t = a;
-    t.ntiles = (Nout + TC_TILE - 1) / TC_TILE;
-    const uint32_t all = M == 32 ? 0xffffffffu : (1u << M) - 1u;
-    t.live_mask = fail_mode == NE_FAIL_SKIP ? (all & ~(1u << failed)) : all;
-    const int st = dispatch_tc_conv<true>(t, w, vec, s);
-    if (st != NE_OK) return st;
-    if (fail_mode == NE_FAIL_NONE)
-      return ne_extract(d, ldd, M, Nout, w, l, d, ldd, stream);
-    return ne_recover(d, ldd, M, Nout, w, l, failed, d, ldd, stream);
-  }
+  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s);
+  if (tc != kNotTaken) return tc;
   if (use_cluster(M, K, w, mode, a.ntiles)) {
     if (dispatch_cluster(a, w, mode, vec, s) == NE_OK) return NE_OK;
     // a refused cluster launch (configuration error, not sticky): clear it
@@ -1216,15 +1230,8 @@ extern "C" int ne_protected_conv_noalloc(const void* c, int64_t ldc, int M,
   const int wb = w / 8;
   if (overlaps(c, rows_bytes(M, ldc, N, wb), d, rows_bytes(M, ldd, Nout, wb)))
     return NE_ERR_INVALID_ARG;
-  uint32_t* ws = nullptr;
-  const int st = noalloc_arrivals(&ws);
-  if (st != NE_OK) return st;
-  const int64_t ntiles = (Nout + CONV_TILE - 1) / CONV_TILE;
   cudaStream_t s = (cudaStream_t)stream;
-  // the array keeps the previous call's words: clear the ones this call uses
-  if (cudaMemsetAsync(ws, 0, (size_t)ntiles * 2 * sizeof(uint32_t), s) !=
-      cudaSuccess)
-    return NE_ERR_CUDA;
+  const int64_t ntiles = (Nout + CONV_TILE - 1) / CONV_TILE;
   ConvArgs a{};
   a.x = c;
   a.ldx = ldc;
@@ -1241,10 +1248,20 @@ extern "C" int ne_protected_conv_noalloc(const void* c, int64_t ldc, int M,
   a.l = l;
   a.failed = failed;
   a.fail_mode = fail_mode;
-  a.ws = ws;
   const __int128 f = ((__int128)1 << l) + 1;
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
+  // the tensor-core forms need no arrival words
+  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s);
+  if (tc != kNotTaken) return tc;
+  uint32_t* ws = nullptr;
+  const int st = noalloc_arrivals(&ws);
+  if (st != NE_OK) return st;
+  // the array keeps the previous call's words: clear the ones this call uses
+  if (cudaMemsetAsync(ws, 0, (size_t)ntiles * 2 * sizeof(uint32_t), s) !=
+      cudaSuccess)
+    return NE_ERR_CUDA;
+  a.ws = ws;
   return dispatch_conv<true>(a, w, mode, vec, s);
 }
