@@ -359,8 +359,11 @@ def ne_protected_conv(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
                       failed: int = -1, fail_mode: int = NE_FAIL_NONE,
                       ws: torch.Tensor | None = None, N: int | None = None,
                       stream=None) -> torch.Tensor:
-    """Entangle-on-load -> conv -> extract/recover, one launch (d = c * g).
-    c_range = (c_min, c_max): declared range of the inputs."""
+    """Entangle-on-load -> conv -> extract/recover in one call (d = c * g):
+    one fused launch for M <= 8 (tensor cores when the job fits their
+    window, else the multiply-add kernels), two for the tensor-core form at
+    M > 8.  c_range = (c_min, c_max): declared range of the inputs;
+    max_abs_g: declared bound on |g|."""
     pc, M, n, ldc = _rows(c, "c")
     pd, _, _, ldd = _rows(d, "d")
     n = n if N is None else N
