@@ -20,10 +20,12 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
 
+#include "ne_conv_args.cuh"
 #include "ne_conv_core.cuh"
 #include "ne_tc5.cuh"
 
@@ -31,26 +33,6 @@ namespace ne {
 
 namespace {
 
-struct ConvArgs {
-  const void* x;   // input rows (raw, entangled, or raw to entangle on load)
-  int64_t ldx;
-  int M;
-  int64_t N;
-  int64_t Nout;
-  int64_t ntiles;
-  const int32_t* g;
-  int K;
-  int Kp;          // K rounded up to CONV_KC
-  void* y;         // output rows
-  int64_t ldy;
-  uint32_t live_mask;  // plain conv: streams to compute
-  int l;               // entanglement shift (protected kernel)
-  int failed;
-  int fail_mode;
-  uint32_t* ws;        // protected kernel: per-tile {claim, ready} words
-  long long bias;      // MODE_WIDE range shift b (x - b fits 32 bits)
-  int kind;            // NE_CONV_LINEAR / NE_CONV_CIRCULAR / NE_CONV_XCORR
-};
 
 // Stage s[j] = x[n0 - Kp + j] (zero outside [0, N)) for j in [0, TILE+Kp)
 // through registers, optionally entangling on load: x = row + (prev << l).
@@ -898,6 +880,76 @@ inline size_t rows_bytes(int rows, int64_t ld, int64_t n, int wb) {
   return ((size_t)(rows - 1) * (size_t)ld + (size_t)n) * (size_t)wb;
 }
 
+// ---- raw-plane tcgen05 kernels ------------------------------------------
+// NE_CONV_TCR=0 keeps the earlier tensor-core kernels where these would run.
+inline bool tcr_enabled() {
+  static const bool off = [] {
+    const char* e = getenv("NE_CONV_TCR");
+    return e && strcmp(e, "0") == 0;
+  }();
+  return !off;
+}
+
+// Byte digits for values in [lo, hi]: the least ND with hi - lo < 256^ND,
+// or 0 beyond four bytes.
+inline int tcr_digits(__int128 lo, __int128 hi) {
+  for (int nd = 1; nd <= 4; ++nd)
+    if (hi - lo < ((__int128)1 << (8 * nd))) return nd;
+  return 0;
+}
+
+// Fault injection for tests (ne_debug_set_fault): the next launches of the
+// raw-plane kernels get a short wait limit and a role that never runs.
+std::atomic<uint32_t> g_debug_wait_limit{0};
+std::atomic<int> g_debug_stall_role{0};
+
+// Fill the raw-plane fields of a for inputs in [lo, hi] (known range):
+// returns false if the job is outside these kernels' window.
+inline bool tcr_plan(ConvArgs& a, bool prot, int w, __int128 lo, __int128 hi,
+                     int64_t max_abs_g, bool vec) {
+  if (!tc_enabled() || !tcr_enabled() || a.K > TR_HMAX + 1 || max_abs_g < 0 ||
+      max_abs_g > TC_MAX_G || (prot && (a.M < 3 || a.M > 6)))
+    return false;
+  const int nd = tcr_digits(lo, hi);
+  if (nd == 0 || (prot && nd > 2)) return false;
+  a.nd = nd;
+  a.hist = 16 * ((a.K - 1 + 15) / 16);
+  a.ks = (TR_P + a.hist) / 16;
+  // protected, l = 8 q with q <= nd (M = 4 only): the neighbour's levels
+  // q .. q + nd share the stream's own columns; a merged level gathers at
+  // most P products per tap (P = own pairs + neighbour pairs at that
+  // level), exact while P K 2^14 <= 2^22
+  a.mlev = 0;
+  if (prot && a.M == 4 && a.l % 8 == 0 && a.l / 8 >= 1 && a.l / 8 <= nd) {
+    const int q = a.l / 8;
+    int pmax = 0;
+    for (int L = 0; L <= nd + q; ++L) {
+      int pairs = 0;
+      for (int i = 0; i < nd; ++i)
+        for (int j = 0; j < 2; ++j) pairs += (i + j == L) + (q + i + j == L);
+      pmax = std::max(pmax, pairs);
+    }
+    if ((long long)pmax * a.K <= 256) a.mlev = q;
+  }
+  a.tcols = (a.mlev ? nd + a.mlev + 1 : (prot ? 2 : 1) * (nd + 1)) * 32;
+  a.tslots = std::min(4, 512 / a.tcols);
+  a.vec = vec ? 1 : 0;
+  a.ntiles = (a.Nout + TR_TILE - 1) / TR_TILE;
+  a.bias = (long long)(uint64_t)(unsigned __int128)lo;
+  // x = B + sum of balanced digits, B = lo + 128 (1 + 256 + ...)
+  unsigned long long beff = (unsigned long long)(unsigned __int128)lo;
+  for (int i = 0; i < nd; ++i) beff += 128ull << (8 * i);
+  const unsigned long long f = prot ? (1ull << a.l) + 1ull : 1ull;
+  a.corr_mul = (w == 32 ? (unsigned long long)(uint32_t)(beff * f) : beff * f);
+  a.wait_limit = g_debug_wait_limit.load();
+  a.stall_role = g_debug_stall_role.load();
+  return true;
+}
+
+int dispatch_tcr(const ConvArgs& a, bool prot, int w, cudaStream_t s) {
+  return w == 32 ? tcr_launch_w32(a, prot, s) : tcr_launch_w64(a, prot, s);
+}
+
 // The tensor-core forms of the protected convolution; none needs a
 // workspace.  a describes the job (a.ntiles unset); returns the status of
 // the form that ran, or kNotTaken when the job is outside the tensor-core
@@ -905,9 +957,18 @@ inline size_t rows_bytes(int rows, int64_t ld, int64_t n, int wb) {
 // |g| > 2^15) or another form is forced.
 constexpr int kNotTaken = 1 << 30;
 int protected_tc(const ConvArgs& a, int mode, int64_t max_abs_g, int w,
-                 bool vec, cudaStream_t s) {
-  if (!tc_eligible(mode, a.K, max_abs_g)) return kNotTaken;
+                 bool vec, cudaStream_t s, int64_t c_min, int64_t c_max) {
   const ProtForm form = forced_form();
+  if (form == FORM_AUTO && a.M >= 3 && a.M <= 6) {
+    // raw-plane tcgen05 kernel: products from the digit planes of the raw
+    // rows, entangled in the accumulators, recovered in the epilogue
+    ConvArgs t = a;
+    if (tcr_plan(t, true, w, (__int128)c_min, (__int128)c_max, max_abs_g, vec)) {
+      const int st = dispatch_tcr(t, true, w, s);
+      if (st != NE_ERR_UNSUPPORTED) return st;
+    }
+  }
+  if (!tc_eligible(mode, a.K, max_abs_g)) return kNotTaken;
   const int M = a.M, wb = w / 8;
   const bool vec_out = rows_aligned16(a.y, a.ldy, wb);
   if (form == FORM_AUTO && M <= T5_MAX_M && vec && tc5_enabled()) {
@@ -999,6 +1060,32 @@ int ne_conv_range(const void* x, int64_t ldx, int M, int64_t N,
                   int64_t ldy, int w, int64_t x_min, int64_t x_max,
                   uint32_t live_mask, void* stream) {
   if (max_abs_g < 0) return NE_ERR_INVALID_ARG;
+  if (x_min <= x_max && (w == 32 || w == 64) && M >= 1 && M <= 32 && N > 0 &&
+      K >= 1 && K <= TR_HMAX + 1 && ldx >= N && x && y && g &&
+      ldy >= N + K - 1) {
+    // raw-plane tcgen05 kernel, when the declared ranges allow it
+    const int wb = w / 8;
+    const int64_t Nout = N + K - 1;
+    if (overlaps(x, rows_bytes(M, ldx, N, wb), y, rows_bytes(M, ldy, Nout, wb)))
+      return NE_ERR_INVALID_ARG;
+    ConvArgs a{};
+    a.x = x;
+    a.ldx = ldx;
+    a.M = M;
+    a.N = N;
+    a.Nout = Nout;
+    a.g = g;
+    a.K = K;
+    a.y = y;
+    a.ldy = ldy;
+    a.live_mask = M == 32 ? live_mask : (live_mask & ((1u << M) - 1u));
+    if (a.live_mask == 0) return NE_OK;
+    if (tcr_plan(a, false, w, (__int128)x_min, (__int128)x_max, max_abs_g,
+                 rows_aligned16(x, ldx, wb))) {
+      const int st = dispatch_tcr(a, false, w, (cudaStream_t)stream);
+      if (st != NE_ERR_UNSUPPORTED) return st;
+    }
+  }
   long long bias = 0;
   const int mode = (w == 32 || w == 64)
                        ? choose_mode(w, x_min <= x_max, (__int128)x_min,
@@ -1141,7 +1228,7 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
-  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s);
+  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s, c_min, c_max);
   if (tc != kNotTaken) return tc;
   if (use_cluster(M, K, w, mode, a.ntiles)) {
     if (dispatch_cluster(a, w, mode, vec, s) == NE_OK) return NE_OK;
@@ -1253,7 +1340,7 @@ extern "C" int ne_protected_conv_noalloc(const void* c, int64_t ldc, int M,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
   // the tensor-core forms need no arrival words
-  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s);
+  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s, c_min, c_max);
   if (tc != kNotTaken) return tc;
   uint32_t* ws = nullptr;
   const int st = noalloc_arrivals(&ws);

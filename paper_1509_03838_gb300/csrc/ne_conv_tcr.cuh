@@ -1,0 +1,819 @@
+// Exact integer convolution on the tcgen05 tensor cores from the byte-digit
+// planes of the RAW input rows, plain (one stream at a time) or protected
+// (entangled products, recovered in the epilogue).  Included by
+// ne_conv_tcr_w32.cu and ne_conv_tcr_w64.cu, one word width each.
+//
+// Digits.  After a range shift b, every raw input x - b lies in
+// [0, 256^ND) (ND = 1..4 bytes); its bytes u_i become the balanced digits
+// u_i - 128 in [-128, 127], so x = B + sum_i 256^i (u_i - 128) with
+// B = b + 128 (1 + 256 + ... + 256^(ND-1)).  A tap (|g| <= 2^15) is the two
+// balanced digits g = g_0 + 256 g_1.  Every digit is an integer that fp16
+// holds exactly; a digit product is at most 2^14 in magnitude.  The product
+// of operand digit i and tap digit j is accumulated at level i + j, so a
+// level gathers at most two products per tap: over K <= 65 taps every fp32
+// partial sum is an integer of at most 2^21.1 in magnitude and exact.
+// Samples outside [0, N) get all digits 0 (bytes 128).
+//
+// The product as a GEMM.  Row a of a tile (a < 128) holds the 32 outputs
+// y[n0 + 32a + o], o < 32, which read the inputs x[n0 - H + 32a + k],
+// k < 32 + H (H = K - 1 rounded up to 16):
+//     y[n0 + 32a + o] = sum_k A[a][k] B[(j, o)][k],
+//     A[a][k] = digit of x[n0 - H + 32a + k],  B[(j, o)][k] = g_j[o + H - k].
+// A is a generalised Hankel matrix (rows 32 samples apart).  A digit plane
+// stores the staged window in 16-byte chunks (8 samples): chunk rho at
+// column rho % 4, row rho / 4, columns 2080 bytes apart.  For k-step s the
+// descriptor starts at column 2 (s % 2), row s / 2, with the leading
+// (k-half) offset one column and the stride of 8 rows 128 bytes: element
+// (a, k) then lands on chunk 4a + 2s + k / 8, as A requires, and every
+// sample is stored once.  B's 64 columns are (tap digit j, offset o); with
+// D starting at column 32 i for operand digit i, tap digit j lands at level
+// i + j.  One instruction (M = 128, N = 64, K = 16) covers 4096 outputs for
+// one operand digit and one k-step; a plane set takes ND x (2 + H / 16).
+//
+// Entanglement on the digit planes (protected form).  eps_m = c_m + 2^l
+// c_{m-1} (Eq. 6) is linear, so stream m's products delta_m = eps_m * g
+// (Eq. 9) are formed by stream m's own instructions from two plane sets:
+// its own row c_m (levels 0..ND of its accumulator) and its neighbour
+// c_{m-1} (levels ND+1 .. 2ND+1, weighted by 2^l in the epilogue).  Each
+// stream's products stay in its own tensor-memory slot; a stream that
+// fail-stops loses exactly delta_m.
+//
+// Pipeline (one persistent block of 768 threads per SM, warp-specialised,
+// mbarrier rings, every wait bounded):
+//   loader   (warp 22)      raw rows by bulk copies into a ring of NRAW;
+//   staging  (warps 16-21)  raw row -> ND digit planes into a ring of 3-4
+//                           (the ragged ends of the rows and rows that are
+//                           not 16-byte aligned straight from global
+//                           memory, with bounds checks);
+//   MMA      (warp 23)      per stream: the products into a tensor-memory
+//                           slot (the first instruction spans the slot with
+//                           a zero-extended B and no accumulate, which
+//                           clears it); commits to the slot and the planes;
+//   epilogue (warps 0-15)   warp w reads lanes 32 (w % 4) .. + 31 (rows a)
+//                           and offsets 8 (w / 4) .. + 7 of every level:
+//                           8 outputs of row a per stream, converted
+//                           exactly (fp32 + 1.5 * 2^23, then integer), the
+//                           range shift undone, then (protected) all M
+//                           outputs recovered from the M - 1 products other
+//                           than r's (Eq. 16-19, w-bit chain); each output
+//                           row passes through a swizzled shared tile so
+//                           that its stores are coalesced.
+// One lane of each role polls an mbarrier (a hinted try_wait, which
+// sleeps); the rest of the role waits on a named barrier, so that waiting
+// warps take no issue slots.
+// Stream order within a tile (protected): r, r+1, ..., r+M-1 (r = M - 1
+// without a failure; stream r computes first and its result is dropped),
+// or r+1, ..., r+M-1 with NE_FAIL_SKIP; rows are staged in the order
+// r-1, r, ..., r+M-1 (or r, ..., r+M-1), so that stream q of the order
+// reads row positions q (neighbour) and q + 1 (own).
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "ne_conv_args.cuh"
+#include "ne_conv_core.cuh"
+#include "ne_tc5.cuh"
+
+namespace ne {
+namespace {
+
+constexpr int TR_SMAX = TR_TILE + TR_HMAX;      // staged samples per row
+constexpr int TR_CROWS = 128 + TR_HMAX / TR_P;  // rows per chunk column
+constexpr int TR_LBO = TR_CROWS * 16;           // bytes per chunk column
+constexpr int TR_PLANE = 4 * TR_LBO;            // bytes per digit plane
+constexpr int TR_NB = 2 * TR_P;                 // B columns (o, tap digit)
+constexpr int TR_B0 = 256 * 32;                 // B bytes of k-step 0 (256 rows)
+constexpr int TR_BS = TR_NB * 32;               // B bytes of a later k-step
+constexpr int TR_KSMAX = (TR_P + TR_HMAX) / 16; // 6
+constexpr int TR_BBYTES = TR_B0 + (TR_KSMAX - 1) * TR_BS;
+constexpr int TR_THREADS = 768;
+constexpr int TR_WSTG = 16;                     // first staging warp (6 warps)
+constexpr int TR_NSTG = 192;                    // staging threads
+constexpr int TR_WLOAD = 22;                    // loader warp
+constexpr int TR_WMMA = 23;                     // MMA warp (owns tensor memory)
+constexpr int TR_EPI = 512;                     // epilogue threads
+constexpr uint32_t TR_MAGIC = 0x4B400000u;      // bits of 1.5 * 2^23
+constexpr int TR_TAPS = 96;                     // taps kept (K <= 65)
+
+// raw-row slots (three while the plane ring leaves room, else two) and
+// digit-plane row slots (four, three with four digits)
+__host__ __device__ constexpr int tr_nraw(int nd) { return nd <= 2 ? 3 : 2; }
+__host__ __device__ constexpr int tr_nrs(int nd) { return nd <= 3 ? 4 : 3; }
+
+struct TrBars {
+  uint64_t raw_full[3], raw_empty[3];
+  uint64_t rs_full[4], rs_empty[4];
+  uint64_t acc_full[4], acc_empty[4];
+  uint64_t drain;
+  uint32_t tbase;
+  int abort;
+  int live_rows[32];  // plain form: the live streams in order
+};
+
+struct TrTaps {
+  int taps[TR_TAPS];
+  long long pref[TR_TAPS];
+  long long total;
+};
+
+// Dynamic shared memory: plane ring, raw ring, output tile, B, taps,
+// barriers.
+template <typename W, int ND>
+__host__ __device__ constexpr size_t tr_smem_bytes() {
+  return (size_t)tr_nrs(ND) * ND * TR_PLANE +
+         (size_t)tr_nraw(ND) * TR_SMAX * sizeof(W) + TR_TILE * sizeof(W) +
+         TR_BBYTES + sizeof(TrTaps) + sizeof(TrBars) + 256;
+}
+
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about `ns` nanoseconds pass, taking no issue slots.
+__device__ __forceinline__ bool tr_try_wait(uint64_t* bar, uint32_t parity,
+                                            uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: at most `limit` suspended polls of up to 20 us each (0: the
+// default, 2^16 polls, about 1.3 s).  Gives up when the block's abort word
+// is set, or sets it (and the library's device error word) when the limit
+// runs out.
+constexpr uint32_t TR_POLL_NS = 20000;
+__device__ __forceinline__ bool tr_wait(uint64_t* bar, uint32_t parity,
+                                        volatile int* abort, uint32_t limit) {
+  const uint32_t lim = limit ? limit : (1u << 16);
+  for (uint32_t it = 0; it < lim; ++it) {
+    if (tr_try_wait(bar, parity, TR_POLL_NS)) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
+  atomicOr(&g_ne_device_error, 1u);
+  return false;
+}
+// Named barrier ID over NT threads with an AND vote: one thread polls an
+// mbarrier and the others sleep here.
+template <int ID, int NT>
+__device__ __forceinline__ bool tr_vote(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(ok ? 1u : 0u), "n"(ID), "n"(NT)
+      : "memory");
+  return r != 0;
+}
+template <int ID, int NT>
+__device__ __forceinline__ void tr_bar() {
+  asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(NT) : "memory");
+}
+__device__ __forceinline__ uint16_t tr_half(int v) {
+  return __half_as_ushort(__int2half_rn(v));
+}
+// Balanced digits (byte I - 128) of two operands as one fp16 pair: the
+// byte is placed under the exponent of 1024, then 1152 is subtracted; both
+// steps are exact.
+template <int I>
+__device__ __forceinline__ uint32_t tr_digit_pair(uint32_t a, uint32_t b) {
+  constexpr uint32_t sel = (uint32_t)I | (0x4u << 4) | ((uint32_t)(I + 4) << 8) |
+                           (0x4u << 12);
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+  r = (r & 0x00ff00ffu) | 0x64006400u;
+  uint32_t h;
+  asm("sub.f16x2 %0, %1, %2;" : "=r"(h) : "r"(r), "r"(0x64806480u));
+  return h;
+}
+// fp32 accumulator bits -> bits of (value + 1.5 * 2^23): an integer value v
+// with |v| <= 2^22 becomes TR_MAGIC + v, exactly.
+__device__ __forceinline__ uint32_t tr_mag(uint32_t bits) {
+  return __float_as_uint(__uint_as_float(bits) + 12582912.0f);
+}
+// sum_L 256^L v_L of the levels 0..ND from their magic-shifted bits c_L:
+// pairs of levels combine exactly in 32 bits (|v0 + 256 v1| < 2^30).
+template <int ND>
+__device__ __forceinline__ long long tr_levels64(const uint32_t (&c)[ND + 1]) {
+  const int t01 = (int)(c[0] + 256u * c[1] - 257u * TR_MAGIC);
+  long long v = t01;
+  if constexpr (ND == 1) return v;
+  if constexpr (ND == 2) return v + (long long)(int)(c[2] - TR_MAGIC) * 65536ll;
+  if constexpr (ND >= 3) {
+    const int t23 = (int)(c[2] + 256u * c[3] - 257u * TR_MAGIC);
+    v += (long long)t23 * 65536ll;
+  }
+  if constexpr (ND == 4) v += (long long)(int)(c[4] - TR_MAGIC) * 4294967296ll;
+  return v;
+}
+template <int ND>
+__device__ __forceinline__ uint32_t tr_levels32(const uint32_t (&c)[ND + 1]) {
+  uint32_t v = c[0] + 256u * c[1] - 257u * TR_MAGIC;
+  if constexpr (ND == 2) v += (c[2] - TR_MAGIC) << 16;
+  if constexpr (ND >= 3) v += (c[2] + 256u * c[3] - 257u * TR_MAGIC) << 16;
+  return v;  // level 4 (2^32) vanishes modulo 2^32
+}
+__device__ __forceinline__ void tr_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+        "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr));
+}
+
+// One plane set's products (ND digits x KS k-steps) into columns dc + 32 d;
+// with CLEAR the first instruction spans all `idw` columns with no
+// accumulate.  Descriptors arrive as 32-bit halves; every k-step's offset
+// is a compile-time constant.
+template <int ND, int KS, bool CLEAR>
+__device__ __forceinline__ void tr_issue_set(uint32_t dc, uint32_t pa,
+                                             uint32_t a_hi, uint32_t b_lo,
+                                             uint32_t b_hi, uint32_t idw,
+                                             uint32_t id64) {
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+#pragma unroll
+    for (int s = 0; s < KS; ++s) {
+      const uint32_t al = pa + (uint32_t)((d * TR_PLANE + TR_LBO * 2 * (s & 1) +
+                                           16 * (s >> 1)) >> 4);
+      const uint32_t bl = b_lo + (uint32_t)(s == 0 ? 0 : (TR_B0 + (s - 1) * TR_BS) >> 4);
+      if (CLEAR && d == 0 && s == 0)
+        t5_mma_lh<false>(dc, al, a_hi, bl, b_hi, idw);
+      else
+        t5_mma_lh<true>(dc + 32u * d, al, a_hi, bl, b_hi, id64);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PROT = false: y_m = x_m * g for every stream of live_mask (ne_conv_range).
+// PROT = true (MM = M): the fused protected convolution (ne_protected_conv).
+// ND: byte digits of the shifted raw inputs.  Q (protected, l = 8 Q): the
+// neighbour's levels start at level Q of the stream's own and share its
+// accumulator columns (exact while a merged level gathers at most 4 K
+// products <= 2^22 in all); Q = 0 keeps them in levels of their own.
+// ---------------------------------------------------------------------------
+template <typename W, bool PROT, int MM, int ND, int Q>
+__global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs p) {
+  extern __shared__ __align__(128) int4 tr_dyn[];
+  constexpr int NRAW = tr_nraw(ND);
+  constexpr int TR_NRS = tr_nrs(ND);
+  constexpr int NLEV = ND + 1;                    // levels per plane set
+  constexpr int NLM = ND + Q + 1;                 // merged levels (Q > 0)
+  const int H = p.hist, KS = p.ks;
+  const int S = TR_TILE + H;                      // staged samples per row
+  const int tcols = p.tcols, tslots = p.tslots;   // tensor-memory slots
+  unsigned char* planes = reinterpret_cast<unsigned char*>(tr_dyn);
+  W* raw = reinterpret_cast<W*>(planes + (size_t)TR_NRS * ND * TR_PLANE);
+  W* otile = raw + NRAW * TR_SMAX;  // one output row of a tile, swizzled
+  unsigned char* bmat = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(otile + TR_TILE) + 127) & ~(uintptr_t)127);
+  TrTaps& tt = *reinterpret_cast<TrTaps*>(bmat + TR_BBYTES);
+  TrBars& bars = *reinterpret_cast<TrBars*>(
+      (reinterpret_cast<uintptr_t>(&tt + 1) + 7) & ~(uintptr_t)7);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const W* x = reinterpret_cast<const W*>(p.x);
+  W* y = reinterpret_cast<W*>(p.y);
+  const int M = PROT ? MM : p.M;
+  const int r = PROT ? (p.fail_mode == NE_FAIL_NONE ? MM - 1 : p.failed) : 0;
+  const bool skip = PROT && p.fail_mode == NE_FAIL_SKIP;
+  // stream and row sequences of one tile
+  const uint32_t live = p.live_mask & (M >= 32 ? 0xffffffffu : ((1u << M) - 1u));
+  const int nstreams = PROT ? (skip ? MM - 1 : MM) : __popc(live);
+  const int nrows = PROT ? nstreams + 1 : nstreams;
+  const int rbase = PROT ? (skip ? r : (r == 0 ? MM - 1 : r - 1)) : 0;
+  auto row_of = [&](int j) -> int {  // raw row staged at position j
+    if constexpr (PROT) {
+      const int v = rbase + j;
+      return v >= MM ? v - MM : v;
+    } else {
+      return bars.live_rows[j];
+    }
+  };
+
+  // ---- setup: barriers and tensor memory, then (without the loader, which
+  // starts its copies at once) B and the tap sums ---------------------------
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NRAW; ++s) {
+      mbar_init(&bars.raw_full[s], 1);
+      mbar_init(&bars.raw_empty[s], TR_NSTG / 32);  // one per staging warp
+    }
+    for (int s = 0; s < TR_NRS; ++s) {
+      mbar_init(&bars.rs_full[s], TR_NSTG / 32);
+      mbar_init(&bars.rs_empty[s], 1);    // tcgen05.commit
+    }
+    for (int s = 0; s < 4; ++s) {
+      mbar_init(&bars.acc_full[s], 1);    // tcgen05.commit
+      mbar_init(&bars.acc_empty[s], 16);  // one arrival per epilogue warp
+    }
+    mbar_init(&bars.drain, 1);
+    bars.abort = 0;
+    if (!PROT) {
+      int n = 0;
+      for (int m = 0; m < M; ++m)
+        if (live & (1u << m)) bars.live_rows[n++] = m;
+    }
+    fence_mbar_init();
+  }
+  if (warp == TR_WMMA) t5_alloc(&bars.tbase, 512);
+  t5_fence_before();
+  __syncthreads();
+  t5_fence_after();
+  if (warp != TR_WLOAD) {
+    for (int t = threadIdx.x; t < TR_TAPS; t += TR_THREADS)
+      tt.taps[t] = t < p.K ? __ldg(p.g + t) : 0;
+    tr_bar<3, TR_THREADS - 32>();
+    // B, K-major without swizzling: element (n, kk) of k-step s at
+    // 256 (n / 8) + 16 (n % 8) + 128 (kk / 8) + 2 (kk % 8) of its block; the
+    // block of k-step 0 has 256 rows, rows n >= 64 zero (the clearing
+    // instruction spans a whole slot)
+    const int tid = threadIdx.x < TR_WLOAD * 32 ? threadIdx.x : threadIdx.x - 32;
+    for (int idx = tid; idx < TR_BBYTES / 2; idx += TR_THREADS - 32) {
+      const int off = 2 * idx;
+      const int s = off < TR_B0 ? 0 : 1 + (off - TR_B0) / TR_BS;
+      const int o2 = off < TR_B0 ? off : (off - TR_B0) % TR_BS;
+      const int n = (o2 / 256) * 8 + (o2 % 128) / 16;
+      const int kk = ((o2 % 256) / 128) * 8 + (o2 % 16) / 2;
+      int v = 0;
+      if (n < TR_NB && s < KS) {
+        const int jg = n / TR_P, o = n % TR_P;
+        const int t = o + H - (16 * s + kk);
+        if (t >= 0 && t < p.K) {
+          const int gv = tt.taps[t];
+          const int g0 = (int)(int8_t)(gv & 0xff);
+          v = jg == 0 ? g0 : (gv - g0) >> 8;
+        }
+      }
+      reinterpret_cast<uint16_t*>(bmat)[idx] = tr_half(v);
+    }
+    if (warp == 0) {
+      // prefix sums of the taps (K <= 65 < 96) and their total, one warp
+      long long run = 0;
+      for (int c0 = 0; c0 < TR_TAPS; c0 += 32) {
+        long long v = tt.taps[c0 + lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long u = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += u;
+        }
+        tt.pref[c0 + lane] = run + v;
+        run += __shfl_sync(0xffffffffu, v, 31);
+      }
+      if (lane == 0) tt.total = run;
+    }
+    fence_proxy_async_smem();  // B, written by ordinary stores, is read by MMA
+    tr_bar<3, TR_THREADS - 32>();
+  }
+  const uint32_t tb = bars.tbase;
+  volatile int* abort = &bars.abort;
+  const uint32_t lim = p.wait_limit;
+  const int my_n = (int64_t)blockIdx.x < p.ntiles
+                       ? (int)((p.ntiles - 1 - blockIdx.x) / gridDim.x + 1)
+                       : 0;
+  auto tile_n0 = [&](int i) {
+    return ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * TR_TILE;
+  };
+  // The window [n0 - H, n0 + 4096) of a tile: its samples inside [0, N)
+  // arrive by one bulk copy (16-byte aligned rows), all but a ragged tail of
+  // fewer than 16 bytes; window positions [blo, bhi) come from shared
+  // memory, the rest from global memory (the tail) or as zero.
+  constexpr int V = 16 / (int)sizeof(W);
+  auto bulk_range = [&](int64_t n0, int& blo, int& bhi) {
+    const int64_t lo = lmax(0, n0 - H), hi = lmin(p.N, n0 + TR_TILE);
+    blo = (int)(lo - (n0 - H));
+    bhi = blo + (p.vec != 0 ? (int)((hi - lo) / V * V) : 0);
+  };
+  if (warp == TR_WLOAD) {
+    // ---- loader (one lane) ---------------------------------------------
+    // bit s of pending: the last phase of slot s was a bulk copy, of phase
+    // parity bit s of last_ph (a later plain arrival makes it settled)
+    uint32_t pending = 0;
+    uint32_t last_ph = 0;
+    if (lane == 0 && p.stall_role != 1) {
+      uint32_t rc = 0;
+#pragma unroll 1
+      for (int i = 0; i < my_n && !*abort; ++i) {
+        const int64_t n0 = tile_n0(i);
+        int blo, bhi;
+        bulk_range(n0, blo, bhi);
+#pragma unroll 1
+        for (int j = 0; j < nrows; ++j, ++rc) {
+          const int s = rc % NRAW;
+          const uint32_t ph = (rc / NRAW) & 1u;
+          if (!tr_wait(&bars.raw_empty[s], ph ^ 1u, abort, lim)) break;
+          if (bhi > blo) {
+            const int m = row_of(j);
+            const uint32_t bytes = (uint32_t)((bhi - blo) * sizeof(W));
+            mbar_arrive_expect_tx(&bars.raw_full[s], bytes);
+            bulk_copy_g2s(raw + s * TR_SMAX + blo,
+                          x + (int64_t)m * p.ldx + n0 - H + blo, bytes,
+                          &bars.raw_full[s]);
+            pending |= 1u << s;
+            last_ph = (last_ph & ~(1u << s)) | (ph << s);
+          } else {
+            // the slot's previous copy was consumed before it was released
+            pending &= ~(1u << s);
+            t5_arrive(&bars.raw_full[s]);
+          }
+        }
+      }
+      // drain: every bulk copy issued has landed before the block exits
+      for (int s = 0; s < NRAW; ++s)
+        if (pending & (1u << s)) {
+          for (uint32_t it = 0; it < (1u << 16); ++it)
+            if (tr_try_wait(&bars.raw_full[s], (last_ph >> s) & 1u, TR_POLL_NS)) break;
+        }
+    }
+    __syncwarp();
+  } else if (warp >= TR_WSTG && warp < TR_WLOAD) {
+    // ---- staging: raw row -> ND digit planes ---------------------------
+    const int ts = threadIdx.x - TR_WSTG * 32;
+    const uint32_t bias_lo = (uint32_t)(unsigned long long)p.bias;
+    // pair pi (samples 2 pi, 2 pi + 1 of the window [n0 - H, n0 + 4096)) is
+    // chunk pi / 4 at bytes 4 (pi % 4); thread ts takes pi = ts + 192 k,
+    // whose slot advances by 12 rows (192 bytes) per step
+    const uint32_t doff = ((ts >> 2) & 3) * TR_LBO + (ts >> 4) * 16 + (ts & 3) * 4;
+    const int npairs = S / 2;
+    const int S_ = S;
+    uint32_t rc = 0;
+    bool ok = true;
+#pragma unroll 1
+    for (int i = 0; i < my_n && ok; ++i) {
+      const int64_t n0 = tile_n0(i);
+      int blo, bhi;
+      bulk_range(n0, blo, bhi);
+      const bool inner = blo == 0 && bhi == S_;
+#pragma unroll 1
+      for (int j = 0; j < nrows; ++j, ++rc) {
+        const int s = rc % NRAW, ps = rc % TR_NRS;
+        const uint32_t ph = (rc / NRAW) & 1u, pph = (rc / TR_NRS) & 1u;
+        bool got = true;
+        if (ts == 0)
+          got = tr_wait(&bars.raw_full[s], ph, abort, lim) &&
+                tr_wait(&bars.rs_empty[ps], pph ^ 1u, abort, lim);
+        if (!tr_vote<2, TR_NSTG>(got)) {
+          ok = false;
+          break;
+        }
+        const int m = row_of(j);
+        unsigned char* dst = planes + (size_t)ps * ND * TR_PLANE + doff;
+        auto put = [&](uint32_t a, uint32_t b) {
+          *reinterpret_cast<uint32_t*>(dst) = tr_digit_pair<0>(a, b);
+          if constexpr (ND > 1)
+            *reinterpret_cast<uint32_t*>(dst + TR_PLANE) = tr_digit_pair<1>(a, b);
+          if constexpr (ND > 2)
+            *reinterpret_cast<uint32_t*>(dst + 2 * TR_PLANE) = tr_digit_pair<2>(a, b);
+          if constexpr (ND > 3)
+            *reinterpret_cast<uint32_t*>(dst + 3 * TR_PLANE) = tr_digit_pair<3>(a, b);
+          dst += TR_NSTG;
+        };
+        const W* rs = raw + s * TR_SMAX + 2 * ts;
+        auto pair_smem = [&]() {
+          if constexpr (sizeof(W) == 8) {
+            const longlong2 v = *reinterpret_cast<const longlong2*>(rs);
+            put((uint32_t)v.x - bias_lo, (uint32_t)v.y - bias_lo);
+          } else {
+            const int2 v = *reinterpret_cast<const int2*>(rs);
+            put((uint32_t)v.x - bias_lo, (uint32_t)v.y - bias_lo);
+          }
+        };
+        if (inner) {
+#pragma unroll 4
+          for (int pi = ts; pi < npairs; pi += TR_NSTG, rs += 2 * TR_NSTG) pair_smem();
+        } else {
+          // a pair lies wholly inside or outside [blo, bhi) (both even)
+          const W* grow = x + (int64_t)m * p.ldx;
+#pragma unroll 2
+          for (int pi = ts; pi < npairs; pi += TR_NSTG, rs += 2 * TR_NSTG) {
+            if (2 * pi >= blo && 2 * pi < bhi) {
+              pair_smem();
+            } else {
+              const int64_t gi = n0 - H + 2 * pi;
+              const uint32_t a =
+                  (gi >= 0 && gi < p.N) ? (uint32_t)grow[gi] - bias_lo : 0x80808080u;
+              const uint32_t b = (gi + 1 >= 0 && gi + 1 < p.N)
+                                     ? (uint32_t)grow[gi + 1] - bias_lo
+                                     : 0x80808080u;
+              put(a, b);
+            }
+          }
+        }
+        fence_proxy_async_smem();  // the planes are read by the tensor cores
+        __syncwarp();
+        if (lane == 0) {
+          t5_arrive(&bars.raw_empty[s]);
+          t5_arrive(&bars.rs_full[ps]);
+        }
+      }
+    }
+  } else if (warp == TR_WMMA) {
+    // ---- MMA issue (one lane) ---------------------------------------------
+    if (lane == 0 && p.stall_role != 2) {
+      const uint64_t bd0 = t5_sdesc(smem_addr(bmat), 128, 256);
+      const uint32_t b_hi = (uint32_t)(bd0 >> 32), b_lo = (uint32_t)bd0;
+      const uint64_t ad0 = t5_sdesc(smem_addr(planes), TR_LBO, 128);
+      const uint32_t a_hi = (uint32_t)(ad0 >> 32), a_lo0 = (uint32_t)ad0;
+      const uint32_t id64 = t5_idesc(128, TR_NB);
+      const uint32_t idw = t5_idesc(128, tcols);
+      constexpr uint32_t SLOT16 = ND * TR_PLANE / 16;  // plane-set stride >> 4
+      uint32_t rc = 0, sc = 0;
+      bool ok = true;
+#pragma unroll 1
+      for (int i = 0; i < my_n && ok; ++i) {
+#pragma unroll 1
+        for (int q = 0; q < nstreams; ++q, ++sc) {
+          const uint32_t jo = rc + (PROT ? q + 1 : q), jn = rc + q;
+          const int po = jo % TR_NRS, pn = jn % TR_NRS;
+          const int ts = (int)(sc % (uint32_t)tslots);
+          if (!tr_wait(&bars.rs_full[po], (jo / TR_NRS) & 1u, abort, lim) ||
+              (PROT && !tr_wait(&bars.rs_full[pn], (jn / TR_NRS) & 1u, abort, lim)) ||
+              !tr_wait(&bars.acc_empty[ts], ((sc / tslots) & 1u) ^ 1u, abort, lim)) {
+            ok = false;
+            break;
+          }
+          t5_fence_after();
+          const uint32_t dcol = tb + (uint32_t)(ts * tcols);
+          const uint32_t pao = a_lo0 + (uint32_t)po * SLOT16;
+          const uint32_t pan = a_lo0 + (uint32_t)pn * SLOT16;
+          const uint32_t dn = dcol + 32u * (Q > 0 ? Q : NLEV);
+          switch (KS) {
+#define TR_ISSUE(K_)                                                      \
+  case K_:                                                                \
+    tr_issue_set<ND, K_, true>(dcol, pao, a_hi, b_lo, b_hi, idw, id64);   \
+    if (PROT) tr_issue_set<ND, K_, false>(dn, pan, a_hi, b_lo, b_hi, idw, id64); \
+    break;
+            TR_ISSUE(2)
+            TR_ISSUE(3)
+            TR_ISSUE(4)
+            TR_ISSUE(5)
+            default:
+            TR_ISSUE(6)
+#undef TR_ISSUE
+          }
+          t5_commit(&bars.acc_full[ts]);
+          if (PROT) {
+            t5_commit(&bars.rs_empty[pn]);
+            if (q == nstreams - 1) t5_commit(&bars.rs_empty[po]);
+          } else {
+            t5_commit(&bars.rs_empty[po]);
+          }
+        }
+        rc += (uint32_t)nrows;
+      }
+      // drain: every product issued has completed before the block exits
+      t5_commit(&bars.drain);
+      for (uint32_t it = 0; it < (1u << 16); ++it)
+        if (tr_try_wait(&bars.drain, 0, TR_POLL_NS)) break;
+    }
+    __syncwarp();
+  } else if (warp < 16) {
+    // ---- epilogue ----------------------------------------------------------
+    const int qd = warp & 3, og = warp >> 2;
+    const int a = 32 * qd + lane;                 // row of the tile
+    const int pos0 = TR_P * a + 8 * og;           // first local output
+    const uint32_t tl = tb + ((uint32_t)(32 * qd) << 16) + 8u * og;
+    const int l = p.l;
+    const unsigned long long corr_c = p.corr_mul * (unsigned long long)tt.total;
+    uint32_t sc = 0;
+    // delta (PROT) or y of one stream slot: 8 outputs of this thread
+    auto read_slot = [&](int ts, int64_t nb, bool edge, W (&out)[8]) {
+      const uint32_t base = tl + (uint32_t)(ts * tcols);
+      // own levels (all levels of the merged form)
+      constexpr int NL0 = (PROT && Q > 0) ? NLM : NLEV;
+      uint32_t u[NL0][8];
+#pragma unroll
+      for (int L = 0; L < NL0; ++L) tr_ld8(base + 32u * L, u[L]);
+      t5_wait_ld();
+      W own[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        uint32_t c[NL0];
+#pragma unroll
+        for (int L = 0; L < NL0; ++L) c[L] = tr_mag(u[L][e]);
+        if constexpr (sizeof(W) == 8)
+          own[e] = (W)tr_levels64<NL0 - 1>(c);
+        else
+          own[e] = (W)tr_levels32<NL0 - 1>(c);
+      }
+      if constexpr (PROT && Q == 0) {
+#pragma unroll
+        for (int L = 0; L < NLEV; ++L) tr_ld8(base + 32u * (NLEV + L), u[L]);
+        t5_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          uint32_t c[NLEV];
+#pragma unroll
+          for (int L = 0; L < NLEV; ++L) c[L] = tr_mag(u[L][e]);
+          if constexpr (sizeof(W) == 8)
+            own[e] = wadd<W>(own[e], shl<W>((W)tr_levels64<ND>(c), l));
+          else
+            own[e] = wadd<W>(own[e], shl<W>((W)tr_levels32<ND>(c), l));
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const unsigned long long corr =
+            edge ? shift_correction((long long)p.corr_mul, tt.pref, nb + e, p.N, p.K)
+                 : corr_c;
+        out[e] = wadd<W>(own[e], (W)corr);
+      }
+    };
+    // Output row m of the tile at n0: every epilogue thread parks its 8
+    // outputs in the output tile (16-byte chunks, chunk c of block b at
+    // c ^ (b % 8), so that lanes 256 bytes apart fall in distinct banks),
+    // then the 512 threads store the row segment with coalesced 16-byte
+    // stores (word stores for rows that are not 16-byte aligned).
+    constexpr int CPB = TR_P * (int)sizeof(W) / 16;  // chunks per block
+    constexpr int CPT = 8 * (int)sizeof(W) / 16;     // chunks per thread
+    constexpr int VW = 16 / (int)sizeof(W);          // words per chunk
+    constexpr int NCH = TR_TILE / VW;                // chunks per row
+    auto emit_row = [&](int m, int64_t n0, const W (&v)[8]) {
+      const int c0 = pos0 / VW;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int c = c0 + k;
+        int4* dst = reinterpret_cast<int4*>(otile) + (c ^ ((c / CPB) & 7));
+        if constexpr (sizeof(W) == 8)
+          *reinterpret_cast<longlong2*>(dst) = make_longlong2(v[2 * k], v[2 * k + 1]);
+        else
+          *dst = make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      }
+      tr_bar<4, TR_EPI>();
+      W* grow = y + (int64_t)m * p.ldy + n0;
+      const bool al = (reinterpret_cast<uintptr_t>(grow) & 15) == 0;
+      const int64_t nvalid = p.Nout - n0;  // outputs of the row in this tile
+#pragma unroll
+      for (int c = threadIdx.x; c < NCH; c += TR_EPI) {
+        const int4 w4 = reinterpret_cast<const int4*>(otile)[c ^ ((c / CPB) & 7)];
+        const W* wv = reinterpret_cast<const W*>(&w4);
+        const int64_t j0 = (int64_t)c * VW;
+        if (al && j0 + VW <= nvalid) {
+          *reinterpret_cast<int4*>(grow + j0) = w4;
+        } else {
+#pragma unroll
+          for (int e = 0; e < VW; ++e)
+            if (j0 + e < nvalid) grow[j0 + e] = wv[e];
+        }
+      }
+      tr_bar<4, TR_EPI>();
+    };
+#pragma unroll 1
+    for (int i = 0; i < my_n; ++i) {
+      const int64_t n0 = tile_n0(i);
+      const int64_t nb = n0 + pos0;
+      const bool edge = n0 < (int64_t)p.K - 1 || n0 + TR_TILE > p.N;
+      bool ok = true;
+      if constexpr (PROT) {
+        W dl[MM - 1][8];
+#pragma unroll
+        for (int q = 0; q < MM; ++q) {
+          if (q == MM - 1 && skip) break;
+          const int ts = (int)(sc % (uint32_t)tslots);
+          const uint32_t ph = (sc / tslots) & 1u;
+          bool got = true;
+          if (threadIdx.x == 0) got = tr_wait(&bars.acc_full[ts], ph, abort, lim);
+          if (!tr_vote<1, TR_EPI>(got)) {
+            ok = false;
+            break;
+          }
+          t5_fence_after();
+          // position q holds stream r + 1 + q (skip) or r + q; the product
+          // of stream r + 1 + qq goes to dl[qq]; stream r's is dropped
+          if (skip)
+            read_slot(ts, nb, edge, dl[q < MM - 1 ? q : MM - 2]);
+          else if (q >= 1)
+            read_slot(ts, nb, edge, dl[q >= 1 ? q - 1 : 0]);
+          t5_fence_before();
+          __syncwarp();
+          if (lane == 0) t5_arrive(&bars.acc_empty[ts]);
+          ++sc;
+        }
+        if (!ok) break;
+        // recovery of all M outputs at these 8 positions (Eq. 16-19): the
+        // Horner sum of Eq. 16 gives d_{r-1} (Eq. 17), the chain
+        // d_{j-1} = (delta_j - d_j) >> l the others
+        W dcur[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          W t = dl[0][e];
+#pragma unroll
+          for (int q = 1; q < MM - 1; ++q)
+            t = (q & 1) ? wsub<W>(shl<W>(t, l), dl[q][e])
+                        : wadd<W>(shl<W>(t, l), dl[q][e]);
+          dcur[e] = sext_low<W>((MM & 1) ? wsub<W>((W)0, t) : t, (MM - 1) * l);
+        }
+#pragma unroll
+        for (int q = MM - 2; q >= 0; --q) {
+          const int m = r + 1 + q >= MM ? r + 1 + q - MM : r + 1 + q;
+          emit_row(m, n0, dcur);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) dcur[e] = wsub<W>(dl[q][e], dcur[e]) >> l;
+        }
+        emit_row(r, n0, dcur);
+      } else {
+#pragma unroll 1
+        for (int q = 0; q < nstreams; ++q) {
+          const int ts = (int)(sc % (uint32_t)tslots);
+          const uint32_t ph = (sc / tslots) & 1u;
+          bool got = true;
+          if (threadIdx.x == 0) got = tr_wait(&bars.acc_full[ts], ph, abort, lim);
+          if (!tr_vote<1, TR_EPI>(got)) {
+            ok = false;
+            break;
+          }
+          t5_fence_after();
+          W out[8];
+          read_slot(ts, nb, edge, out);
+          t5_fence_before();
+          __syncwarp();
+          if (lane == 0) t5_arrive(&bars.acc_empty[ts]);
+          ++sc;
+          emit_row(row_of(q), n0, out);
+        }
+        if (!ok) break;
+      }
+    }
+  }
+  // ---- teardown --------------------------------------------------------------
+  t5_fence_before();
+  __syncthreads();
+  if (warp == TR_WMMA) {
+    t5_fence_after();
+    t5_dealloc(tb, 512);
+  }
+}
+
+template <typename W, bool PROT, int MM, int ND, int Q>
+int tr_launch_one(const ConvArgs& a, cudaStream_t s) {
+  static std::once_flag once;
+  static int attr = NE_OK;
+  constexpr size_t smem = tr_smem_bytes<W, ND>();
+  std::call_once(once, [] {
+    auto k = tcr_conv_kernel<W, PROT, MM, ND, Q>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      attr = NE_ERR_CUDA;
+  });
+  if (attr != NE_OK) {
+    cudaGetLastError();
+    return attr;
+  }
+  const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)sm_count());
+  tcr_conv_kernel<W, PROT, MM, ND, Q><<<(unsigned)grid, TR_THREADS, smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? NE_OK : NE_ERR_CUDA;
+}
+
+template <typename W, bool PROT, int MM>
+int tr_launch_nd(const ConvArgs& a, cudaStream_t s) {
+  if constexpr (PROT && MM == 4) {
+    // l = 8 or 16 (M = 4 in 32- or 64-bit words): merged levels
+    if (a.mlev == 1)
+      return a.nd == 1 ? tr_launch_one<W, PROT, MM, 1, 1>(a, s)
+                       : tr_launch_one<W, PROT, MM, 2, 1>(a, s);
+    if (a.mlev == 2 && a.nd == 2) return tr_launch_one<W, PROT, MM, 2, 2>(a, s);
+  }
+  switch (a.nd) {
+    case 1: return tr_launch_one<W, PROT, MM, 1, 0>(a, s);
+    case 2: return tr_launch_one<W, PROT, MM, 2, 0>(a, s);
+    default: break;
+  }
+  if constexpr (!PROT) {
+    if (a.nd == 3) return tr_launch_one<W, PROT, MM, 3, 0>(a, s);
+    if (a.nd == 4) return tr_launch_one<W, PROT, MM, 4, 0>(a, s);
+  }
+  return NE_ERR_UNSUPPORTED;
+}
+
+template <typename W>
+int tr_launch(const ConvArgs& a, bool prot, cudaStream_t s) {
+  if (!prot) return tr_launch_nd<W, false, 0>(a, s);
+  switch (a.M) {
+    case 3: return tr_launch_nd<W, true, 3>(a, s);
+    case 4: return tr_launch_nd<W, true, 4>(a, s);
+    case 5: return tr_launch_nd<W, true, 5>(a, s);
+    case 6: return tr_launch_nd<W, true, 6>(a, s);
+    default: return NE_ERR_UNSUPPORTED;
+  }
+}
+
+// Host reader of this translation unit's device error word.
+unsigned tr_tu_device_error(bool clear) {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_ne_device_error, sizeof(v)) != cudaSuccess)
+    return 0x80000000u;
+  if (clear && v) {
+    const unsigned z = 0;
+    cudaMemcpyToSymbol(g_ne_device_error, &z, sizeof(z));
+  }
+  return v;
+}
+
+}  // namespace
+}  // namespace ne

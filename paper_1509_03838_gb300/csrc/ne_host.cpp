@@ -8,6 +8,7 @@
 
 #include "../../include/ne.h"
 #include "ne_common.cuh"
+#include "ne_conv_args.cuh"
 
 namespace ne {
 
@@ -52,7 +53,9 @@ int ne_get_device_error(uint32_t* out, int clear) {
   if (!out) return NE_ERR_INVALID_ARG;
   if (cudaDeviceSynchronize() != cudaSuccess) return NE_ERR_CUDA;
   const unsigned v = ne::conv_tu_device_error(clear != 0) |
-                     ne::batch_tu_device_error(clear != 0);
+                     ne::batch_tu_device_error(clear != 0) |
+                     ne::tcr_w32_device_error(clear != 0) |
+                     ne::tcr_w64_device_error(clear != 0);
   if (v & 0x80000000u) return NE_ERR_CUDA;
   *out = v;
   return NE_OK;
