@@ -1,12 +1,14 @@
 """GPU parity of the tensor-core convolution (exact integer products from
-byte digits on fp16 mma.sync) against the CPU oracle, bit-exact: the plain
+byte digits, fp32 accumulation) against the CPU oracle, bit-exact: the plain
 convolution with declared ranges (ne_conv_range) and the protected
-convolution (the fused tcgen05 kernel for 3 <= M <= 4 with aligned rows,
-the fused mma.sync kernel for the rest up to M = 8, every tile size),
-every failure mode, operands at the ends of the 32-bit window, the largest
-taps, K from 1 to 65, ragged and unaligned rows; and the same cases on the
-two-pass form (NE_PROT_KERNEL=twopass), on the mma.sync kernels alone
-(NE_CONV_TC5=0) and on the multiply-add kernels (NE_CONV_TC=0)."""
+convolution, every failure mode, operands at the ends of the 32-bit window,
+the largest taps, K from 1 to 65, ragged and unaligned rows.  By default
+these cases run where the library sends them (the raw-plane tcgen05 kernel
+for most, ne_conv_tcr.cuh; the entangled-digit kernels for M = 7, 8); the
+child runs repeat them on the entangled-digit kernels (NE_CONV_TCR=0: the
+tcgen05 fused kernel and mma.sync), on mma.sync alone (NE_CONV_TC5=0), on
+the two-pass form (NE_PROT_KERNEL=twopass) and on the multiply-add kernels
+(NE_CONV_TC=0)."""
 import numpy as np
 import pytest
 
@@ -210,18 +212,26 @@ def _child_run(env_extra, select):
 def test_same_cases_on_the_two_pass_form(ne):
     """NE_PROT_KERNEL=twopass (read once per process, hence the child run):
     the protected cases through the tensor-core products and a separate
-    recovery pass instead of the fused kernel."""
+    recovery pass instead of a fused kernel."""
     _child_run({"NE_PROT_KERNEL": "twopass"}, "protected_tc")
 
 
+def test_same_cases_on_the_entangled_digit_kernels(ne):
+    """NE_CONV_TCR=0: every case above through the earlier tensor-core
+    kernels, whose digits are those of the entangled words (the tcgen05
+    fused kernel for 3 <= M <= 4 with aligned rows, mma.sync otherwise)."""
+    _child_run({"NE_CONV_TCR": "0"},
+               "not multiply_add and not two_pass and not mma_sync and not entangled_digit")
+
+
 def test_same_cases_on_the_mma_sync_kernels(ne):
-    """NE_CONV_TC5=0: the protected cases through the mma.sync kernels where
-    the tcgen05 one would run (3 <= M <= 4, aligned rows)."""
-    _child_run({"NE_CONV_TC5": "0"}, "protected_tc")
+    """NE_CONV_TCR=0 NE_CONV_TC5=0: the protected cases through the mma.sync
+    kernels where a tcgen05 one would run."""
+    _child_run({"NE_CONV_TCR": "0", "NE_CONV_TC5": "0"}, "protected_tc")
 
 
 def test_same_cases_on_the_multiply_add_kernels(ne):
     """NE_CONV_TC=0 (read once per process, hence the child run): every case
     above through the multiply-add kernels."""
     _child_run({"NE_CONV_TC": "0"},
-               "not multiply_add and not two_pass and not mma_sync")
+               "not multiply_add and not two_pass and not mma_sync and not entangled_digit")

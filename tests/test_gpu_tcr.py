@@ -1,0 +1,274 @@
+"""GPU parity of the raw-plane tcgen05 convolution (byte-digit planes of the
+raw rows, 32 outputs per MMA row) against the CPU oracle, bit-exact.
+
+Covered: the plain convolution (ne_conv_range) for 1 to 4 byte digits, 32-
+and 64-bit words, any live mask; the fused protected convolution
+(ne_protected_conv) for M = 3..6, one and two digits, the neighbour's levels
+apart and merged (M = 4: l = 8 and l = 16), every failure mode; ragged last
+tiles, inputs shorter than the history, rows that are not 16-byte aligned
+(staged from global memory), odd output strides, extreme operands and taps;
+and, at the benchmark's full size (M = 4, N = 2^22, K = 64), every output of
+every failure mode, with several tiles per block so that every ring wraps.
+The oracle side runs in independent output pieces on all host cores
+(tests/oracle_par.py)."""
+import numpy as np
+import pytest
+
+from oracle_par import conv_par
+from paper_1509_03838_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TILE = 4096  # outputs per stream per tile
+
+
+@pytest.fixture(scope="module")
+def ne():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_03838_gb300 import build, ne as nemod
+    build.build()
+    return nemod
+
+
+def dt(w):
+    return torch.int32 if w == 32 else torch.int64
+
+
+def dev(a, w, ld=None):
+    """[rows, n] int64 array -> CUDA tensor view [rows, n] of a [rows, ld]
+    buffer (ld > n gives rows that are not contiguous with each other)."""
+    a = np.asarray(a, dtype=np.int64)
+    rows, n = a.shape
+    ld = n if ld is None else ld
+    buf = torch.zeros((rows, ld), dtype=dt(w))
+    buf[:, :n] = torch.from_numpy(a.astype(np.int32 if w == 32 else np.int64))
+    return buf.cuda()[:, :n]
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.int64)
+
+
+def modes(ne, M):
+    return [(ne.NE_FAIL_NONE, -1)] + [(fm, r) for fm in (ne.NE_FAIL_SKIP,
+                                                         ne.NE_FAIL_DROP)
+                                      for r in range(M)]
+
+
+PLAIN = [
+    # w, M, N, K, [lo, hi], max|g|, row padding of x (odd: unaligned rows)
+    (64, 2, 3 * TILE + 11, 64, (-2**15, 2**15 - 1), 2**15, 0),    # 2 digits
+    (64, 3, 2 * TILE + 5, 65, (-2**31, 2**31 - 1), 2**15, 0),     # 4 digits
+    (64, 1, 5000, 33, (2**40, 2**40 + 2**24 - 1), 2**15, 0),      # 3 digits, shifted
+    (64, 2, 7000, 16, (-100, 155), 1000, 0),                      # 1 digit
+    (32, 3, 9000, 48, (-2**23, 2**23 - 1), 2**15, 1),             # unaligned rows
+    (32, 1, 5000, 16, (-100, 100), 1000, 0),
+    (64, 4, 30, 64, (-2**15, 2**15 - 1), 2**15, 0),               # N < K
+    (64, 5, 1, 1, (-7, 7), 100, 0),                               # N = 1, K = 1
+    (64, 2, TILE - 63, 64, (-2**15, 2**15 - 1), 2**15, 3),        # one tile, odd ld
+    (32, 4, 300 * TILE + 17, 24, (-2**10, 2**10), 2**15, 0),      # ~8 tiles per block
+]
+
+
+@pytest.mark.parametrize("case", PLAIN)
+def test_tcr_plain_matches_oracle(ne, orc, case):
+    w, M, N, K, (lo, hi), gmax, pad = case
+    gen = synth.rng(N * 7 + K + M)
+    x = synth.uniform_int(gen, (M, N), lo, hi + 1)
+    x[:, 0] = hi
+    x[:, -1] = lo
+    g = synth.uniform_int(gen, (K,), -gmax + 1, gmax)
+    g[0] = gmax
+    expect = conv_par(orc, x, g, w, strict=False)
+    y = torch.full((M, N + K - 1), 5, dtype=dt(w), device="cuda")
+    ne.ne_conv(dev(x, w, ld=N + pad), torch.from_numpy(g.astype(np.int32)).cuda(),
+               y, x_range=(lo, hi), max_abs_g=gmax)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), expect)
+
+
+def test_tcr_plain_live_mask(ne, orc):
+    w, M, N, K = 64, 5, 3 * TILE + 100, 64
+    gen = synth.rng(91)
+    x = synth.uniform_int(gen, (M, N), -(1 << 15), 1 << 15)
+    g = synth.uniform_int(gen, (K,), -(1 << 15) + 1, 1 << 15)
+    expect = conv_par(orc, x, g, w)
+    y = torch.full((M, N + K - 1), -3, dtype=torch.int64, device="cuda")
+    live = 0b10110
+    ne.ne_conv(dev(x, w), torch.from_numpy(g.astype(np.int32)).cuda(), y,
+               x_range=(-(1 << 15), (1 << 15) - 1), max_abs_g=32767,
+               live_mask=live)
+    torch.cuda.synchronize()
+    got = host(y)
+    for m in range(M):
+        if (live >> m) & 1:
+            assert np.array_equal(got[m], expect[m])
+        else:
+            assert (got[m] == -3).all()
+
+
+PROT = [
+    # w, M, N, K, data bits, tap bits, pad c, pad d   (levels: apart / merged)
+    (64, 4, 3 * TILE + 7, 64, 15, 15, 0, 0),     # l = 16: merged at level 2
+    (64, 4, 5 * TILE, 65, 15, 14, 0, 1),         # K = 65, odd ld of d
+    (64, 3, 2 * TILE + 100, 65, 15, 15, 2, 1),   # l = 22, apart
+    (64, 5, 10000, 48, 12, 15, 0, 0),            # l = 13
+    (64, 6, 6000, 64, 10, 12, 0, 3),             # l = 11
+    (64, 4, 40, 17, 15, 15, 0, 0),               # N shorter than the history
+    (64, 3, 1, 1, 7, 7, 0, 0),                   # N = 1, K = 1
+    (64, 4, 2 * TILE + 9, 64, 7, 15, 1, 0),      # one digit; unaligned rows
+    (32, 3, 4096, 16, 7, 7, 0, 0),               # l = 11
+    (32, 4, 3 * TILE + 1, 64, 7, 7, 0, 1),       # l = 8, one digit: merged at 1
+    (32, 4, 2 * TILE + 3, 33, 8, 7, 0, 0),       # l = 8, two digits: merged at 1
+    (32, 5, 9000, 20, 5, 6, 3, 0),               # l = 7
+    (32, 6, 7000, 9, 4, 5, 0, 0),                # l = 6
+]
+
+
+@pytest.mark.parametrize("case", PROT)
+def test_tcr_protected_every_failure(ne, orc, case):
+    w, M, N, K, bc, bg, padc, padd = case
+    p = ne.ne_params(M, w)
+    gen = synth.rng(N + 13 * K + M + w)
+    c = synth.uniform_int(gen, (M, N), -(1 << bc), 1 << bc)
+    c[:, 0] = (1 << bc) - 1
+    c[:, -1] = -(1 << bc)
+    g = synth.uniform_int(gen, (K,), -(1 << bg) + 1, 1 << bg)
+    assert K * (1 << bc) * ((1 << bg) - 1) <= p.d_max_exact
+    plain = conv_par(orc, c, g, w)
+    Nout = N + K - 1
+    cd = dev(c, w, ld=N + padc)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    for fm, r in modes(ne, M):
+        dfull = torch.full((M, Nout + padd), 77, dtype=dt(w), device="cuda")
+        d = dfull[:, :Nout]
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(1 << bc), (1 << bc) - 1),
+                             max_abs_g=(1 << bg) - 1, failed=r, fail_mode=fm)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), plain), (fm, r)
+        if padd:  # nothing written past the end of a row
+            assert (dfull[:, Nout:] == 77).all(), (fm, r)
+
+
+def test_tcr_protected_full_size_every_output(ne, orc):
+    """The benchmark job (M = 4, N = 2^22, K = 64, 16-bit data and taps,
+    64-bit words; 1025 tiles, so every block takes 6 or 7 tiles and every
+    ring wraps): every output of the fused launch equals the oracle's
+    convolution of the raw inputs, without a failure and for every stream
+    failed in turn (skipped and dropped) (Eq. 9, Eq. 16-19; Sec. III-B:
+    any single failure is recoverable)."""
+    j = synth.large_job(seed=2)
+    M, N, K = j.M, j.N, j.K
+    p = ne.ne_params(M, 64)
+    plain = conv_par(orc, j.c, j.g, 64)
+    cd = dev(j.c, 64)
+    gd = torch.from_numpy(j.g.astype(np.int32)).cuda()
+    ws = torch.empty(ne.ne_protected_conv_ws_bytes(M, N, K), dtype=torch.uint8,
+                     device="cuda")
+    d = torch.empty((M, N + K - 1), dtype=torch.int64, device="cuda")
+    for fm, r in modes(ne, M):
+        d.fill_(-1)
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=j.c_range,
+                             max_abs_g=j.bound_g, failed=r, fail_mode=fm, ws=ws)
+        torch.cuda.synchronize()
+        got = host(d)
+        assert np.array_equal(got, plain), (fm, r, int(np.count_nonzero(got != plain)))
+
+
+def test_tcr_w32_several_tiles_per_block_odd_ld(ne, orc):
+    """32-bit words, M = 3, N = 3 * 2^20 + 5 (769 tiles: 5 or 6 per block),
+    an odd leading dimension for d (rows alternately 4, 8 and 12 bytes past
+    a 16-byte boundary): every output, every failure mode."""
+    M, N, K, b = 3, 3 * (1 << 20) + 5, 16, 7
+    p = ne.ne_params(M, 32)
+    gen = synth.rng(777)
+    c = synth.uniform_int(gen, (M, N), -(1 << b), 1 << b)
+    g = synth.uniform_int(gen, (K,), -(1 << b), 1 << b)
+    assert K * (1 << b) * (1 << b) <= p.d_max_exact
+    plain = conv_par(orc, c, g, 32)
+    Nout = N + K - 1
+    cd = dev(c, 32)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    dfull = torch.empty((M, Nout + 3), dtype=torch.int32, device="cuda")
+    d = dfull[:, :Nout]
+    for fm, r in modes(ne, M):
+        dfull.fill_(11)
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(1 << b), (1 << b) - 1),
+                             max_abs_g=1 << b, failed=r, fail_mode=fm)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), plain), (fm, r)
+        assert (dfull[:, Nout:] == 11).all(), (fm, r)
+
+
+# Operands at the byte extremes (every byte 0x00 or 0xFF after the range
+# shift, the top byte of a 32-bit word at 0x80/0x7F) and taps whose balanced
+# digits reach -128 and 128 together (-2^15, 2^15 - 1, 0x7F80, -0x7F80):
+# the level sums of the digit scheme reach their largest magnitudes.
+EXTREME_X = [0x00FFFFFF, 0x7FFFFFFF, -(2**31), -1, 0, 0x00FF00FF, 0x7F00FF00,
+             -0x00010000, 0xFFFF, -0x8000]
+EXTREME_G = [-(2**15), 2**15 - 1, 0x7F80, -0x7F80, 0x80, -0x80, 0xFF, 1]
+
+
+def _extreme_streams(M, N, vals, seed):
+    gen = synth.rng(seed)
+    idx = gen.integers(0, len(vals), size=(M, N))
+    return np.asarray(vals, dtype=np.int64)[idx]
+
+
+def test_tcr_extreme_operands_plain(ne, orc):
+    w, M, N, K = 64, 3, 2 * TILE + 33, 65
+    x = _extreme_streams(M, N, EXTREME_X, 5)
+    gen = synth.rng(6)
+    g = np.asarray(EXTREME_G, dtype=np.int64)[gen.integers(0, len(EXTREME_G), size=K)]
+    g[::2] = -(2**15)
+    expect = conv_par(orc, x, g, w, strict=False)
+    y = torch.full((M, N + K - 1), 1, dtype=torch.int64, device="cuda")
+    ne.ne_conv(dev(x, w), torch.from_numpy(g.astype(np.int32)).cuda(), y,
+               x_range=(-(2**31), 2**31 - 1), max_abs_g=2**15)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), expect)
+
+
+def test_tcr_extreme_operands_protected(ne, orc):
+    """16-bit data at both ends of [-2^15, 2^15) and extreme taps, K = 65
+    (the neighbour's levels merged at level 2, l = 16), every failure."""
+    w, M, N, K = 64, 4, 2 * TILE + 65, 65
+    p = ne.ne_params(M, w)
+    vals = [-(2**15), 2**15 - 1, -1, 0, 0xFF, -0x100, 0x7F00, -0x7F01]
+    c = _extreme_streams(M, N, vals, 8)
+    gen = synth.rng(9)
+    g = np.asarray(EXTREME_G, dtype=np.int64)[gen.integers(0, len(EXTREME_G), size=K)]
+    assert K * (2**15) * (2**15) <= p.d_max_exact
+    plain = conv_par(orc, c, g, w)
+    cd = dev(c, w)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    for fm, r in modes(ne, M):
+        d = torch.full((M, N + K - 1), 3, dtype=torch.int64, device="cuda")
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(2**15), 2**15 - 1),
+                             max_abs_g=2**15, failed=r, fail_mode=fm)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), plain), (fm, r)
+
+
+def _child_run(env_extra, select):
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ, **env_extra)
+    out = subprocess.run(
+        [sys.executable, "-m", "pytest", __file__, "-q", "-x", "-m", "gpu",
+         "-p", "no:cacheprovider", "-k", select],
+        env=env, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stdout[-3000:] + out.stderr[-2000:]
+    assert " passed" in out.stdout
+
+
+def test_extreme_operands_on_the_earlier_tensor_core_kernels(ne):
+    """NE_CONV_TCR=0 (read once per process, hence the child runs): the
+    extreme-operand cases through the entangled-digit kernels (tcgen05
+    fused kernel and mma.sync), and with NE_CONV_TC5=0 through mma.sync
+    alone."""
+    _child_run({"NE_CONV_TCR": "0"}, "extreme_operands_p")
+    _child_run({"NE_CONV_TCR": "0", "NE_CONV_TC5": "0"}, "extreme_operands_p")
