@@ -408,7 +408,8 @@ int ne_protected_outer(const void *c, int64_t ldc, int M, int64_t N,
                        int failed, int fail_mode, void *d, int64_t sd,
                        void *stream);
 
-/* Largest N + K - 1 that ne_protected_conv_noalloc accepts. */
+/* Largest N + K - 1 that ne_protected_conv_noalloc accepts outside the
+ * tensor-core window (jobs inside it need no arrival words). */
 #define NE_NOALLOC_MAX_NOUT 100663296LL /* 2^25 * 3 output samples */
 
 /*
@@ -421,18 +422,22 @@ int ne_protected_outer(const void *c, int64_t ldc, int M, int64_t N,
  * workspace: the per-tile arrival words live in a fixed array inside
  * libne.so's own device memory, sized for N + K - 1 <= NE_NOALLOC_MAX_NOUT
  * (512 KiB; every GPU that loads the library holds it until the process
- * exits).  Larger jobs return NE_ERR_NOMEM before any launch.
+ * exits).
+ *   - Jobs in the tensor-core window (see ne_protected_conv) run the same
+ *     tensor-core kernels as ne_protected_conv, never touch the array and
+ *     have no size limit beyond ne_protected_conv's.  Other jobs with
+ *     N + K - 1 > NE_NOALLOC_MAX_NOUT return NE_ERR_NOMEM before any launch.
  *   - No cudaMalloc, cudaFree or other allocating call is made.  The array
  *     keeps the last call's contents; each call that uses it clears the
  *     words it uses (an asynchronous memset on `stream`) before its launch.
- *   - Jobs in the tensor-core window (see ne_protected_conv) run the same
- *     tensor-core kernels as ne_protected_conv and never touch the array.
- *   - All other calls share the one array per device: calls whose launches
- *     can overlap on the GPU (different streams, or different host threads)
- *     race and give wrong results.  Order them on one stream.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture.
+ *   - All calls that use the array share it, one per device: calls whose
+ *     launches can overlap on the GPU (different streams, or different host
+ *     threads) race and give wrong results.  Order them on one stream.
+ *   - The first call on each device that uses the array looks up its device
+ *     address (cudaGetSymbolAddress, with that device current) and caches it
+ *     for the rest of the process; make that first call before any stream
+ *     capture, and do not reset the device (cudaDeviceReset) afterwards: a
+ *     new context may place the array elsewhere.
  */
 int ne_protected_conv_noalloc(const void *c, int64_t ldc, int M, int64_t N,
                               const int32_t *g, int K, int w, int l,

@@ -1312,8 +1312,6 @@ extern "C" int ne_protected_conv_noalloc(const void* c, int64_t ldc, int M,
   if (N == 0) return NE_OK;
   const int64_t Nout = N + K - 1;
   if (!c || !g || !d || ldd < Nout) return NE_ERR_INVALID_ARG;
-  // the fixed array covers NE_NOALLOC_MAX_NOUT output samples per stream
-  if (Nout > NE_NOALLOC_MAX_NOUT) return NE_ERR_NOMEM;
   const int wb = w / 8;
   if (overlaps(c, rows_bytes(M, ldc, N, wb), d, rows_bytes(M, ldd, Nout, wb)))
     return NE_ERR_INVALID_ARG;
@@ -1342,6 +1340,8 @@ extern "C" int ne_protected_conv_noalloc(const void* c, int64_t ldc, int M,
   // the tensor-core forms need no arrival words
   const int tc = protected_tc(a, mode, max_abs_g, w, vec, s, c_min, c_max);
   if (tc != kNotTaken) return tc;
+  // the fixed array covers NE_NOALLOC_MAX_NOUT output samples per stream
+  if (Nout > NE_NOALLOC_MAX_NOUT) return NE_ERR_NOMEM;
   uint32_t* ws = nullptr;
   const int st = noalloc_arrivals(&ws);
   if (st != NE_OK) return st;
