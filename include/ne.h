@@ -86,7 +86,8 @@ int ne_version(void);
  * bounded wait (for one of its own bulk copies, or for its tensor-core
  * products or another warp's stage) expired; the kernel then stopped early
  * and its outputs are incomplete.  clear != 0 resets it.
- * Blocks the host.  Returns NE_OK, NE_ERR_INVALID_ARG or NE_ERR_CUDA.
+ * Blocks the host.  Returns NE_ERR_TIMEOUT when bit 0 is set (with *out
+ * filled), else NE_OK, NE_ERR_INVALID_ARG or NE_ERR_CUDA.
  */
 int ne_get_device_error(uint32_t *out, int clear);
 
@@ -206,6 +207,18 @@ int ne_dot(const void *x, int64_t ldx, int M, int64_t N, const void *g,
  */
 int ne_recover(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
                int l, int failed, void *d, int64_t ld_out, void *stream);
+
+/*
+ * ne_recover_mask -- ne_recover with the failed streams given as a mask
+ * (bit m = stream m fail-stopped).  Only single failures are recoverable
+ * (Sec. I): with no bit set this is ne_extract, with one bit ne_recover of
+ * that stream, and with two or more bits it returns NE_ERR_UNRECOVERABLE on
+ * the host before any launch (d is not written).  Bits at or above M are
+ * NE_ERR_INVALID_ARG.  Other arguments, layouts and errors as ne_recover.
+ */
+int ne_recover_mask(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
+                    int l, uint32_t failed_mask, void *d, int64_t ld_out,
+                    void *stream);
 
 /*
  * ne_extract -- extraction with all M entangled outputs present.  The
@@ -407,6 +420,70 @@ int ne_protected_outer(const void *c, int64_t ldc, int M, int64_t N,
                        int64_t c_min, int64_t c_max, int64_t max_abs_g,
                        int failed, int fail_mode, void *d, int64_t sd,
                        void *stream);
+
+/* ------------------------------------------------------------------------
+ * Fail-stop detection by deadline (Sec. I: a core that is unresponsive or
+ * misses a predetermined deadline has failed; Sec. V: the outputs are
+ * disentangled as soon as any M - 1 entangled outputs are available).  Each
+ * entangled stream's product runs as its own unit of work ("core") on its
+ * own CUDA stream; the host declares late every core whose completion event
+ * has not fired by the deadline.
+ * ------------------------------------------------------------------------ */
+typedef struct ne_fs ne_fs;
+
+/* Create the per-core CUDA streams and completion events for up to max_M
+ * cores (3 <= max_M <= 32); ne_fs_destroy releases them.  Neither allocates
+ * device memory. */
+int ne_fs_create(ne_fs **out, int max_M);
+int ne_fs_destroy(ne_fs *fs);
+
+/* Block the host until every core launched on fs has finished, late ones
+ * included.  eps and delta of a call must stay valid until then. */
+int ne_fs_sync(ne_fs *fs);
+
+/*
+ * ne_fs_decide -- the decision after a deadline, from the mask of cores that
+ * completed in time (bit m = core m; bits >= M ignored): *failed = -1 and
+ * NE_OK when all M completed (extraction), *failed = r and NE_OK when only
+ * core r is late (recovery without r), NE_ERR_UNRECOVERABLE when two or
+ * more are late (only single failures are recoverable).  Host-only.
+ */
+int ne_fs_decide(int M, uint32_t done_mask, int *failed);
+
+/*
+ * ne_fs_protected_conv -- the protected convolution with fail-stop
+ * detection by deadline:
+ *   1. eps = E{c} (ne_entangle, Eq. 15) into eps (M rows, lde) on `stream`;
+ *   2. core m, on its own CUDA stream after step 1, computes the entangled
+ *      product delta_m = eps_m * g (Eq. 9) into row m of delta (ldd >=
+ *      N + K - 1), on the tensor cores where ne_conv_range would;
+ *   3. the host polls the cores' completion events until all completed or
+ *      deadline_ms (wall clock since the call began) passed;
+ *   4. the cores that had not completed are late (fail-stopped); their mask
+ *      goes to *late_mask (if non-NULL) and ne_fs_decide decides: none late,
+ *      d = the extraction of delta; one late (r), d = the recovery of all M
+ *      outputs without row r (Eq. 16-19), enqueued on `stream` after the
+ *      other cores' events; two or more, NE_ERR_UNRECOVERABLE and d is not
+ *      written.  A late core keeps running and writes only row r of delta,
+ *      which the recovery never reads.
+ *   c, g, ranges and l as ne_protected_conv (same NE_ERR_RANGE rule); eps,
+ *   delta and d must not overlap each other or c.
+ *   inject_late: fault injection on the host: a mask of cores whose launch
+ *      is held back until after the deadline (cores that miss it); 0 for
+ *      none.
+ * Blocks the host until every core completed or the deadline passed (with
+ * injected cores, always the full deadline).  Late cores go on running after
+ * the call returns: keep eps and delta valid until ne_fs_sync.  Calls on one
+ * ne_fs must not overlap.  Returns NE_OK, NE_ERR_UNRECOVERABLE, NE_ERR_INVALID_ARG,
+ * NE_ERR_RANGE or NE_ERR_CUDA.
+ */
+int ne_fs_protected_conv(ne_fs *fs, const void *c, int64_t ldc, int M,
+                         int64_t N, const int32_t *g, int K, int w, int l,
+                         int64_t c_min, int64_t c_max, int64_t max_abs_g,
+                         void *eps, int64_t lde, void *delta, int64_t ldd,
+                         void *d, int64_t ld_out, double deadline_ms,
+                         uint32_t inject_late, uint32_t *late_mask,
+                         void *stream);
 
 /* Largest N + K - 1 that ne_protected_conv_noalloc accepts outside the
  * tensor-core window (jobs inside it need no arrival words). */

@@ -20,6 +20,7 @@ LIB = os.path.join(HERE, "libne.so")
 
 SOURCES = ["ne_host.cpp", "ne_stream_ops.cu", "ne_conv.cu", "ne_conv_tcr_w32.cu",
            "ne_conv_tcr_w64.cu", "ne_batch.cu", "ne_gemm.cu", "ne_pipe.cu",
+           "ne_failstop.cu",
            "ne_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",

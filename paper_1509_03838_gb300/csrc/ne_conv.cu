@@ -25,6 +25,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "../../include/ne_debug.h"
 #include "ne_conv_args.cuh"
 #include "ne_conv_core.cuh"
 #include "ne_tc5.cuh"
@@ -899,7 +900,7 @@ inline int tcr_digits(__int128 lo, __int128 hi) {
 }
 
 // Fault injection for tests (ne_debug_set_fault): the next launches of the
-// raw-plane kernels get a short wait limit and a role that never runs.
+// tcgen05 kernels get a short wait limit and a role that never runs.
 std::atomic<uint32_t> g_debug_wait_limit{0};
 std::atomic<int> g_debug_stall_role{0};
 
@@ -1163,6 +1164,13 @@ int ne_conv_kind(const void* x, int64_t ldx, int M, int64_t N,
              : launch_simple<int64_t, MODE_SPLIT, false, false>(a, s);
 }
 
+int ne_debug_set_fault(int stall_role, uint32_t wait_polls) {
+  if (stall_role < 0 || stall_role > 2) return NE_ERR_INVALID_ARG;
+  g_debug_stall_role.store(stall_role);
+  g_debug_wait_limit.store(wait_polls);
+  return NE_OK;
+}
+
 size_t ne_protected_conv_ws_bytes(int M, int64_t N, int K) {
   (void)M;
   if (N <= 0 || K <= 0) return 0;
@@ -1221,6 +1229,8 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   a.l = l;
   a.failed = failed;
   a.fail_mode = fail_mode;
+  a.wait_limit = g_debug_wait_limit.load();
+  a.stall_role = g_debug_stall_role.load();
   a.ws = (uint32_t*)ws;
   // eps = c_m + 2^l c_{m-1} is increasing in both inputs, so it lies in
   // [c_min (2^l + 1), c_max (2^l + 1)]
@@ -1333,6 +1343,8 @@ extern "C" int ne_protected_conv_noalloc(const void* c, int64_t ldc, int M,
   a.l = l;
   a.failed = failed;
   a.fail_mode = fail_mode;
+  a.wait_limit = g_debug_wait_limit.load();
+  a.stall_role = g_debug_stall_role.load();
   const __int128 f = ((__int128)1 << l) + 1;
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);

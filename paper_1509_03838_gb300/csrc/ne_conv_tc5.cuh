@@ -56,13 +56,13 @@ __device__ __forceinline__ void t5_col(int n, int& o, int& jg) {
 }
 
 // ---- mbarrier helpers of the pipelined kernel ------------------------------
-// Bounded wait for the phase of parity `parity`; gives up (false) when the
-// block's abort word is set, or after the limit (then sets it and flags the
-// library's device error word).
+// Bounded wait for the phase of parity `parity` (at most `limit` polls; 0:
+// 2^24); gives up (false) when the block's abort word is set, or after the
+// limit (then sets it and flags the library's device error word).
 __device__ __forceinline__ bool t5_wait(uint64_t* bar, uint32_t parity,
-                                        volatile int* abort) {
-  constexpr uint32_t limit = 1u << 24;
-  for (uint32_t it = 0; it < limit; ++it) {
+                                        volatile int* abort, uint32_t limit) {
+  const uint32_t lim = limit ? limit : (1u << 24);
+  for (uint32_t it = 0; it < lim; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 1023u) == 1023u && *abort) return false;
   }
@@ -113,7 +113,9 @@ __device__ __forceinline__ bool t5_epi_vote(bool ok) {
 //                         Eq. 18-19 the other way round) and parks them in
 //                         a swizzled shared output tile (two buffers).
 // Every wait is bounded; a wait that expires sets the block's abort word,
-// every role then leaves its loop, and the block frees its tensor memory.
+// every role then leaves its loop, the loader waits (bounded) for the bulk
+// copies it issued, each MMA warp for the products it issued, and the block
+// frees its tensor memory.
 // ---------------------------------------------------------------------------
 constexpr int T5P_THREADS = 480;
 constexpr int T5P_WSTG = 8;     // first staging warp
@@ -124,6 +126,7 @@ constexpr int T5P_TMEM = 512;   // tensor-memory columns: 2 x M x 64 <= 512
 struct T5PBars {
   uint64_t raw_full[2], raw_empty[2], dig_full[2], dig_empty[2];
   uint64_t acc_full[2], acc_empty[2], out_full[2], out_empty[2];
+  uint64_t drain[2];  // each MMA warp's last commit (teardown)
   uint32_t tbase;
   int abort;
 };
@@ -199,6 +202,7 @@ tc5p_prot_kernel(const ConvArgs p) {
       mbar_init(&bars.acc_empty[s], 256);
       mbar_init(&bars.out_full[s], 256);
       mbar_init(&bars.out_empty[s], 128);
+      mbar_init(&bars.drain[s], 1);
     }
     bars.abort = 0;
     fence_mbar_init();
@@ -265,11 +269,14 @@ tc5p_prot_kernel(const ConvArgs p) {
 
   if (warp == T5P_WLOAD) {
     // ---- loader ----------------------------------------------------------
+    // bit s of pending: slot s's last phase was bulk copies of phase parity
+    // bit s of last_ph (drained before the block exits)
+    uint32_t pending = 0, last_ph = 0;
 #pragma unroll 1
-    for (int i = 0; i < my_n; ++i) {
+    for (int i = 0; i < (p.stall_role == 1 ? 0 : my_n); ++i) {
       const int s = i & 1;
       const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-      if (!t5_wait(&bars.raw_empty[s], ph ^ 1u, abort)) break;
+      if (!t5_wait(&bars.raw_empty[s], ph ^ 1u, abort, p.wait_limit)) break;
       const int64_t n0 = tile_n0(i);
       W* rs = raw + s * RAW;
       if (interior(n0)) {
@@ -279,7 +286,10 @@ tc5p_prot_kernel(const ConvArgs p) {
             bulk_copy_g2s(rs + m * T5_STAGE, x + (int64_t)m * p.ldx + n0 - TC_KP,
                           (uint32_t)(T5_STAGE * sizeof(W)), &bars.raw_full[s]);
         }
+        pending |= 1u << s;
+        last_ph = (last_ph & ~(1u << s)) | (ph << s);
       } else {
+        pending &= ~(1u << s);  // the slot's earlier copies were consumed
         for (int k = lane; k < MM * CPS; k += 32) {
           const int m = k / CPS, cc = k - m * CPS;
           tc_prefetch_chunk<W>(x + (int64_t)m * p.ldx, p.N, n0, cc,
@@ -291,6 +301,14 @@ tc5p_prot_kernel(const ConvArgs p) {
         if (lane == 0) t5_arrive(&bars.raw_full[s]);
       }
     }
+    // drain: every bulk copy issued has landed before the block exits (a
+    // wait that gave up may leave copies in flight)
+    if (lane == 0)
+      for (int s = 0; s < 2; ++s)
+        if (pending & (1u << s))
+          for (uint32_t it = 0; it < (1u << 24); ++it)
+            if (mbar_try_wait(&bars.raw_full[s], (last_ph >> s) & 1u)) break;
+    __syncwarp();
   } else if (warp >= T5P_WSTG && warp < T5P_WSTG + 4) {
     // ---- staging ---------------------------------------------------------
     const int ts = threadIdx.x - T5P_WSTG * 32;
@@ -300,7 +318,7 @@ tc5p_prot_kernel(const ConvArgs p) {
     // j % 2
     auto store_tile = [&](int j) {
       const int so = j & 1;
-      if (!t5_wait(&bars.out_full[so], (uint32_t)(j >> 1) & 1u, abort))
+      if (!t5_wait(&bars.out_full[so], (uint32_t)(j >> 1) & 1u, abort, p.wait_limit))
         return false;
       store_rows(outb + so * MM * T5_TILE, tile_n0(j), 0, MM, ts, 128);
       t5_arrive(&bars.out_empty[so]);
@@ -310,8 +328,8 @@ tc5p_prot_kernel(const ConvArgs p) {
     for (int i = 0; i < my_n; ++i) {
       const int s = i & 1;
       const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-      if (!t5_wait(&bars.raw_full[s], ph, abort)) break;
-      if (!t5_wait(&bars.dig_empty[s], ph ^ 1u, abort)) break;
+      if (!t5_wait(&bars.raw_full[s], ph, abort, p.wait_limit)) break;
+      if (!t5_wait(&bars.dig_empty[s], ph ^ 1u, abort, p.wait_limit)) break;
       const int64_t n0 = tile_n0(i);
       const W* rs = raw + s * RAW;
       uint16_t* ds = dig + s * DIG;
@@ -364,7 +382,7 @@ tc5p_prot_kernel(const ConvArgs p) {
     // ---- MMA issue: warp 13 takes the even streams, warp 14 the odd ones,
     // from different schedulers ---------------------------------------------
     const int parity = warp - T5P_WMMA;
-    if (lane == 0) {
+    if (lane == 0 && p.stall_role != 2) {
       // descriptors as 32-bit halves: the start address (>> 4) sits in the
       // low 14 bits, far from overflowing for addresses below 256 KB, so
       // moving an operand is one add on the low half
@@ -377,8 +395,8 @@ tc5p_prot_kernel(const ConvArgs p) {
       for (int i = 0; i < my_n; ++i) {
         const int s = i & 1;
         const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-        if (!t5_wait(&bars.dig_full[s], ph, abort)) break;
-        if (!t5_wait(&bars.acc_empty[s], ph ^ 1u, abort)) break;
+        if (!t5_wait(&bars.dig_full[s], ph, abort, p.wait_limit)) break;
+        if (!t5_wait(&bars.acc_empty[s], ph ^ 1u, abort, p.wait_limit)) break;
         t5_fence_after();
         const uint32_t a_lo = (uint32_t)a0 + (uint32_t)(s * DIG * 2 / 16);
         const uint32_t dcol = tb + s * ACC;
@@ -402,6 +420,11 @@ tc5p_prot_kernel(const ConvArgs p) {
         t5_commit(&bars.dig_empty[s]);
         t5_commit(&bars.acc_full[s]);
       }
+      // drain: every product this warp issued has completed before the
+      // block frees tensor memory
+      t5_commit(&bars.drain[parity]);
+      for (uint32_t it = 0; it < (1u << 24); ++it)
+        if (mbar_try_wait(&bars.drain[parity], 0)) break;
     }
     __syncwarp();
   } else {
@@ -413,7 +436,7 @@ tc5p_prot_kernel(const ConvArgs p) {
     for (int i = 0; i < my_n; ++i) {
       const int s = i & 1;
       const uint32_t ph = (uint32_t)(i >> 1) & 1u;
-      if (!t5_epi_vote(t5_wait(&bars.acc_full[s], ph, abort))) break;
+      if (!t5_epi_vote(t5_wait(&bars.acc_full[s], ph, abort, p.wait_limit))) break;
       t5_fence_after();
       const int64_t n0 = tile_n0(i);
       const bool edge = n0 < (int64_t)p.K - 1 || n0 + T5_TILE > p.N;
@@ -453,7 +476,7 @@ tc5p_prot_kernel(const ConvArgs p) {
       t5_arrive(&bars.acc_empty[s]);  // this buffer's columns are read
       // the output tile buffer s is free once the staging warps have
       // stored tile i - 2 from it
-      if (!t5_epi_vote(t5_wait(&bars.out_empty[s], ph ^ 1u, abort))) break;
+      if (!t5_epi_vote(t5_wait(&bars.out_empty[s], ph ^ 1u, abort, p.wait_limit))) break;
       W* ob = outb + s * MM * T5_TILE;
       // recovery, 4 positions side by side; each row is parked as soon as
       // the chain reaches it

@@ -58,7 +58,7 @@ int ne_get_device_error(uint32_t* out, int clear) {
                      ne::tcr_w64_device_error(clear != 0);
   if (v & 0x80000000u) return NE_ERR_CUDA;
   *out = v;
-  return NE_OK;
+  return (v & 1u) ? NE_ERR_TIMEOUT : NE_OK;
 }
 
 // Parameter rule (Eq. 12 constraint, Table I objective).  For a fixed l the

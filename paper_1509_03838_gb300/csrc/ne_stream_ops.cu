@@ -454,6 +454,19 @@ int ne_extract(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
   return ne_recover(delta, ldd, M, Nout, w, l, 0, d, ld_out, stream);
 }
 
+int ne_recover_mask(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
+                    int l, uint32_t failed_mask, void* d, int64_t ld_out,
+                    void* stream) {
+  if (M < 3 || M > 32) return NE_ERR_INVALID_ARG;
+  if (M < 32 && (failed_mask >> M) != 0) return NE_ERR_INVALID_ARG;
+  // only a single fail-stop is recoverable (Sec. I)
+  if (__builtin_popcount(failed_mask) >= 2) return NE_ERR_UNRECOVERABLE;
+  if (failed_mask == 0)
+    return ne_extract(delta, ldd, M, Nout, w, l, d, ld_out, stream);
+  return ne_recover(delta, ldd, M, Nout, w, l, __builtin_ctz(failed_mask), d,
+                    ld_out, stream);
+}
+
 int ne_dot(const void* x, int64_t ldx, int M, int64_t N, const void* g,
            int w, void* y, int64_t ldy, uint32_t live_mask, void* stream) {
   if (M < 1 || M > 32 || N < 0 || ldx < N || (w != 32 && w != 64) ||

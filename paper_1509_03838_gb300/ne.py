@@ -122,6 +122,17 @@ _SIGS = {
                                 _i64, _i64, _i32, _i32, _vp, _i64, _vp], _i32),
     "ne_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _vp, _i64, _i64, _i32,
                   _u32, _vp], _i32),
+    "ne_recover_mask": ([_vp, _i64, _i32, _i64, _i32, _i32, _u32, _vp, _i64,
+                         _vp], _i32),
+    "ne_fs_create": ([ctypes.POINTER(_vp), _i32], _i32),
+    "ne_fs_destroy": ([_vp], _i32),
+    "ne_fs_sync": ([_vp], _i32),
+    "ne_fs_decide": ([_i32, _u32, ctypes.POINTER(_i32)], _i32),
+    "ne_fs_protected_conv": ([_vp, _vp, _i64, _i32, _i64, _vp, _i32, _i32,
+                              _i32, _i64, _i64, _i64, _vp, _i64, _vp, _i64,
+                              _vp, _i64, ctypes.c_double, _u32,
+                              ctypes.POINTER(_u32), _vp], _i32),
+    "ne_debug_set_fault": ([_i32, _u32], _i32),
     "ne_protected_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _i32, _i32, _i64,
                             _i64, _i64, _i32, _i32, _vp, _i64, _vp], _i32),
 }
@@ -342,6 +353,82 @@ def ne_recover(delta: torch.Tensor, d: torch.Tensor, *, l: int, failed: int,
     _check(lib().ne_recover(pdl, ldd, M, n if Nout is None else Nout, w, l,
                             failed, pd, ldo, _stream(stream)), "ne_recover")
     return d
+
+
+def ne_recover_mask(delta: torch.Tensor, d: torch.Tensor, *, l: int,
+                    failed_mask: int, Nout: int | None = None,
+                    stream=None) -> torch.Tensor:
+    """Recovery with the failed streams as a mask: none -> extraction, one ->
+    recovery, two or more -> NEError(NE_ERR_UNRECOVERABLE) before any
+    launch."""
+    pdl, M, n, ldd = _rows(delta, "delta")
+    pd, _, _, ldo = _rows(d, "d")
+    w = _word_bits(delta)
+    _check(lib().ne_recover_mask(pdl, ldd, M, n if Nout is None else Nout, w,
+                                 l, failed_mask & 0xFFFFFFFF, pd, ldo,
+                                 _stream(stream)), "ne_recover_mask")
+    return d
+
+
+def ne_fs_decide(M: int, done_mask: int) -> int:
+    """The stream to recover around after a deadline (-1: none late); raises
+    NEError(NE_ERR_UNRECOVERABLE) when two or more are late."""
+    f = _i32()
+    _check(lib().ne_fs_decide(M, done_mask & 0xFFFFFFFF, ctypes.byref(f)),
+           "ne_fs_decide")
+    return int(f.value)
+
+
+class FailStop:
+    """Owner of an ne_fs (per-core CUDA streams and completion events)."""
+
+    def __init__(self, max_M: int):
+        h = _vp()
+        _check(lib().ne_fs_create(ctypes.byref(h), max_M), "ne_fs_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            lib().ne_fs_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        _check(lib().ne_fs_sync(self._h), "ne_fs_sync")
+
+    def protected_conv(self, c: torch.Tensor, g: torch.Tensor,
+                       eps: torch.Tensor, delta: torch.Tensor,
+                       d: torch.Tensor, *, l: int, c_range: tuple[int, int],
+                       max_abs_g: int, deadline_ms: float,
+                       inject_late: int = 0, stream=None) -> int:
+        """ne_fs_protected_conv; returns the mask of late cores (raises
+        NEError(NE_ERR_UNRECOVERABLE) with two or more, see .last_late)."""
+        pc, M, n, ldc = _rows(c, "c")
+        pe, _, _, lde = _rows(eps, "eps")
+        pdl, _, _, ldd = _rows(delta, "delta")
+        pd, _, _, ldo = _rows(d, "d")
+        if g.dtype != torch.int32 or not g.is_cuda:
+            raise ValueError("taps g must be an int32 CUDA tensor")
+        late = _u32()
+        st = lib().ne_fs_protected_conv(
+            self._h, pc, ldc, M, n, ctypes.c_void_p(g.data_ptr()), g.numel(),
+            _word_bits(c), l, c_range[0], c_range[1], int(max_abs_g), pe, lde,
+            pdl, ldd, pd, ldo, float(deadline_ms), inject_late & 0xFFFFFFFF,
+            ctypes.byref(late), _stream(stream))
+        self.last_late = int(late.value)
+        _check(st, "ne_fs_protected_conv")
+        return self.last_late
+
+
+def ne_debug_set_fault(stall_role: int = 0, wait_polls: int = 0) -> None:
+    """Test-only fault injection (include/ne_debug.h)."""
+    _check(lib().ne_debug_set_fault(stall_role, wait_polls & 0xFFFFFFFF),
+           "ne_debug_set_fault")
 
 
 def ne_extract(delta: torch.Tensor, d: torch.Tensor, *, l: int,

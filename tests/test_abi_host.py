@@ -261,3 +261,57 @@ def test_pipe_bytes_needs_a_pipe(ne):
     h, d = ctypes.c_int64(), ctypes.c_int64()
     assert ne.lib().ne_pipe_bytes(None, 10, 3, ctypes.byref(h),
                                   ctypes.byref(d)) == ne.NE_ERR_INVALID_ARG
+
+
+def test_recover_mask_rejects_two_failures_before_launch(ne):
+    """Only a single fail-stop is recoverable (Sec. I): two or more bits of
+    the failure mask return NE_ERR_UNRECOVERABLE on the host, before any
+    CUDA call; bits at or above M are invalid."""
+    L = ne.lib()
+    s = ctypes.c_void_p(0)
+    for M in (3, 4, 8, 32):
+        for mask in (0b11, 0b101, (1 << M) - 1 if M < 32 else 0xFFFFFFFF):
+            assert L.ne_recover_mask(DUMMY, 8, M, 8, 64, 2, mask, DUMMY, 8,
+                                     s) == ne.NE_ERR_UNRECOVERABLE
+    assert L.ne_recover_mask(DUMMY, 8, 4, 8, 64, 16, 1 << 4, DUMMY, 8,
+                             s) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_recover_mask(DUMMY, 8, 2, 8, 64, 16, 0b11, DUMMY, 8,
+                             s) == ne.NE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("M", [3, 4, 5, 6, 8, 32])
+def test_deadline_decision(ne, M):
+    """After a deadline: every core in time -> extraction (-1); exactly one
+    late -> recovery around it; two or more late -> unrecoverable.  Checked
+    over every completion mask for small M and sampled ones at M = 32."""
+    import random
+    rnd = random.Random(M)
+    full = (1 << M) - 1
+    masks = range(1 << M) if M <= 8 else [full, full & ~(1 << 7),
+                                           full & ~0b11] + [rnd.getrandbits(32)
+                                                            for _ in range(200)]
+    for done in masks:
+        late = full & ~done
+        if bin(late).count("1") >= 2:
+            with pytest.raises(ne.NEError) as ei:
+                ne.ne_fs_decide(M, done)
+            assert ei.value.status == ne.NE_ERR_UNRECOVERABLE
+        else:
+            assert ne.ne_fs_decide(M, done) == (late.bit_length() - 1 if late else -1)
+
+
+def test_failstop_and_debug_argument_checks(ne):
+    L = ne.lib()
+    h = ctypes.c_void_p()
+    for max_M in (2, 33):
+        assert L.ne_fs_create(ctypes.byref(h), max_M) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_fs_destroy(None) == ne.NE_OK
+    assert L.ne_fs_sync(None) == ne.NE_ERR_INVALID_ARG
+    late = ctypes.c_uint32()
+    assert L.ne_fs_protected_conv(None, DUMMY, 8, 4, 8, DUMMY, 4, 64, 16, -9,
+                                  9, 9, DUMMY, 8, DUMMY, 11, DUMMY, 11, 10.0,
+                                  0, ctypes.byref(late),
+                                  ctypes.c_void_p(0)) == ne.NE_ERR_INVALID_ARG
+    for role in (-1, 3):
+        assert L.ne_debug_set_fault(role, 0) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_debug_set_fault(0, 0) == ne.NE_OK
