@@ -63,9 +63,11 @@
 // warps take no issue slots.
 // Stream order within a tile (protected): r, r+1, ..., r+M-1 (r = M - 1
 // without a failure; stream r computes first and its result is dropped),
-// or r+1, ..., r+M-1 with NE_FAIL_SKIP; rows are staged in the order
-// r-1, r, ..., r+M-1 (or r, ..., r+M-1), so that stream q of the order
-// reads row positions q (neighbour) and q + 1 (own).
+// or r+1, ..., r+M-1 with NE_FAIL_SKIP; rows are staged once each, in the
+// order r-1, r, ..., r+M-2 (or r, ..., r+M-1), so that stream q of the
+// order reads row positions q (neighbour) and q + 1 (own), the last stream
+// of the wrapped order row position 0 again: that row's planes wait in one
+// of two head slots until the tile's last stream.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -106,6 +108,7 @@ __host__ __device__ constexpr int tr_nrs(int nd) { return nd <= 3 ? 4 : 3; }
 struct TrBars {
   uint64_t raw_full[3], raw_empty[3];
   uint64_t rs_full[4], rs_empty[4];
+  uint64_t head_full[2], head_empty[2];  // protected: the tile's first row
   uint64_t acc_full[4], acc_empty[4];
   uint64_t drain;
   uint32_t tbase;
@@ -119,13 +122,20 @@ struct TrTaps {
   long long total;
 };
 
-// Dynamic shared memory: plane ring, raw ring, output tile, B, taps,
-// barriers.
-template <typename W, int ND>
+// Raw-row slots of a form: the protected form keeps two (its plane ring has
+// two more slots, the head slots below), the plain form three while the
+// plane ring leaves room.
+template <bool PROT>
+__host__ __device__ constexpr int tr_nraw_form(int nd) {
+  return PROT ? 2 : tr_nraw(nd);
+}
+// Dynamic shared memory: plane ring (+ two head slots, protected), raw
+// ring, output tile, B, taps, barriers.
+template <typename W, bool PROT, int ND>
 __host__ __device__ constexpr size_t tr_smem_bytes() {
-  return (size_t)tr_nrs(ND) * ND * TR_PLANE +
-         (size_t)tr_nraw(ND) * TR_SMAX * sizeof(W) + TR_TILE * sizeof(W) +
-         TR_BBYTES + sizeof(TrTaps) + sizeof(TrBars) + 256;
+  return (size_t)(tr_nrs(ND) + (PROT ? 2 : 0)) * ND * TR_PLANE +
+         (size_t)tr_nraw_form<PROT>(ND) * TR_SMAX * sizeof(W) +
+         TR_TILE * sizeof(W) + TR_BBYTES + sizeof(TrTaps) + sizeof(TrBars) + 256;
 }
 
 // try_wait with a suspend-time hint: the thread sleeps until the phase
@@ -263,15 +273,16 @@ __device__ __forceinline__ void tr_issue_set(uint32_t dc, uint32_t pa,
 template <typename W, bool PROT, int MM, int ND, int Q>
 __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs p) {
   extern __shared__ __align__(128) int4 tr_dyn[];
-  constexpr int NRAW = tr_nraw(ND);
+  constexpr int NRAW = tr_nraw_form<PROT>(ND);
   constexpr int TR_NRS = tr_nrs(ND);
+  constexpr int NHEAD = PROT ? 2 : 0;
   constexpr int NLEV = ND + 1;                    // levels per plane set
   constexpr int NLM = ND + Q + 1;                 // merged levels (Q > 0)
   const int H = p.hist, KS = p.ks;
   const int S = TR_TILE + H;                      // staged samples per row
   const int tcols = p.tcols, tslots = p.tslots;   // tensor-memory slots
   unsigned char* planes = reinterpret_cast<unsigned char*>(tr_dyn);
-  W* raw = reinterpret_cast<W*>(planes + (size_t)TR_NRS * ND * TR_PLANE);
+  W* raw = reinterpret_cast<W*>(planes + (size_t)(TR_NRS + NHEAD) * ND * TR_PLANE);
   W* otile = raw + NRAW * TR_SMAX;  // one output row of a tile, swizzled
   unsigned char* bmat = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(otile + TR_TILE) + 127) & ~(uintptr_t)127);
@@ -287,7 +298,13 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
   // stream and row sequences of one tile
   const uint32_t live = p.live_mask & (M >= 32 ? 0xffffffffu : ((1u << M) - 1u));
   const int nstreams = PROT ? (skip ? MM - 1 : MM) : __popc(live);
-  const int nrows = PROT ? nstreams + 1 : nstreams;
+  // every raw row is staged once per tile; without NE_FAIL_SKIP the stream
+  // order wraps around (the last stream's own row is the first row staged),
+  // so that first row's planes stay in a head slot until the tile's last
+  // stream; the other rows pass through the plane ring
+  const int nrows = PROT ? MM : nstreams;
+  const bool head = PROT && !skip;
+  const int nring = head ? nrows - 1 : nrows;
   const int rbase = PROT ? (skip ? r : (r == 0 ? MM - 1 : r - 1)) : 0;
   auto row_of = [&](int j) -> int {  // raw row staged at position j
     if constexpr (PROT) {
@@ -296,6 +313,25 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
     } else {
       return bars.live_rows[j];
     }
+  };
+
+  // plane slot of row position j of the block's tile i, whose ring rows
+  // start at ring count rc0
+  struct PSlot {
+    int idx;
+    uint64_t* full;
+    uint64_t* empty;
+    uint32_t ph;
+  };
+  auto slot_of = [&](int i, uint32_t rc0, int j) -> PSlot {
+    if (head && j == 0) {
+      const int h = i & 1;
+      return {TR_NRS + h, &bars.head_full[h], &bars.head_empty[h],
+              (uint32_t)(i >> 1) & 1u};
+    }
+    const uint32_t k = rc0 + (uint32_t)(head ? j - 1 : j);
+    return {(int)(k % TR_NRS), &bars.rs_full[k % TR_NRS],
+            &bars.rs_empty[k % TR_NRS], (k / TR_NRS) & 1u};
   };
 
   // ---- setup: barriers and tensor memory, then (without the loader, which
@@ -308,6 +344,10 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
     for (int s = 0; s < TR_NRS; ++s) {
       mbar_init(&bars.rs_full[s], TR_NSTG / 32);
       mbar_init(&bars.rs_empty[s], 1);    // tcgen05.commit
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&bars.head_full[s], TR_NSTG / 32);
+      mbar_init(&bars.head_empty[s], 1);
     }
     for (int s = 0; s < 4; ++s) {
       mbar_init(&bars.acc_full[s], 1);    // tcgen05.commit
@@ -442,28 +482,29 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
     const uint32_t doff = ((ts >> 2) & 3) * TR_LBO + (ts >> 4) * 16 + (ts & 3) * 4;
     const int npairs = S / 2;
     const int S_ = S;
-    uint32_t rc = 0;
+    uint32_t rc = 0, rc0 = 0;  // raw rows, ring rows before this tile
     bool ok = true;
 #pragma unroll 1
-    for (int i = 0; i < my_n && ok; ++i) {
+    for (int i = 0; i < my_n && ok; ++i, rc0 += (uint32_t)nring) {
       const int64_t n0 = tile_n0(i);
       int blo, bhi;
       bulk_range(n0, blo, bhi);
       const bool inner = blo == 0 && bhi == S_;
 #pragma unroll 1
       for (int j = 0; j < nrows; ++j, ++rc) {
-        const int s = rc % NRAW, ps = rc % TR_NRS;
-        const uint32_t ph = (rc / NRAW) & 1u, pph = (rc / TR_NRS) & 1u;
+        const int s = rc % NRAW;
+        const uint32_t ph = (rc / NRAW) & 1u;
+        const PSlot ps = slot_of(i, rc0, j);
         bool got = true;
         if (ts == 0)
           got = tr_wait(&bars.raw_full[s], ph, abort, lim) &&
-                tr_wait(&bars.rs_empty[ps], pph ^ 1u, abort, lim);
+                tr_wait(ps.empty, ps.ph ^ 1u, abort, lim);
         if (!tr_vote<2, TR_NSTG>(got)) {
           ok = false;
           break;
         }
         const int m = row_of(j);
-        unsigned char* dst = planes + (size_t)ps * ND * TR_PLANE + doff;
+        unsigned char* dst = planes + (size_t)ps.idx * ND * TR_PLANE + doff;
         auto put = [&](uint32_t a, uint32_t b) {
           *reinterpret_cast<uint32_t*>(dst) = tr_digit_pair<0>(a, b);
           if constexpr (ND > 1)
@@ -509,7 +550,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
         __syncwarp();
         if (lane == 0) {
           t5_arrive(&bars.raw_empty[s]);
-          t5_arrive(&bars.rs_full[ps]);
+          t5_arrive(ps.full);
         }
       }
     }
@@ -523,25 +564,27 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
       const uint32_t id64 = t5_idesc(128, TR_NB);
       const uint32_t idw = t5_idesc(128, tcols);
       constexpr uint32_t SLOT16 = ND * TR_PLANE / 16;  // plane-set stride >> 4
-      uint32_t rc = 0, sc = 0;
+      uint32_t rc0 = 0, sc = 0;
       bool ok = true;
 #pragma unroll 1
-      for (int i = 0; i < my_n && ok; ++i) {
+      for (int i = 0; i < my_n && ok; ++i, rc0 += (uint32_t)nring) {
 #pragma unroll 1
         for (int q = 0; q < nstreams; ++q, ++sc) {
-          const uint32_t jo = rc + (PROT ? q + 1 : q), jn = rc + q;
-          const int po = jo % TR_NRS, pn = jn % TR_NRS;
+          // stream q reads row positions q (neighbour) and q + 1 (own; the
+          // first row again for the last stream of a wrapped order)
+          const int jo = PROT ? (q + 1 == MM ? 0 : q + 1) : q;
+          const PSlot so = slot_of(i, rc0, jo), sn = slot_of(i, rc0, q);
           const int ts = (int)(sc % (uint32_t)tslots);
-          if (!tr_wait(&bars.rs_full[po], (jo / TR_NRS) & 1u, abort, lim) ||
-              (PROT && !tr_wait(&bars.rs_full[pn], (jn / TR_NRS) & 1u, abort, lim)) ||
+          if (!tr_wait(so.full, so.ph, abort, lim) ||
+              (PROT && !tr_wait(sn.full, sn.ph, abort, lim)) ||
               !tr_wait(&bars.acc_empty[ts], ((sc / tslots) & 1u) ^ 1u, abort, lim)) {
             ok = false;
             break;
           }
           t5_fence_after();
           const uint32_t dcol = tb + (uint32_t)(ts * tcols);
-          const uint32_t pao = a_lo0 + (uint32_t)po * SLOT16;
-          const uint32_t pan = a_lo0 + (uint32_t)pn * SLOT16;
+          const uint32_t pao = a_lo0 + (uint32_t)so.idx * SLOT16;
+          const uint32_t pan = a_lo0 + (uint32_t)sn.idx * SLOT16;
           const uint32_t dn = dcol + 32u * (Q > 0 ? Q : NLEV);
           switch (KS) {
 #define TR_ISSUE(K_)                                                      \
@@ -558,14 +601,17 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
 #undef TR_ISSUE
           }
           t5_commit(&bars.acc_full[ts]);
+          // release each plane slot after its last reader: a ring row after
+          // the stream that reads it as neighbour (the head, row 0 of a
+          // wrapped order, after the last stream), the last row of an
+          // unwrapped order after the last stream
           if (PROT) {
-            t5_commit(&bars.rs_empty[pn]);
-            if (q == nstreams - 1) t5_commit(&bars.rs_empty[po]);
+            if (!(head && q == 0)) t5_commit(sn.empty);
+            if (q == nstreams - 1) t5_commit(so.empty);
           } else {
-            t5_commit(&bars.rs_empty[po]);
+            t5_commit(so.empty);
           }
         }
-        rc += (uint32_t)nrows;
       }
       // drain: every product issued has completed before the block exits
       t5_commit(&bars.drain);
@@ -754,7 +800,7 @@ template <typename W, bool PROT, int MM, int ND, int Q>
 int tr_launch_one(const ConvArgs& a, cudaStream_t s) {
   static std::once_flag once;
   static int attr = NE_OK;
-  constexpr size_t smem = tr_smem_bytes<W, ND>();
+  constexpr size_t smem = tr_smem_bytes<W, PROT, ND>();
   std::call_once(once, [] {
     auto k = tcr_conv_kernel<W, PROT, MM, ND, Q>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
