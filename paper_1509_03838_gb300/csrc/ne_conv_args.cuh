@@ -34,6 +34,10 @@ struct ConvArgs {
                        // in the stream's own levels (l = 8 mlev), 0: apart
   int vec;             // rows of x 16-byte aligned
   unsigned long long corr_mul;  // range-shift correction per unit tap sum
+  int ytma;            // output rows stored by tensor copies (tensor map
+                       // passed beside the arguments), else by the threads
+  int64_t yfull;       // outputs per row inside the tensor map (whole
+                       // 128-byte pieces); the rest by the threads
   uint32_t wait_limit; // polls before a wait gives up (0: default)
   int stall_role;      // fault injection: 1 loader, 2 MMA issue never run
 };

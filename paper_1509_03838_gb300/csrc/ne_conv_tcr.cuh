@@ -70,7 +70,9 @@
 // of two head slots until the tile's last stream.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <mutex>
@@ -130,12 +132,13 @@ __host__ __device__ constexpr int tr_nraw_form(int nd) {
   return PROT ? 2 : tr_nraw(nd);
 }
 // Dynamic shared memory: plane ring (+ two head slots, protected), raw
-// ring, output tile, B, taps, barriers.
+// ring, output tile (1024-byte aligned), B, taps, barriers.
 template <typename W, bool PROT, int ND>
 __host__ __device__ constexpr size_t tr_smem_bytes() {
   return (size_t)(tr_nrs(ND) + (PROT ? 2 : 0)) * ND * TR_PLANE +
          (size_t)tr_nraw_form<PROT>(ND) * TR_SMAX * sizeof(W) +
-         TR_TILE * sizeof(W) + TR_BBYTES + sizeof(TrTaps) + sizeof(TrBars) + 256;
+         TR_TILE * sizeof(W) + 1024 + TR_BBYTES + sizeof(TrTaps) + sizeof(TrBars) +
+         256;
 }
 
 // try_wait with a suspend-time hint: the thread sleeps until the phase
@@ -238,6 +241,32 @@ __device__ __forceinline__ void tr_ld8(uint32_t taddr, uint32_t (&r)[8]) {
       : "r"(taddr));
 }
 
+// Tensor copy of a box of the output (x, y, z) from shared memory, in the
+// issuing thread's bulk group; commit, and the waits for the groups'
+// shared-memory reads or full completion.
+__device__ __forceinline__ void tr_tma_store3(const CUtensorMap* tm,
+                                              const void* src, int c0, int c1,
+                                              int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+      ::"l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2),
+      "r"(smem_addr(src))
+      : "memory");
+}
+__device__ __forceinline__ void tr_bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tr_bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void tr_bulk_wait0() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+template <int NT>
+__device__ __forceinline__ void tr_bar_id(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NT) : "memory");
+}
+
 // One plane set's products (ND digits x KS k-steps) into columns dc + 32 d;
 // with CLEAR the first instruction spans all `idw` columns with no
 // accumulate.  Descriptors arrive as 32-bit halves; every k-step's offset
@@ -271,7 +300,8 @@ __device__ __forceinline__ void tr_issue_set(uint32_t dc, uint32_t pa,
 // products <= 2^22 in all); Q = 0 keeps them in levels of their own.
 // ---------------------------------------------------------------------------
 template <typename W, bool PROT, int MM, int ND, int Q>
-__global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs p) {
+__global__ void __launch_bounds__(TR_THREADS, 1)
+    tcr_conv_kernel(const ConvArgs p, const __grid_constant__ CUtensorMap ytm) {
   extern __shared__ __align__(128) int4 tr_dyn[];
   constexpr int NRAW = tr_nraw_form<PROT>(ND);
   constexpr int TR_NRS = tr_nrs(ND);
@@ -283,7 +313,10 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
   const int tcols = p.tcols, tslots = p.tslots;   // tensor-memory slots
   unsigned char* planes = reinterpret_cast<unsigned char*>(tr_dyn);
   W* raw = reinterpret_cast<W*>(planes + (size_t)(TR_NRS + NHEAD) * ND * TR_PLANE);
-  W* otile = raw + NRAW * TR_SMAX;  // one output row of a tile, swizzled
+  // one output row of a tile, swizzled; four quarters of 1024 outputs, one
+  // per tensor-memory lane quadrant, in the tensor-copy layout
+  W* otile = reinterpret_cast<W*>(
+      (reinterpret_cast<uintptr_t>(raw + NRAW * TR_SMAX) + 1023) & ~(uintptr_t)1023);
   unsigned char* bmat = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(otile + TR_TILE) + 127) & ~(uintptr_t)127);
   TrTaps& tt = *reinterpret_cast<TrTaps*>(bmat + TR_BBYTES);
@@ -671,16 +704,69 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
         out[e] = wadd<W>(own[e], (W)corr);
       }
     };
-    // Output row m of the tile at n0: every epilogue thread parks its 8
-    // outputs in the output tile (16-byte chunks, chunk c of block b at
-    // c ^ (b % 8), so that lanes 256 bytes apart fall in distinct banks),
-    // then the 512 threads store the row segment with coalesced 16-byte
-    // stores (word stores for rows that are not 16-byte aligned).
+    // Output row m of the tile at n0.
+    // With a tensor map (rows 16-byte aligned): the four warps of a lane
+    // quadrant own 1024 consecutive outputs (blocks 32 qd .. 32 qd + 31)
+    // and move them on their own: each thread writes its 8 outputs into
+    // the quadrant's quarter of the output tile in the 128-byte swizzled
+    // layout of the tensor copy (16-byte chunk c of 128-byte row R at
+    // c ^ (R % 8)), and the quadrant's first thread stores the quarter by
+    // one tensor copy, which runs on while the warps go on.  For 64-bit
+    // words a thread's four chunks sit in one half of two rows; lanes
+    // 4..7 of every eight take them in the order k ^ 1, so that the eight
+    // lanes of a 16-byte store phase meet eight distinct bank groups.
+    // Outputs past the map's last whole 128-byte piece of a row are stored
+    // by their threads.
+    constexpr int EPR = 128 / (int)sizeof(W);        // words per 128 bytes
+    constexpr int QBYTES = 1024 * (int)sizeof(W);    // bytes of a quarter
+    unsigned char* qbuf = reinterpret_cast<unsigned char*>(otile) + qd * QBYTES;
+    const bool qlead = og == 0 && lane == 0;         // issues the quarter
+    auto emit_tma = [&](int m, int64_t n0, const W (&v)[8]) {
+      if (qlead) tr_bulk_wait_read0();  // the quarter's last copy has read it
+      tr_bar_id<128>(5 + qd);
+      if constexpr (sizeof(W) == 8) {
+        const int u = (lane >> 2) & 1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t o = 256u * lane + 64u * og + 16u * (uint32_t)(k ^ u);
+          const W lo = u ? v[2 * (k ^ 1)] : v[2 * k];
+          const W hi = u ? v[2 * (k ^ 1) + 1] : v[2 * k + 1];
+          *reinterpret_cast<longlong2*>(qbuf + (o ^ ((o >> 3) & 0x70u))) =
+              make_longlong2(lo, hi);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const uint32_t o = 128u * lane + 32u * og + 16u * k;
+          *reinterpret_cast<int4*>(qbuf + (o ^ ((o >> 3) & 0x70u))) =
+              make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        }
+      }
+      fence_proxy_async_smem();
+      tr_bar_id<128>(5 + qd);
+      // (a quarter wholly past the map's pieces is not stored)
+      if (qlead && n0 + 1024 * qd < p.yfull) {
+        tr_tma_store3(&ytm, qbuf, 0, (int)((n0 + 1024 * qd) / EPR), m);
+        tr_bulk_commit();
+      }
+      const int64_t nb = n0 + pos0;
+      if (nb + 8 > p.yfull) {
+        W* grow = y + (int64_t)m * p.ldy;
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (nb + e >= p.yfull && nb + e < p.Nout) grow[nb + e] = v[e];
+      }
+    };
+    // Without a tensor map: every epilogue thread parks its 8 outputs in
+    // the output tile (16-byte chunks, chunk c of block b at c ^ (b % 8), so
+    // that lanes 256 bytes apart fall in distinct banks), then the 512
+    // threads store the row segment with coalesced 16-byte stores (word
+    // stores for rows that are not 16-byte aligned).
     constexpr int CPB = TR_P * (int)sizeof(W) / 16;  // chunks per block
     constexpr int CPT = 8 * (int)sizeof(W) / 16;     // chunks per thread
     constexpr int VW = 16 / (int)sizeof(W);          // words per chunk
     constexpr int NCH = TR_TILE / VW;                // chunks per row
-    auto emit_row = [&](int m, int64_t n0, const W (&v)[8]) {
+    auto emit_threads = [&](int m, int64_t n0, const W (&v)[8]) {
       const int c0 = pos0 / VW;
 #pragma unroll
       for (int k = 0; k < CPT; ++k) {
@@ -709,6 +795,12 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
         }
       }
       tr_bar<4, TR_EPI>();
+    };
+    auto emit_row = [&](int m, int64_t n0, const W (&v)[8]) {
+      if (p.ytma)
+        emit_tma(m, n0, v);
+      else
+        emit_threads(m, n0, v);
     };
 #pragma unroll 1
     for (int i = 0; i < my_n; ++i) {
@@ -786,6 +878,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
         if (!ok) break;
       }
     }
+    // every tensor copy of the block has completed before it exits
+    if (p.ytma && qlead) tr_bulk_wait0();
   }
   // ---- teardown --------------------------------------------------------------
   t5_fence_before();
@@ -796,8 +890,56 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tcr_conv_kernel(const ConvArgs 
   }
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime.
+inline PFN_cuTensorMapEncodeTiled_v12000 tr_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                         cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of the output rows for the quarter-row tensor copies: the
+// rows as (128-byte pieces of EPR words) x (whole pieces per row) x (M
+// rows), box one quarter row (1024 outputs), 128-byte swizzle.  Taken only
+// when the base is 16-byte aligned and the row stride a multiple of 16
+// bytes (any stride for one row); otherwise a.ytma stays 0 and the threads
+// store.
+template <typename W>
+void tr_output_map(ConvArgs& a, CUtensorMap* tm) {
+  constexpr int64_t EPR = 128 / (int64_t)sizeof(W);
+  a.ytma = 0;
+  a.yfull = 0;
+  const int64_t pieces = a.Nout / EPR;
+  const uint64_t rs = (uint64_t)a.ldy * sizeof(W);
+  if (pieces < 1 || pieces > INT32_MAX / 2 || a.M < 1 ||
+      (reinterpret_cast<uintptr_t>(a.y) & 15) != 0 || (a.M > 1 && rs % 16 != 0))
+    return;
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tr_encoder();
+  if (!enc) return;
+  const cuuint64_t dims[3] = {(cuuint64_t)EPR, (cuuint64_t)pieces, (cuuint64_t)a.M};
+  const cuuint64_t strides[2] = {128, a.M > 1 ? (cuuint64_t)rs : (cuuint64_t)pieces * 128};
+  const cuuint32_t box[3] = {(cuuint32_t)EPR, (cuuint32_t)(1024 / EPR), 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(
+      tm, sizeof(W) == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+      3, a.y, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return;
+  a.ytma = 1;
+  a.yfull = pieces * EPR;
+}
+
 template <typename W, bool PROT, int MM, int ND, int Q>
-int tr_launch_one(const ConvArgs& a, cudaStream_t s) {
+int tr_launch_one(const ConvArgs& a0, cudaStream_t s) {
   static std::once_flag once;
   static int attr = NE_OK;
   constexpr size_t smem = tr_smem_bytes<W, PROT, ND>();
@@ -811,8 +953,11 @@ int tr_launch_one(const ConvArgs& a, cudaStream_t s) {
     cudaGetLastError();
     return attr;
   }
+  ConvArgs a = a0;
+  alignas(64) CUtensorMap tm{};
+  tr_output_map<W>(a, &tm);
   const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)sm_count());
-  tcr_conv_kernel<W, PROT, MM, ND, Q><<<(unsigned)grid, TR_THREADS, smem, s>>>(a);
+  tcr_conv_kernel<W, PROT, MM, ND, Q><<<(unsigned)grid, TR_THREADS, smem, s>>>(a, tm);
   return cudaGetLastError() == cudaSuccess ? NE_OK : NE_ERR_CUDA;
 }
 
