@@ -283,6 +283,15 @@ def timed(fn, steps, world, stream, per_launch=False):
     return total, launches
 
 
+def out_rows(rows, n, dev):
+    """Output rows of n int64 words whose stride is a multiple of 16 bytes
+    (one spare word when n is odd), the layout whose rows the tensor-copy
+    output of the convolution kernels stores in whole 128-byte pieces; a
+    view [rows, n] of the buffer."""
+    import torch
+    return torch.empty((rows, n + (n & 1)), dtype=torch.int64, device=dev)[:, :n]
+
+
 def run_ne(args):
     import torch
 
@@ -304,7 +313,7 @@ def run_ne(args):
     stream = torch.cuda.current_stream()
     c = torch.from_numpy(j.c).to(dev)
     g = torch.from_numpy(j.g.astype(np.int32)).to(dev)
-    d = torch.empty((M, Nout), dtype=torch.int64, device=dev)
+    d = out_rows(M, Nout, dev)
     ws = torch.empty(ne.ne_protected_conv_ws_bytes(M, N, K), dtype=torch.uint8,
                      device=dev)
 
@@ -345,7 +354,7 @@ def run_ne(args):
 
     cs = torch.empty((M + 1, N), dtype=torch.int64, device=dev)
     cs[:M] = c
-    cso = torch.empty((M + 1, Nout), dtype=torch.int64, device=dev)
+    cso = out_rows(M + 1, Nout, dev)
 
     def checksum(i):      # Eq. 3-5: checksum stream, M+1 convs, recovery
         f = i % M
@@ -355,7 +364,7 @@ def run_ne(args):
         ne.ne_checksum_recover(cso[:M], cso[M], cso[f], f=f)
 
     eps = torch.empty_like(c)
-    delta = torch.empty_like(d)
+    delta = out_rows(M, Nout, dev)
 
     f_ent = (1 << p.l) + 1
     eps_range = (j.c_range[0] * f_ent, j.c_range[1] * f_ent)
@@ -398,38 +407,54 @@ def run_ne(args):
         probe[nm] = rate
     span = (j.c_range[1] - j.c_range[0]) * f_ent
     algo_bytes = float((M * N + M * Nout) * 8)
-    tc_path = (span <= 0xFFFFFFFF and K <= 65 and j.bound_g <= 32768 and M <= 4
+    # the raw-plane tcgen05 kernel takes the job: K <= 65, |g| <= 2^15,
+    # 3 <= M <= 6 and the raw inputs' span within two byte digits
+    raw_span = j.c_range[1] - j.c_range[0]
+    tc_path = (K <= 65 and j.bound_g <= 32768 and 3 <= M <= 6
+               and raw_span < (1 << 16)
                and os.environ.get("NE_CONV_TC", "1") != "0"
-               and os.environ.get("NE_CONV_TC5", "1") != "0"
+               and os.environ.get("NE_CONV_TCR", "1") != "0"
                and os.environ.get("NE_PROT_KERNEL") is None)
     if tc_path:
         # Exact products on the tensor cores leave the step bound by memory:
         # c read once and d written once (algorithmic bytes) against the
-        # measured copy bandwidth.  The step is one kernel (M <= 4, 16-byte
-        # rows): tcgen05 products in tensor memory, recovery in its epilogue.
+        # measured copy bandwidth.  The step is one kernel: the byte-digit
+        # planes of the raw rows, every stream's entangled products in
+        # tensor memory, recovery in its epilogue, quarter rows out by
+        # tensor copies.
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         hbm = float(peaks["hbm_gbs"])
         achieved = algo_bytes / (prot_ms * 1e-3) / 1e9
-        # 20 tcgen05.mma (4 operand digits x 5 k-steps) per stream per
-        # 1024-output tile; every stream computes (the failure drops one)
-        mma_per_step = M * float((Nout + 1023) // 1024) * 20.0
+        # per stream and 4096-output tile: (own + neighbour) x 2 operand
+        # digits x (2 + H / 16) k-steps of M = 128, N = 64, K = 16 products
+        # (H = K - 1 rounded up to 16); every stream computes (the failure
+        # drops one)
+        H = 16 * ((K - 1 + 15) // 16)
+        mma_per_step = M * float((Nout + 4095) // 4096) * 2 * 2 * (2 + H // 16)
+        flop_per_step = mma_per_step * 2.0 * 128 * 64 * 16
         traffic = (TRAFFIC_CAPTURE["bytes"]
                    if TRAFFIC_CAPTURE["sources_sha256"] == conv_sources_sha()
                    else None)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm,
                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                     "algorithmic_bytes": algo_bytes,
-                    "kernel": "tc5p_prot_kernel<int64, BIAS, 4> (fused, "
-                              "warp-specialised: bulk-copy loads, entangled "
-                              "digit staging, tcgen05.mma into tensor memory, "
-                              "recovery in the epilogue)",
+                    "kernel": "tcr_conv_kernel<int64, PROT, M=4, ND=2, Q=2, "
+                              "YS=0> (fused, warp-specialised: bulk-copy raw "
+                              "rows, byte-digit planes, tcgen05.mma into "
+                              "tensor memory with the neighbour's levels "
+                              "merged, recovery in the epilogue, quarter rows "
+                              "out by cp.async.bulk.tensor)",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured "
-                                   "copy bandwidth)",
+                                   "copy bandwidth), of measured",
                     "launch_ms": prot_ms,
-                    "tensor": {"tcgen05_mma_per_s": mma_per_step / (prot_ms * 1e-3),
-                               "probe_tcgen05_mma_per_s": probe["tcgen05_f16_n16"],
-                               "frac": mma_per_step / (prot_ms * 1e-3)
-                                       / probe["tcgen05_f16_n16"]},
+                    "tensor": {"tcgen05_mma_per_launch": mma_per_step,
+                               "tflops": flop_per_step / (prot_ms * 1e-3) / 1e12,
+                               "peak_tflops": float(peaks["bf16_tflops"]),
+                               "frac": flop_per_step / (prot_ms * 1e-3) / 1e12
+                                       / float(peaks["bf16_tflops"]),
+                               "note": "fp16 operands, fp32 accumulation; "
+                                       "peak = measured bf16 burst (same "
+                                       "nominal rate)"},
                     "probe_instr_per_s": probe}
     else:
         # The entangled words c_m + 2^l c_{m-1} with c in [-2^15, 2^15) and
@@ -537,17 +562,16 @@ def run_ne(args):
 E2E_CHUNK = 1 << 20
 E2E_STREAMS = 4
 
+# DRAM bytes of one launch of the fused kernel from an ncu capture of the
+# committed sources (CONV_SOURCES, by hash); None until taken again after a
+# change of those sources.
 TRAFFIC_CAPTURE = {
-    "sources_sha256":
-        "ce630cfbc87cbd149d22c9924493df67821cb5495e7e364e343ee8ca4ace76fa",
-    # tc5p_prot_kernel<int64, BIAS, 4>, second of three captured launches:
-    # 134301440 bytes read + 76453632 written (the rest of d is still in L2
-    # when the launch ends); profiles/conv_tc5_protected_M4_N2e22_K64.md
-    "bytes": 134301440 + 76453632,
+    "sources_sha256": None,
+    "bytes": None,
 }
-CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_conv_tc.cuh",
-                "ne_conv_tc5.cuh", "ne_tc5.cuh", "ne_recover.cuh",
-                "ne_common.cuh", "ne_stream_ops.cu"]
+CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_conv_args.cuh",
+                "ne_conv_tcr.cuh", "ne_conv_tcr_w64.cu", "ne_tc5.cuh",
+                "ne_common.cuh"]
 
 
 def conv_sources_sha() -> str:
@@ -606,8 +630,8 @@ def bench_paper_shapes(ne, dev, stream, reps=5):
             g = torch.empty(K, dtype=torch.int32, device=dev).random_(
                 -b, b, generator=gen)
             Nout = N + K - 1
-            d = torch.empty((M, Nout), dtype=torch.int64, device=dev)
-            dcs = torch.empty((M + 1, Nout), dtype=torch.int64, device=dev)
+            d = out_rows(M, Nout, dev)
+            dcs = out_rows(M + 1, Nout, dev)
             ws = torch.empty(ne.ne_protected_conv_ws_bytes(M, N, K),
                              dtype=torch.uint8, device=dev)
 

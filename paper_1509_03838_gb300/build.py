@@ -19,8 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libne.so")
 
 SOURCES = ["ne_host.cpp", "ne_stream_ops.cu", "ne_conv.cu", "ne_conv_tcr_w32.cu",
-           "ne_conv_tcr_w64.cu", "ne_batch.cu", "ne_gemm.cu", "ne_pipe.cu",
-           "ne_failstop.cu",
+           "ne_conv_tcr_w64.cu", "ne_conv_tcr_w32s.cu", "ne_conv_tcr_w64s.cu",
+           "ne_batch.cu", "ne_gemm.cu", "ne_pipe.cu", "ne_failstop.cu",
            "ne_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",

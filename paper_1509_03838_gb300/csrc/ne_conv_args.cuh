@@ -34,10 +34,13 @@ struct ConvArgs {
                        // in the stream's own levels (l = 8 mlev), 0: apart
   int vec;             // rows of x 16-byte aligned
   unsigned long long corr_mul;  // range-shift correction per unit tap sum
-  int ytma;            // output rows stored by tensor copies (tensor map
-                       // passed beside the arguments), else by the threads
-  int64_t yfull;       // outputs per row inside the tensor map (whole
-                       // 128-byte pieces); the rest by the threads
+  int ytma;            // output rows stored by tensor copies (two tensor
+                       // maps passed beside the arguments, rows of even and
+                       // of odd index), else by the threads
+  int yoff[2];         // per row class: leading outputs of a row before its
+                       // first 16-byte boundary (the map starts there)
+  int64_t yfull[2];    // per row class: outputs of a row up to the end of
+                       // the map's last whole 128-byte piece
   uint32_t wait_limit; // polls before a wait gives up (0: default)
   int stall_role;      // fault injection: 1 loader, 2 MMA issue never run
 };
@@ -54,8 +57,15 @@ constexpr int TR_HMAX = 64;
 // for M = 4 only); NE_ERR_UNSUPPORTED when the form cannot run here.
 int tcr_launch_w32(const ConvArgs& a, bool prot, cudaStream_t s);
 int tcr_launch_w64(const ConvArgs& a, bool prot, cudaStream_t s);
+// The forms for output rows of a class 8 bytes past a 16-byte boundary
+// (a planned by the entry points above, output maps built; tm points to the
+// two CUtensorMaps).
+int tcr_launch_w32s(const ConvArgs& a, const void* tm, bool prot, cudaStream_t s);
+int tcr_launch_w64s(const ConvArgs& a, const void* tm, bool prot, cudaStream_t s);
 // Host readers of those translation units' device error words.
 unsigned tcr_w32_device_error(bool clear);
 unsigned tcr_w64_device_error(bool clear);
+unsigned tcr_w32s_device_error(bool clear);
+unsigned tcr_w64s_device_error(bool clear);
 
 }  // namespace ne

@@ -55,9 +55,11 @@
 //                           exactly (fp32 + 1.5 * 2^23, then integer), the
 //                           range shift undone, then (protected) all M
 //                           outputs recovered from the M - 1 products other
-//                           than r's (Eq. 16-19, w-bit chain); each output
-//                           row passes through a swizzled shared tile so
-//                           that its stores are coalesced.
+//                           than r's (Eq. 16-19, w-bit chain); each
+//                           quadrant's quarter of an output row passes
+//                           through a swizzled shared tile and leaves by
+//                           one tensor copy (cp.async.bulk.tensor) issued
+//                           by one thread of the quadrant.
 // One lane of each role polls an mbarrier (a hinted try_wait, which
 // sleeps); the rest of the role waits on a named barrier, so that waiting
 // warps take no issue slots.
@@ -298,10 +300,14 @@ __device__ __forceinline__ void tr_issue_set(uint32_t dc, uint32_t pa,
 // neighbour's levels start at level Q of the stream's own and share its
 // accumulator columns (exact while a merged level gathers at most 4 K
 // products <= 2^22 in all); Q = 0 keeps them in levels of their own.
+// YS (tensor-copy output): 0 when every row starts on a 16-byte boundary,
+// 1 when a row class starts 8 bytes past one (its outputs shifted by 8
+// bytes in the output tile).
 // ---------------------------------------------------------------------------
-template <typename W, bool PROT, int MM, int ND, int Q>
+template <typename W, bool PROT, int MM, int ND, int Q, int YS>
 __global__ void __launch_bounds__(TR_THREADS, 1)
-    tcr_conv_kernel(const ConvArgs p, const __grid_constant__ CUtensorMap ytm) {
+    tcr_conv_kernel(const ConvArgs p, const __grid_constant__ CUtensorMap ytm0,
+                    const __grid_constant__ CUtensorMap ytm1) {
   extern __shared__ __align__(128) int4 tr_dyn[];
   constexpr int NRAW = tr_nraw_form<PROT>(ND);
   constexpr int TR_NRS = tr_nrs(ND);
@@ -705,56 +711,114 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
       }
     };
     // Output row m of the tile at n0.
-    // With a tensor map (rows 16-byte aligned): the four warps of a lane
-    // quadrant own 1024 consecutive outputs (blocks 32 qd .. 32 qd + 31)
-    // and move them on their own: each thread writes its 8 outputs into
-    // the quadrant's quarter of the output tile in the 128-byte swizzled
-    // layout of the tensor copy (16-byte chunk c of 128-byte row R at
-    // c ^ (R % 8)), and the quadrant's first thread stores the quarter by
-    // one tensor copy, which runs on while the warps go on.  For 64-bit
-    // words a thread's four chunks sit in one half of two rows; lanes
-    // 4..7 of every eight take them in the order k ^ 1, so that the eight
-    // lanes of a 16-byte store phase meet eight distinct bank groups.
-    // Outputs past the map's last whole 128-byte piece of a row are stored
-    // by their threads.
+    // With tensor maps: the four warps of a lane quadrant own 1024
+    // consecutive outputs (blocks 32 qd .. 32 qd + 31) and move them on
+    // their own.  The rows of even and of odd index form two classes, each
+    // with its own map; a class whose rows do not start on a 16-byte
+    // boundary has its map start off outputs later, at the first boundary,
+    // and a quarter's box one 128-byte piece short, so that every box of
+    // the class starts on a boundary.  Each thread writes its outputs that
+    // lie in the box into the quadrant's quarter of the output tile, in the
+    // 128-byte swizzled layout of the tensor copy (16-byte chunk c of
+    // 128-byte row R at c ^ (R % 8)), and stores the rest (outputs before
+    // the class's first boundary, past the box, past the map's last piece)
+    // itself; the quadrant's first thread then stores the box by one
+    // tensor copy, which runs on while the warps go on.  For 64-bit words
+    // on a boundary a thread's four chunks sit in one half of two rows;
+    // lanes 4..7 of every eight take them in the order k ^ 1, so that the
+    // eight lanes of a 16-byte store phase meet eight distinct bank groups.
     constexpr int EPR = 128 / (int)sizeof(W);        // words per 128 bytes
     constexpr int QBYTES = 1024 * (int)sizeof(W);    // bytes of a quarter
     unsigned char* qbuf = reinterpret_cast<unsigned char*>(otile) + qd * QBYTES;
     const bool qlead = og == 0 && lane == 0;         // issues the quarter
     auto emit_tma = [&](int m, int64_t n0, const W (&v)[8]) {
+      const int cls = m & 1;
+      const int off = YS ? p.yoff[cls] : 0;
+      const int64_t full = p.yfull[cls];
+      const int box = off ? 1024 - EPR : 1024;       // outputs of a box
+      const int64_t q0 = n0 + 1024 * qd;             // first output of the quarter
+      const int pl0 = TR_P * lane + 8 * og;          // first local output
       if (qlead) tr_bulk_wait_read0();  // the quarter's last copy has read it
       tr_bar_id<128>(5 + qd);
-      if constexpr (sizeof(W) == 8) {
-        const int u = (lane >> 2) & 1;
+      if constexpr (YS == 0) {
+        if constexpr (sizeof(W) == 8) {
+          const int u = (lane >> 2) & 1;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t o = 256u * lane + 64u * og + 16u * (uint32_t)(k ^ u);
-          const W lo = u ? v[2 * (k ^ 1)] : v[2 * k];
-          const W hi = u ? v[2 * (k ^ 1) + 1] : v[2 * k + 1];
-          *reinterpret_cast<longlong2*>(qbuf + (o ^ ((o >> 3) & 0x70u))) =
-              make_longlong2(lo, hi);
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t o = 256u * lane + 64u * og + 16u * (uint32_t)(k ^ u);
+            const W lo = u ? v[2 * (k ^ 1)] : v[2 * k];
+            const W hi = u ? v[2 * (k ^ 1) + 1] : v[2 * k + 1];
+            *reinterpret_cast<longlong2*>(qbuf + (o ^ ((o >> 3) & 0x70u))) =
+                make_longlong2(lo, hi);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const uint32_t o = 128u * lane + 32u * og + 16u * k;
+            *reinterpret_cast<int4*>(qbuf + (o ^ ((o >> 3) & 0x70u))) =
+                make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          }
+        }
+        if (q0 + pl0 + 8 > full) {
+          // outputs past the map's last piece (the copy leaves them out)
+          W* grow = y + (int64_t)m * p.ldy;
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (q0 + pl0 + e >= full && q0 + pl0 + e < p.Nout) grow[q0 + pl0 + e] = v[e];
         }
       } else {
+        // The thread's outputs from byte o0 of the box (8 bytes before its
+        // 16-byte chunk when the class starts 8 bytes past a boundary): a
+        // store goes to the tile where it lies wholly in the box (the box
+        // and the chunks are 16-byte multiples, so a 16-byte pair is in or
+        // out as a whole); outputs outside the box or past the map's last
+        // piece are then stored directly.
+        const int boxb = box * (int)sizeof(W);
+        const int o0 = pl0 * (int)sizeof(W) - (off ? 8 : 0);
+        auto swz = [&](int o) { return qbuf + (o ^ ((o >> 3) & 0x70)); };
+        auto st8 = [&](int o, long long u) {
+          if (o >= 0 && o + 8 <= boxb) *reinterpret_cast<long long*>(swz(o)) = u;
+        };
+        auto st16 = [&](int o, long long a, long long b) {
+          if (o >= 0 && o + 16 <= boxb)
+            *reinterpret_cast<longlong2*>(swz(o)) = make_longlong2(a, b);
+        };
+        auto u8 = [&](int e) -> long long {  // 8 bytes from output e
+          if constexpr (sizeof(W) == 8)
+            return (long long)v[e];
+          else
+            return (long long)(((unsigned long long)(uint32_t)v[e + 1] << 32) |
+                               (uint32_t)v[e]);
+        };
+        constexpr int UW = 8 / (int)sizeof(W);  // outputs per 8 bytes
+        if (off) {
+          st8(o0, u8(0));
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const uint32_t o = 128u * lane + 32u * og + 16u * k;
-          *reinterpret_cast<int4*>(qbuf + (o ^ ((o >> 3) & 0x70u))) =
-              make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          for (int k = 0; k < 8 / UW / 2 - 1; ++k)
+            st16(o0 + 8 + 16 * k, u8(UW * (1 + 2 * k)), u8(UW * (2 + 2 * k)));
+          st8(o0 + 8 * (8 / UW - 1), u8(8 - UW));
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8 / UW / 2; ++k)
+            st16(o0 + 16 * k, u8(UW * 2 * k), u8(UW * (2 * k + 1)));
+        }
+        if (o0 < 0 || o0 + 8 * (int)sizeof(W) > boxb || q0 + pl0 + 8 > full) {
+          W* grow = y + (int64_t)m * p.ldy;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int oe = o0 + e * (int)sizeof(W);
+            const int64_t pos = q0 + pl0 + e;
+            const bool inbox = oe >= 0 && oe + (int)sizeof(W) <= boxb && pos < full;
+            if (!inbox && pos < p.Nout) grow[pos] = v[e];
+          }
         }
       }
       fence_proxy_async_smem();
       tr_bar_id<128>(5 + qd);
-      // (a quarter wholly past the map's pieces is not stored)
-      if (qlead && n0 + 1024 * qd < p.yfull) {
-        tr_tma_store3(&ytm, qbuf, 0, (int)((n0 + 1024 * qd) / EPR), m);
+      // (a box wholly past the map's pieces is not stored)
+      if (qlead && q0 + off < full) {
+        tr_tma_store3(cls ? &ytm1 : &ytm0, qbuf, 0, (int)(q0 / EPR), m >> 1);
         tr_bulk_commit();
-      }
-      const int64_t nb = n0 + pos0;
-      if (nb + 8 > p.yfull) {
-        W* grow = y + (int64_t)m * p.ldy;
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (nb + e >= p.yfull && nb + e < p.Nout) grow[nb + e] = v[e];
       }
     };
     // Without a tensor map: every epilogue thread parks its 8 outputs in
@@ -906,45 +970,58 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tr_encoder() {
   return fn;
 }
 
-// Tensor map of the output rows for the quarter-row tensor copies: the
-// rows as (128-byte pieces of EPR words) x (whole pieces per row) x (M
-// rows), box one quarter row (1024 outputs), 128-byte swizzle.  Taken only
-// when the base is 16-byte aligned and the row stride a multiple of 16
-// bytes (any stride for one row); otherwise a.ytma stays 0 and the threads
-// store.
+// Tensor maps of the output rows for the quarter-row tensor copies, one
+// per row class (rows of even index, rows of odd index): the class's rows
+// as (128-byte pieces of EPR words) x (whole pieces per row) x (rows of the
+// class, stride two rows), starting at the first 16-byte boundary of the
+// class's first row (yoff outputs in), box one quarter row (1024 outputs,
+// one piece fewer when yoff > 0), 128-byte swizzle.  Taken when every row
+// starts on an 8-byte boundary and two rows span a multiple of 16 bytes
+// (64-bit words: always, given an 8-byte aligned base; 32-bit words: an
+// even row stride); otherwise a.ytma stays 0 and the threads store.
 template <typename W>
-void tr_output_map(ConvArgs& a, CUtensorMap* tm) {
+void tr_output_maps(ConvArgs& a, CUtensorMap* tm) {
   constexpr int64_t EPR = 128 / (int64_t)sizeof(W);
   a.ytma = 0;
-  a.yfull = 0;
-  const int64_t pieces = a.Nout / EPR;
-  const uint64_t rs = (uint64_t)a.ldy * sizeof(W);
-  if (pieces < 1 || pieces > INT32_MAX / 2 || a.M < 1 ||
-      (reinterpret_cast<uintptr_t>(a.y) & 15) != 0 || (a.M > 1 && rs % 16 != 0))
-    return;
+  a.yoff[0] = a.yoff[1] = 0;
+  a.yfull[0] = a.yfull[1] = 0;
+  const uint64_t row = (uint64_t)a.ldy * sizeof(W);
+  const uintptr_t base = reinterpret_cast<uintptr_t>(a.y);
+  if (a.M < 1 || (base & 7) != 0 || (a.M > 1 && (2 * row) % 16 != 0)) return;
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tr_encoder();
   if (!enc) return;
-  const cuuint64_t dims[3] = {(cuuint64_t)EPR, (cuuint64_t)pieces, (cuuint64_t)a.M};
-  const cuuint64_t strides[2] = {128, a.M > 1 ? (cuuint64_t)rs : (cuuint64_t)pieces * 128};
-  const cuuint32_t box[3] = {(cuuint32_t)EPR, (cuuint32_t)(1024 / EPR), 1};
-  const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = enc(
-      tm, sizeof(W) == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
-      3, a.y, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return;
+  for (int c = 0; c < 2; ++c) {
+    const int64_t rows = (a.M - c + 1) / 2;
+    if (rows < 1) continue;
+    const uintptr_t start = base + (uintptr_t)c * row;
+    const int off = (int)(((16 - (start & 15)) & 15) / sizeof(W));
+    const int64_t pieces = (a.Nout - off) / EPR;
+    if (pieces < 1 || pieces > INT32_MAX / 2) return;
+    const cuuint64_t dims[3] = {(cuuint64_t)EPR, (cuuint64_t)pieces, (cuuint64_t)rows};
+    const cuuint64_t span = (cuuint64_t)pieces * 128;
+    const cuuint64_t strides[2] = {128, rows > 1 ? (cuuint64_t)(2 * row) : span};
+    const cuuint32_t box[3] = {(cuuint32_t)EPR,
+                               (cuuint32_t)(1024 / EPR - (off ? 1 : 0)), 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = enc(
+        &tm[c], sizeof(W) == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+        3, reinterpret_cast<void*>(start + off * sizeof(W)), dims, strides, box, es,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return;
+    a.yoff[c] = off;
+    a.yfull[c] = off + pieces * EPR;
+  }
   a.ytma = 1;
-  a.yfull = pieces * EPR;
 }
 
-template <typename W, bool PROT, int MM, int ND, int Q>
-int tr_launch_one(const ConvArgs& a0, cudaStream_t s) {
+template <typename W, bool PROT, int MM, int ND, int Q, int YS>
+int tr_launch_one(const ConvArgs& a, const CUtensorMap* tm, cudaStream_t s) {
   static std::once_flag once;
   static int attr = NE_OK;
   constexpr size_t smem = tr_smem_bytes<W, PROT, ND>();
   std::call_once(once, [] {
-    auto k = tcr_conv_kernel<W, PROT, MM, ND, Q>;
+    auto k = tcr_conv_kernel<W, PROT, MM, ND, Q, YS>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       attr = NE_ERR_CUDA;
@@ -953,43 +1030,43 @@ int tr_launch_one(const ConvArgs& a0, cudaStream_t s) {
     cudaGetLastError();
     return attr;
   }
-  ConvArgs a = a0;
-  alignas(64) CUtensorMap tm{};
-  tr_output_map<W>(a, &tm);
   const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)sm_count());
-  tcr_conv_kernel<W, PROT, MM, ND, Q><<<(unsigned)grid, TR_THREADS, smem, s>>>(a, tm);
+  tcr_conv_kernel<W, PROT, MM, ND, Q, YS>
+      <<<(unsigned)grid, TR_THREADS, smem, s>>>(a, tm[0], tm[1]);
   return cudaGetLastError() == cudaSuccess ? NE_OK : NE_ERR_CUDA;
 }
 
-template <typename W, bool PROT, int MM>
-int tr_launch_nd(const ConvArgs& a, cudaStream_t s) {
+template <typename W, bool PROT, int MM, int YS>
+int tr_launch_nd(const ConvArgs& a, const CUtensorMap* tm, cudaStream_t s) {
   if constexpr (PROT && MM == 4) {
     // l = 8 or 16 (M = 4 in 32- or 64-bit words): merged levels
     if (a.mlev == 1)
-      return a.nd == 1 ? tr_launch_one<W, PROT, MM, 1, 1>(a, s)
-                       : tr_launch_one<W, PROT, MM, 2, 1>(a, s);
-    if (a.mlev == 2 && a.nd == 2) return tr_launch_one<W, PROT, MM, 2, 2>(a, s);
+      return a.nd == 1 ? tr_launch_one<W, PROT, MM, 1, 1, YS>(a, tm, s)
+                       : tr_launch_one<W, PROT, MM, 2, 1, YS>(a, tm, s);
+    if (a.mlev == 2 && a.nd == 2) return tr_launch_one<W, PROT, MM, 2, 2, YS>(a, tm, s);
   }
   switch (a.nd) {
-    case 1: return tr_launch_one<W, PROT, MM, 1, 0>(a, s);
-    case 2: return tr_launch_one<W, PROT, MM, 2, 0>(a, s);
+    case 1: return tr_launch_one<W, PROT, MM, 1, 0, YS>(a, tm, s);
+    case 2: return tr_launch_one<W, PROT, MM, 2, 0, YS>(a, tm, s);
     default: break;
   }
   if constexpr (!PROT) {
-    if (a.nd == 3) return tr_launch_one<W, PROT, MM, 3, 0>(a, s);
-    if (a.nd == 4) return tr_launch_one<W, PROT, MM, 4, 0>(a, s);
+    if (a.nd == 3) return tr_launch_one<W, PROT, MM, 3, 0, YS>(a, tm, s);
+    if (a.nd == 4) return tr_launch_one<W, PROT, MM, 4, 0, YS>(a, tm, s);
   }
   return NE_ERR_UNSUPPORTED;
 }
 
-template <typename W>
-int tr_launch(const ConvArgs& a, bool prot, cudaStream_t s) {
-  if (!prot) return tr_launch_nd<W, false, 0>(a, s);
+// Every form of one word width and output-row alignment (YS); a carries
+// the output maps' fields (tr_output_maps) and tm the two maps.
+template <typename W, int YS>
+int tr_launch(const ConvArgs& a, const CUtensorMap* tm, bool prot, cudaStream_t s) {
+  if (!prot) return tr_launch_nd<W, false, 0, YS>(a, tm, s);
   switch (a.M) {
-    case 3: return tr_launch_nd<W, true, 3>(a, s);
-    case 4: return tr_launch_nd<W, true, 4>(a, s);
-    case 5: return tr_launch_nd<W, true, 5>(a, s);
-    case 6: return tr_launch_nd<W, true, 6>(a, s);
+    case 3: return tr_launch_nd<W, true, 3, YS>(a, tm, s);
+    case 4: return tr_launch_nd<W, true, 4, YS>(a, tm, s);
+    case 5: return tr_launch_nd<W, true, 5, YS>(a, tm, s);
+    case 6: return tr_launch_nd<W, true, 6, YS>(a, tm, s);
     default: return NE_ERR_UNSUPPORTED;
   }
 }

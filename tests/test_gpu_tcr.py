@@ -6,7 +6,8 @@ and 64-bit words, any live mask; the fused protected convolution
 (ne_protected_conv) for M = 3..6, one and two digits, the neighbour's levels
 apart and merged (M = 4: l = 8 and l = 16), every failure mode; ragged last
 tiles, inputs shorter than the history, rows that are not 16-byte aligned
-(staged from global memory), odd output strides, extreme operands and taps;
+(staged from global memory), output rows in every alignment (odd strides,
+bases 8 bytes past a 16-byte boundary), extreme operands and taps;
 and, at the benchmark's full size (M = 4, N = 2^22, K = 64), every output of
 every failure mode, with several tiles per block so that every ring wraps.
 The oracle side runs in independent output pieces on all host cores
@@ -150,6 +151,49 @@ def test_tcr_protected_every_failure(ne, orc, case):
         assert np.array_equal(host(d), plain), (fm, r)
         if padd:  # nothing written past the end of a row
             assert (dfull[:, Nout:] == 77).all(), (fm, r)
+
+
+LAYOUT = [
+    # w, M, N, K, data bits, extra columns after, columns before (output rows)
+    (64, 3, 3 * TILE + 12, 64, 15, 0, 0),    # odd stride: odd rows 8 bytes off
+    (64, 4, 2 * TILE + 300, 40, 15, 1, 1),   # base 8 bytes off, even stride
+    (64, 4, 3 * TILE + 1000, 64, 15, 0, 1),  # both classes 8 bytes off
+    (32, 3, 2 * TILE + 301, 16, 7, 2, 0),    # 32-bit, stride 2 mod 4
+    (32, 3, 2 * TILE + 301, 16, 7, 2, 2),    # 32-bit, base 8 bytes off
+    (32, 3, 2 * TILE + 301, 16, 7, 1, 0),    # 32-bit, odd stride: thread stores
+    (64, 3, 5, 3, 7, 1, 1),                  # rows shorter than one 128-byte piece
+]
+
+
+@pytest.mark.parametrize("case", LAYOUT)
+def test_tcr_output_row_layouts(ne, orc, case):
+    """Output rows in every alignment the tensor-copy output meets: rows of
+    even and odd index with their own maps, a class starting 8 bytes past a
+    16-byte boundary, and the thread stores where no map applies; plain and
+    protected (every failure mode), nothing written outside the rows."""
+    w, M, N, K, bc, after, before = case
+    gen = synth.rng(N + 3 * K + M + w + after + 5 * before)
+    c = synth.uniform_int(gen, (M, N), -(1 << bc), 1 << bc)
+    g = synth.uniform_int(gen, (K,), -(1 << bc) + 1, 1 << bc)
+    plain = conv_par(orc, c, g, w)
+    Nout = N + K - 1
+    cd = dev(c, w)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    rng_c = (-(1 << bc), (1 << bc) - 1)
+    buf = torch.full((M, before + Nout + after), 77, dtype=dt(w), device="cuda")
+    y = buf[:, before:before + Nout]
+    ne.ne_conv(cd, gd, y, x_range=rng_c, max_abs_g=(1 << bc) - 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), plain)
+    assert (buf[:, :before] == 77).all() and (buf[:, before + Nout:] == 77).all()
+    p = ne.ne_params(M, w)
+    for fm, r in modes(ne, M):
+        buf.fill_(77)
+        ne.ne_protected_conv(cd, gd, y, l=p.l, c_range=rng_c,
+                             max_abs_g=(1 << bc) - 1, failed=r, fail_mode=fm)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(y), plain), (fm, r)
+        assert (buf[:, :before] == 77).all() and (buf[:, before + Nout:] == 77).all()
 
 
 def test_tcr_protected_full_size_every_output(ne, orc):
