@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--impl", choices=["ne", "reference"], default="ne")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-pipeline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-paper-shapes", action="store_true")
     ap.add_argument("--no-gemm", action="store_true")
@@ -515,8 +516,9 @@ def run_ne(args):
     gemm = (None if args.no_gemm
             else bench_gemm(ne, dev, stream, probe["imad_wide"] / 1e12,
                             probe["wide_plus_imad32"] / 1e12))
+    pipeline = None if args.no_pipeline else bench_pipeline(ne, dev, stream)
     batch = None if args.no_batch else bench_batch(ne, synth, dev, stream)
-    served = None if args.no_serve else bench_serve(dev)
+    served = None if args.no_serve else bench_serve(ne, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(args.cpu_seconds)
@@ -546,6 +548,7 @@ def run_ne(args):
             "small": small,
             "paper_shapes": paper,
             "gemm": gemm,
+            "pipeline": pipeline,
             "batch": batch,
             "serve": served,
             "p99_ms_served": served["p99_ms"] if served else None,
@@ -585,8 +588,13 @@ def conv_sources_sha() -> str:
 
 
 def bench_small(ne, synth, dev, stream, reps=200):
-    """M=3 int32 streams, N=4096, K=16 (32-bit words): launch-latency bound;
-    microseconds per protected job through the fused call."""
+    """M=3 int32 streams, N=4096, K=16 (32-bit words): a job this small runs
+    on the multiply-add kernels (the tensor-core forms' set-up costs more
+    than the job).  Microseconds per protected job, back to back, through
+    the general call (ne_protected_conv: argument checks and conversions on
+    every call), through the prepared call (ne.ProtectedConvCall: arguments
+    converted once), and the GPU's own time per job (the prepared call
+    captured in a CUDA graph and replayed)."""
     import torch
     j = synth.small_job(seed=1)
     p = ne.ne_choose_width(j.M, j.K, j.bound_c, j.bound_g)
@@ -603,9 +611,132 @@ def bench_small(ne, synth, dev, stream, reps=200):
     for i in range(10):
         one(i)
     t, _ = timed(one, reps, 1, stream)
+    call = ne.ProtectedConvCall(c, g, d, l=p.l, c_range=j.c_range,
+                                max_abs_g=j.bound_g, ws=ws, stream=stream)
+
+    def prepared(i):
+        call(failed=i % j.M, fail_mode=ne.NE_FAIL_DROP)
+    for i in range(10):
+        prepared(i)
+    tp, _ = timed(prepared, reps, 1, stream)
+    # the GPU's time per job: one prepared call captured and replayed
+    side = torch.cuda.Stream(device=dev)
+    gcall = ne.ProtectedConvCall(c, g, d, l=p.l, c_range=j.c_range,
+                                 max_abs_g=j.bound_g, ws=ws, stream=side)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        gcall(failed=1, fail_mode=ne.NE_FAIL_DROP)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        gcall(failed=1, fail_mode=ne.NE_FAIL_DROP)
+    graph.replay()
+    torch.cuda.synchronize()
+    tg, _ = timed(lambda i: graph.replay(), reps, 1, stream)
     return {"workload": "M=3 int32 streams, N=4096, K=16, data/taps in "
                         "[-2^7,2^7), w=32 (l=11, k=10)",
-            "us_per_job": 1e3 * t / reps, "w": p.w}
+            "us_per_job": 1e3 * t / reps,
+            "us_per_job_prepared_call": 1e3 * tp / reps,
+            "gpu_us_per_job": 1e3 * tg / reps,
+            "form": "multiply-add kernels (small-job dispatch)", "w": p.w}
+
+
+def bench_pipeline(ne, dev, stream, reps=3):
+    """The mixed LSB pipeline on entangled streams (Eq. 2, Eq. 9): M=5
+    streams of N=2^24 ints in [-2^12, 2^12), entangle both sets, scale by a
+    seeded integer, add the second set, K=1024-tap convolution with the
+    failed stream not run, a seeded permutation of the output order, then
+    recovery of all M.  Seeded inputs made on the device.  Per step and for
+    the whole pipeline: milliseconds, and for the element-wise steps the
+    fraction of the measured copy bandwidth (algorithmic bytes: every word
+    read and written once); GOPS over the convolution's 2 M N K."""
+    import torch
+    M, N, K = 5, 1 << 24, 1024
+    Nout = N + K - 1
+    p = ne.ne_params(M, 64)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4)
+    b = 1 << 12
+    c0 = torch.empty((M, N), dtype=torch.int64, device=dev).random_(-b, b, generator=gen)
+    c20 = torch.empty((M, N), dtype=torch.int64, device=dev).random_(-b, b, generator=gen)
+    g = torch.empty(K, dtype=torch.int32, device=dev).random_(-b, b, generator=gen)
+    perm = torch.randperm(Nout, generator=gen, device=dev)
+    s_ = 77
+    failed = 3
+    c = torch.empty_like(c0)
+    c2 = torch.empty_like(c20)
+    delta = out_rows(M, Nout, dev)
+    moved = out_rows(M, Nout, dev)
+    live = ((1 << M) - 1) & ~(1 << failed)
+    wb = 8
+    steps = [
+        ("entangle", lambda: (ne.ne_entangle(c, l=p.l), ne.ne_entangle(c2, l=p.l)),
+         2 * 2 * M * N * wb),
+        ("scale", lambda: ne.ne_scale(c, s_), 2 * M * N * wb),
+        ("add", lambda: ne.ne_add(c, c2), 3 * M * N * wb),
+        ("conv", lambda: ne.ne_conv(c, g, delta, live_mask=live), None),
+        ("permute", lambda: ne.ne_permute(delta, perm, moved),
+         2 * M * Nout * wb + Nout * 8),
+        ("recover", lambda: ne.ne_recover(moved, moved, l=p.l, failed=failed),
+         (M - 1) * Nout * wb + M * Nout * wb),
+    ]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm = float(peaks["hbm_gbs"])
+
+    def reset():
+        c.copy_(c0)
+        c2.copy_(c20)
+
+    def whole():
+        for _, fn, _ in steps:
+            fn()
+    reset()
+    whole()
+    torch.cuda.synchronize()
+    per = {}
+    for name, fn, byts in steps:
+        tot = 0.0
+        for r in range(reps):
+            reset()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            # run the steps before this one untimed, then this one timed
+            for nm, f, _ in steps:
+                if nm == name:
+                    break
+                f()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / reps
+        rec = {"ms": ms}
+        if byts is not None:
+            rec["hbm_frac"] = byts / (ms * 1e-3) / 1e9 / hbm
+        per[name] = rec
+    tot = 0.0
+    for r in range(reps):
+        reset()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        whole()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / reps
+    ops = 2.0 * (M - 1) * N * K  # the failed stream's product is not run
+    return {"workload": "M=5 entangled streams, N=2^24, ints in [-2^12,2^12), "
+                        "scale, add, K=1024 conv, permutation, recovery of a "
+                        "failed stream (seeded, made on the device)",
+            "ms": ms, "gops": ops / (ms * 1e-3) / 1e9,
+            "conv_gops": ops / (per["conv"]["ms"] * 1e-3) / 1e9,
+            "steps": per, "hbm_peak_gbs": hbm,
+            "conv_form": "multiply-add kernels (K > 65: outside the "
+                         "tensor-core window)"}
 
 
 def bench_paper_shapes(ne, dev, stream, reps=5):
@@ -801,22 +932,77 @@ def bench_batch(ne, synth, dev, stream):
             "tuned": {"threads": threads, "blocks_per_sm": bps}}
 
 
-def bench_serve(dev, n_jobs=6000):
+def one_launch_per_job(ne, b, dev, seed, data_bits=15, tap_bits=15):
+    """The jobs of a serve spec run one fused call each, back to back on one
+    stream, each job's inputs made on the device just before its call (as
+    the serving loop does): jobs per second and GOPS."""
+    import torch
+    n = len(b)
+    M = b.M.astype(np.int64)
+    N = b.N.astype(np.int64)
+    K = b.K.astype(np.int64)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    cbuf = torch.empty(int(np.max(M * N)), dtype=torch.int64, device=dev)
+    dbuf = torch.empty(int(np.max(M * (N + K - 1))), dtype=torch.int64, device=dev)
+    gbuf = torch.empty(int(np.max(K)), dtype=torch.int32, device=dev)
+    ws = torch.empty(max(ne.ne_protected_conv_ws_bytes(int(M[i]), int(N[i]), int(K[i]))
+                         for i in range(n)), dtype=torch.uint8, device=dev)
+    lo_c, hi_c = -(1 << data_bits), 1 << data_bits
+    lo_g, hi_g = -(1 << tap_bits), 1 << tap_bits
+    lv = {m: ne.ne_params(int(m), 64).l for m in set(M.tolist())}
+
+    def job(i):
+        m, nn, k = int(M[i]), int(N[i]), int(K[i])
+        c = cbuf[:m * nn].view(m, nn).random_(lo_c, hi_c, generator=gen)
+        g = gbuf[:k].random_(lo_g, hi_g, generator=gen)
+        d = dbuf[:m * (nn + k - 1)].view(m, nn + k - 1)
+        f = int(b.failed[i])
+        ne.ne_protected_conv(c, g, d, l=lv[m], c_range=(lo_c, hi_c - 1),
+                             max_abs_g=-lo_g, failed=f,
+                             fail_mode=ne.NE_FAIL_DROP if f >= 0 else ne.NE_FAIL_NONE,
+                             ws=ws)
+    for i in range(min(n, 50)):
+        job(i)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(n):
+        job(i)
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) * 1e-3
+    return {"jobs_per_s": n / s, "gops": 2.0 * float(np.sum(M * N * K)) / s / 1e9,
+            "seconds": s}
+
+
+def bench_serve(ne, dev, n_jobs=6000):
     """Poisson arrivals at 20k jobs/s of protected convolutions (M in
     {3..6}, N log-uniform [2^12, 2^20], K in {16..512}, 16-bit data, 10 %
-    with an injected fail-stop) through the continuous-batching loop."""
+    with an injected fail-stop) through the continuous-batching loop; then
+    the same jobs all arriving at once (the loop's saturated throughput)
+    against one fused call per job, back to back."""
     from paper_1509_03838_gb300 import serve, synth
     spec = synth.serve_spec(seed=5, n_jobs=n_jobs)
     warm = synth.serve_spec(seed=6, n_jobs=300)
     serve.serve(warm, budget_bytes=8 << 30, streams=3, seed=1, device=dev)
     r = serve.serve(spec, budget_bytes=8 << 30, streams=3, seed=2, device=dev)
+    sat = synth.ServeSpec(arrival_s=np.zeros(n_jobs), batch=spec.batch,
+                          inject=spec.inject)
+    rs = serve.serve(sat, budget_bytes=8 << 30, streams=3, seed=3, device=dev)
+    one = one_launch_per_job(ne, spec.batch, dev, seed=3)
     return {"workload": f"{n_jobs} jobs, Poisson 20k jobs/s, M in {{3..6}}, N "
                         "log-uniform [2^12,2^20], K in {16..512}, 16-bit "
                         "data, 10% injected single-stream fail-stop",
             "p50_ms": r.p50_ms, "p99_ms": r.p99_ms,
             "jobs_per_s": r.jobs_per_s, "gops": r.gops, "batches": r.batches,
             "peak_device_bytes": r.peak_bytes, "budget_bytes": r.budget_bytes,
-            "offered_jobs_per_s": 20000.0}
+            "offered_jobs_per_s": 20000.0,
+            "saturated": {"jobs_per_s": rs.jobs_per_s, "gops": rs.gops,
+                          "batches": rs.batches, "p99_ms": rs.p99_ms},
+            "one_launch_per_job": one,
+            "saturated_vs_one_launch_per_job": rs.jobs_per_s / one["jobs_per_s"]}
 
 
 def main():

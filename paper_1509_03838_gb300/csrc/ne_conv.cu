@@ -891,6 +891,25 @@ inline bool tcr_enabled() {
   return !off;
 }
 
+// Whether a job is large enough for the tensor-core kernels.  Their fixed
+// cost (tensor-memory allocation, barrier and tap set-up in every block,
+// warp-specialised pipeline start) is about 16 us per launch, against about
+// 6 us for the multiply-add kernels; past that the tensor-core forms move
+// the job's bytes at about 3.2 TB/s (protected) or 4.4 TB/s (plain) and the
+// multiply-add kernels do about 6.1e12 multiply-adds per second (half that
+// when products need two instructions, split = true).  Estimated times, in
+// microseconds, measured on GB300; the cheaper estimate wins.
+std::atomic<int> g_debug_tc_always{0};  // ne_debug_set_dispatch
+inline bool tensor_cores_pay(int streams, int64_t N, int64_t Nout, int K, int wb,
+                             bool prot, bool split) {
+  if (g_debug_tc_always.load(std::memory_order_relaxed)) return true;
+  const double macs = (double)streams * (double)N * (double)K * (split ? 2.0 : 1.0);
+  const double bytes = (double)streams * (double)(N + Nout) * (double)wb;
+  const double imad_us = 6.0 + macs / 6.1e6;
+  const double tc_us = 16.0 + bytes / (prot ? 3.2e6 : 4.4e6);
+  return tc_us < imad_us;
+}
+
 // Byte digits for values in [lo, hi]: the least ND with hi - lo < 256^ND,
 // or 0 beyond four bytes.
 inline int tcr_digits(__int128 lo, __int128 hi) {
@@ -960,6 +979,14 @@ constexpr int kNotTaken = 1 << 30;
 int protected_tc(const ConvArgs& a, int mode, int64_t max_abs_g, int w,
                  bool vec, cudaStream_t s, int64_t c_min, int64_t c_max) {
   const ProtForm form = forced_form();
+  // small jobs: the multiply-add kernels finish before the tensor-core
+  // forms are set up (the entangled words need split products beyond 32
+  // bits)
+  const __int128 espan = ((__int128)c_max - (__int128)c_min) *
+                         (((__int128)1 << a.l) + 1);
+  if (form == FORM_AUTO &&
+      !tensor_cores_pay(a.M, a.N, a.Nout, a.K, w / 8, true, espan > 0xFFFFFFFF))
+    return kNotTaken;
   if (form == FORM_AUTO && a.M >= 3 && a.M <= 6) {
     // raw-plane tcgen05 kernel: products from the digit planes of the raw
     // rows, entangled in the accumulators, recovered in the epilogue
@@ -1081,7 +1108,9 @@ int ne_conv_range(const void* x, int64_t ldx, int M, int64_t N,
     a.ldy = ldy;
     a.live_mask = M == 32 ? live_mask : (live_mask & ((1u << M) - 1u));
     if (a.live_mask == 0) return NE_OK;
-    if (tcr_plan(a, false, w, (__int128)x_min, (__int128)x_max, max_abs_g,
+    if (tensor_cores_pay(__builtin_popcount(a.live_mask), N, Nout, K, wb, false,
+                         (__int128)x_max - (__int128)x_min > 0xFFFFFFFF) &&
+        tcr_plan(a, false, w, (__int128)x_min, (__int128)x_max, max_abs_g,
                  rows_aligned16(x, ldx, wb))) {
       const int st = dispatch_tcr(a, false, w, (cudaStream_t)stream);
       if (st != NE_ERR_UNSUPPORTED) return st;
@@ -1168,6 +1197,13 @@ int ne_debug_set_fault(int stall_role, uint32_t wait_polls) {
   if (stall_role < 0 || stall_role > 2) return NE_ERR_INVALID_ARG;
   g_debug_stall_role.store(stall_role);
   g_debug_wait_limit.store(wait_polls);
+  return NE_OK;
+}
+
+int ne_debug_set_dispatch(int tensor_cores_always) {
+  if (tensor_cores_always != 0 && tensor_cores_always != 1)
+    return NE_ERR_INVALID_ARG;
+  g_debug_tc_always.store(tensor_cores_always);
   return NE_OK;
 }
 

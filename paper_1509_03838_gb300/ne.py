@@ -133,6 +133,7 @@ _SIGS = {
                               _vp, _i64, ctypes.c_double, _u32,
                               ctypes.POINTER(_u32), _vp], _i32),
     "ne_debug_set_fault": ([_i32, _u32], _i32),
+    "ne_debug_set_dispatch": ([_i32], _i32),
     "ne_protected_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _i32, _i32, _i64,
                             _i64, _i64, _i32, _i32, _vp, _i64, _vp], _i32),
 }
@@ -425,6 +426,14 @@ class FailStop:
         return self.last_late
 
 
+def ne_debug_set_dispatch(tensor_cores_always: bool) -> None:
+    """Test control: take the tensor-core forms for every job in their
+    window (True), or let small jobs run on the multiply-add kernels (False,
+    the default)."""
+    _check(lib().ne_debug_set_dispatch(1 if tensor_cores_always else 0),
+           "ne_debug_set_dispatch")
+
+
 def ne_debug_set_fault(stall_role: int = 0, wait_polls: int = 0) -> None:
     """Test-only fault injection (include/ne_debug.h)."""
     _check(lib().ne_debug_set_fault(stall_role, wait_polls & 0xFFFFFFFF),
@@ -456,8 +465,8 @@ def ne_protected_conv(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
     n = n if N is None else N
     w = _word_bits(c)
     K = g.numel()
-    need = ne_protected_conv_ws_bytes(M, n, K)
-    if ws is None:
+    if ws is None:  # (a given ws is checked against the size by the library)
+        need = ne_protected_conv_ws_bytes(M, n, K)
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=c.device)
     _check(lib().ne_protected_conv(pc, ldc, M, n, ctypes.c_void_p(g.data_ptr()),
                                    K, w, l, int(c_range[0]),
@@ -467,6 +476,51 @@ def ne_protected_conv(c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
                                    ws.numel() * ws.element_size(),
                                    _stream(stream)), "ne_protected_conv")
     return d
+
+
+class ProtectedConvCall:
+    """ne_protected_conv with its arguments converted once: for a caller
+    that runs the same protected convolution (same buffers, shapes, ranges
+    and stream) many times, such as a small job in a loop, where the
+    per-call argument checks and conversions of ne_protected_conv would
+    cost more host time than the GPU spends on the job.  Each call changes
+    only the failure (failed, fail_mode) and issues one C-ABI call.  The
+    tensors must stay alive and in place while this object is used."""
+
+    def __init__(self, c: torch.Tensor, g: torch.Tensor, d: torch.Tensor, *,
+                 l: int, c_range: tuple[int, int], max_abs_g: int,
+                 ws: torch.Tensor | None = None, stream=None):
+        pc, M, n, ldc = _rows(c, "c")
+        pd, _, _, ldd = _rows(d, "d")
+        w = _word_bits(c)
+        if _word_bits(d) != w:
+            raise TypeError("c and d must have the same word type")
+        if g.dtype != torch.int32 or not g.is_cuda:
+            raise ValueError("taps g must be an int32 CUDA tensor")
+        K = g.numel()
+        need = ne_protected_conv_ws_bytes(M, n, K)
+        if ws is None:
+            ws = torch.empty(max(need, 1), dtype=torch.uint8, device=c.device)
+        self._keep = (c, g, d, ws)
+        self._fn = lib().ne_protected_conv
+        self._failed = ctypes.c_int32(-1)
+        self._mode = ctypes.c_int32(NE_FAIL_NONE)
+        self._args = (pc, ctypes.c_int64(ldc), ctypes.c_int32(M),
+                      ctypes.c_int64(n), ctypes.c_void_p(g.data_ptr()),
+                      ctypes.c_int32(K), ctypes.c_int32(w), ctypes.c_int32(l),
+                      ctypes.c_int64(int(c_range[0])),
+                      ctypes.c_int64(int(c_range[1])),
+                      ctypes.c_int64(int(max_abs_g)), self._failed, self._mode,
+                      pd, ctypes.c_int64(ldd), ctypes.c_void_p(ws.data_ptr()),
+                      ctypes.c_size_t(ws.numel() * ws.element_size()),
+                      _stream(stream))
+
+    def __call__(self, failed: int = -1, fail_mode: int = NE_FAIL_NONE) -> None:
+        self._failed.value = failed
+        self._mode.value = fail_mode
+        st = self._fn(*self._args)
+        if st != NE_OK:
+            raise NEError(st, "ne_protected_conv")
 
 
 NE_NOALLOC_MAX_NOUT = 100663296

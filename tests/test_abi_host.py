@@ -315,3 +315,6 @@ def test_failstop_and_debug_argument_checks(ne):
     for role in (-1, 3):
         assert L.ne_debug_set_fault(role, 0) == ne.NE_ERR_INVALID_ARG
     assert L.ne_debug_set_fault(0, 0) == ne.NE_OK
+    for v in (-1, 2):
+        assert L.ne_debug_set_dispatch(v) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_debug_set_dispatch(0) == ne.NE_OK

@@ -26,11 +26,15 @@ TILE = 4096  # outputs per stream per tile
 
 @pytest.fixture(scope="module")
 def ne():
+    """The library, with small jobs kept on the tensor-core forms (they
+    would otherwise run on the multiply-add kernels) for this module."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1509_03838_gb300 import build, ne as nemod
     build.build()
-    return nemod
+    nemod.ne_debug_set_dispatch(True)
+    yield nemod
+    nemod.ne_debug_set_dispatch(False)
 
 
 def dt(w):
