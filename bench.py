@@ -56,6 +56,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true")
+    ap.add_argument("--profile-case", default=None,
+                    help="run one kernel for a profiler instead of the bench "
+                         "(see run_profile_case)")
+    ap.add_argument("--reps", type=int, default=3,
+                    help="launches of --profile-case")
+    ap.add_argument("--N", type=int, default=1 << 22,
+                    help="samples per stream of --profile-case's default job")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-paper-shapes", action="store_true")
     ap.add_argument("--no-gemm", action="store_true")
@@ -284,6 +291,113 @@ def timed(fn, steps, world, stream, per_launch=False):
     return total, launches
 
 
+def probe_rate(kind, iters):
+    """(instructions per second, launch ms) of the instruction-rate probe
+    `kind` (include/ne_probe.h) from libne_probe.so, built beside libne.so
+    for these roofline denominators."""
+    import ctypes
+    from paper_1509_03838_gb300 import build
+    L = ctypes.CDLL(build.PROBE_LIB)
+    fn = L.ne_probe_imad_rate
+    fn.argtypes = [ctypes.c_int32, ctypes.c_int32,
+                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    fn.restype = ctypes.c_int32
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    st = fn(kind, iters, ctypes.byref(rate), ctypes.byref(ms))
+    if st != 0:
+        raise RuntimeError(f"ne_probe_imad_rate({kind}, {iters}): status {st}")
+    return rate.value, ms.value
+
+
+def run_profile_case(args):
+    """`--profile-case CASE`: run one kernel of the hot path `--reps` times on
+    seeded data, nothing timed, for a profiler's launch list or capture.
+    Default data: the benchmark's job (M = 4 streams of N = 2^22 samples, K =
+    64 taps, 16-bit data and taps, 64-bit words; --N changes N), output rows
+    with 16-byte strides.
+      protected     the fused protected conv (entangled products, stream 1
+                    dropped, recovery): the raw-plane tcgen05 kernel
+      conv_tc       plain conv, declared input and tap ranges (tcgen05)
+      conv_wide     plain conv, declared input range (multiply-add kernel)
+      conv_split    plain conv, undeclared range (split 64-bit products)
+      entangle      out-of-place entanglement
+      recover       recovery of all streams with stream 1 missing
+      checksum      checksum stream of the ABFT baseline
+      protected_m8  fused protected conv at the paper's M = 8, N = 10^6, K =
+                    1000 shape (data and taps in [-2^14, 2^14), no failure)
+      conv_m8       unprotected conv of the same data (declared range)
+      gemm_m8       stream-by-stream matrix product, M = 8 blocks of
+                    1000 x 1000 (data and kernel in [-2^14, 2^14))
+      gemm_prot_m8  the protected product of the same blocks (stream 3
+                    dropped)"""
+    import torch
+    from paper_1509_03838_gb300 import build, ne, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    case = args.profile_case
+    ops = {}
+    if case in ("protected", "conv_tc", "conv_wide", "conv_split", "entangle",
+                "recover", "checksum"):
+        j = synth.large_job(seed=2, N=args.N)
+        M, N, K = j.M, j.N, j.K
+        p = ne.ne_params(M, 64)
+        c = torch.from_numpy(j.c).to(dev)
+        g = torch.from_numpy(j.g.astype(np.int32)).to(dev)
+        d = out_rows(M, N + K - 1, dev)
+        ws = torch.empty(ne.ne_protected_conv_ws_bytes(M, N, K),
+                         dtype=torch.uint8, device=dev)
+        eps = torch.empty_like(c)
+        r = torch.empty(N, dtype=torch.int64, device=dev)
+        ops = {
+            "protected": lambda: ne.ne_protected_conv(
+                c, g, d, l=p.l, c_range=j.c_range, max_abs_g=j.bound_g,
+                failed=1, fail_mode=ne.NE_FAIL_DROP, ws=ws),
+            "conv_tc": lambda: ne.ne_conv(c, g, d, x_range=j.c_range,
+                                          max_abs_g=j.bound_g),
+            "conv_wide": lambda: ne.ne_conv(c, g, d, x_range=j.c_range),
+            "conv_split": lambda: ne.ne_conv(c, g, d),
+            "entangle": lambda: ne.ne_entangle(c, eps, l=p.l),
+            "recover": lambda: ne.ne_recover(d, d, l=p.l, failed=1),
+            "checksum": lambda: ne.ne_checksum(c, r),
+        }
+    elif case in ("protected_m8", "conv_m8"):
+        gen = synth.rng(8)
+        b8, M8, N8, K8 = 1 << 14, 8, 1_000_000, 1000
+        c8 = torch.from_numpy(synth.uniform_int(gen, (M8, N8), -b8, b8)).to(dev)
+        g8 = torch.from_numpy(
+            synth.uniform_int(gen, (K8,), -b8, b8).astype(np.int32)).to(dev)
+        d8 = out_rows(M8, N8 + K8 - 1, dev)
+        ws8 = torch.empty(ne.ne_protected_conv_ws_bytes(M8, N8, K8),
+                          dtype=torch.uint8, device=dev)
+        l8 = ne.ne_params(M8, 64).l
+        ops["protected_m8"] = lambda: ne.ne_protected_conv(
+            c8, g8, d8, l=l8, c_range=(-b8, b8 - 1), max_abs_g=b8, ws=ws8)
+        ops["conv_m8"] = lambda: ne.ne_conv(c8, g8, d8, x_range=(-b8, b8 - 1))
+    elif case in ("gemm_m8", "gemm_prot_m8"):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(21)
+        bg, Mg, Ng = 1 << 14, 8, 1000
+        cg = torch.empty((Mg, Ng, Ng), dtype=torch.int64, device=dev).random_(
+            -bg, bg, generator=gen)
+        gg = torch.empty((Ng, Ng), dtype=torch.int32, device=dev).random_(
+            -bg, bg, generator=gen)
+        dg = torch.empty((Mg, Ng, Ng), dtype=torch.int64, device=dev)
+        wsg = torch.empty(ne.ne_protected_gemm_ws_bytes(Mg, Ng, Ng, 64),
+                          dtype=torch.uint8, device=dev)
+        lg = ne.ne_params(Mg, 64).l
+        ops["gemm_m8"] = lambda: ne.ne_gemm(cg, gg, dg, x_range=(-bg, bg - 1))
+        ops["gemm_prot_m8"] = lambda: ne.ne_protected_gemm(
+            cg, gg, dg, l=lg, c_range=(-bg, bg - 1), max_abs_g=bg, failed=3,
+            fail_mode=ne.NE_FAIL_DROP, ws=wsg)
+    if case not in ops:
+        raise SystemExit(f"unknown profile case {case}")
+    for _ in range(args.reps):
+        ops[case]()
+    torch.cuda.synchronize()
+    print(f"{case}: {args.reps} launches ok")
+    return 0
+
+
 def out_rows(rows, n, dev):
     """Output rows of n int64 words whose stride is a multiple of 16 bytes
     (one spare word when n is odd), the layout whose rows the tensor-copy
@@ -404,7 +518,7 @@ def run_ne(args):
     probe = {}
     for kind, nm in [(0, "imad32"), (1, "imad_wide"), (2, "wide_plus_imad32"),
                      (5, "mma_sync_f16"), (6, "tcgen05_f16_n16")]:
-        rate, _ = ne.ne_probe_imad_rate(kind, 2048 if kind < 5 else 512)
+        rate, _ = probe_rate(kind, 2048 if kind < 5 else 512)
         probe[nm] = rate
     span = (j.c_range[1] - j.c_range[0]) * f_ent
     algo_bytes = float((M * N + M * Nout) * 8)
@@ -477,6 +591,7 @@ def run_ne(args):
                               "entangle-on-load + conv + cluster exchange + "
                               "recovery)",
                     "peak_source": "measured on this GPU by ne_probe_imad_rate "
+                                   "(libne_probe.so) "
                                    "(independent mad.wide.s32 chains, 8 per "
                                    "thread, 16 warps per scheduler)",
                     "launch_ms": prot_ms,
@@ -569,8 +684,12 @@ E2E_STREAMS = 4
 # committed sources (CONV_SOURCES, by hash); None until taken again after a
 # change of those sources.
 TRAFFIC_CAPTURE = {
-    "sources_sha256": None,
-    "bytes": None,
+    "sources_sha256":
+        "66deeabf8e7c1350ba6f1e6c1b3d78d4e0b0ef6c2491e59c6ca093de2059be17",
+    # tcr_conv_kernel<int64, 1, 4, 2, 2, 0>, second of three captured
+    # launches: 134553856 bytes read + 80557824 written (the rest of d is
+    # still in L2 when the launch ends), from ncu --set full on the bench job
+    "bytes": 134553856 + 80557824,
 }
 CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_conv_args.cuh",
                 "ne_conv_tcr.cuh", "ne_conv_tcr_w64.cu", "ne_tc5.cuh",
@@ -1007,6 +1126,8 @@ def bench_serve(ne, dev, n_jobs=6000):
 
 def main():
     args = parse()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ne(args)

@@ -1,7 +1,9 @@
 /*
- * ne_probe.h -- measurement utility of libne.so (not an operation of the
- * paper): the integer multiply-add throughput of the current GPU, which is
- * the denominator of the convolution's roofline.
+ * ne_probe.h -- measurement utility (not an operation of the paper), in a
+ * library of its own, libne_probe.so, built beside libne.so and loaded by
+ * the benchmark: the instruction throughput of the current GPU for the
+ * multiply-add and tensor-core instructions the convolution kernels use,
+ * the denominators of their rooflines.
  */
 #ifndef NE_PROBE_H_
 #define NE_PROBE_H_

@@ -20,8 +20,11 @@ LIB = os.path.join(HERE, "libne.so")
 
 SOURCES = ["ne_host.cpp", "ne_stream_ops.cu", "ne_conv.cu", "ne_conv_tcr_w32.cu",
            "ne_conv_tcr_w64.cu", "ne_conv_tcr_w32s.cu", "ne_conv_tcr_w64s.cu",
-           "ne_batch.cu", "ne_gemm.cu", "ne_pipe.cu", "ne_failstop.cu",
-           "ne_probe.cu"]
+           "ne_batch.cu", "ne_gemm.cu", "ne_pipe.cu", "ne_failstop.cu"]
+# the instruction-rate probe (include/ne_probe.h): a library of its own,
+# used by the benchmark for its roofline denominators
+PROBE_SOURCES = ["ne_probe.cu"]
+PROBE_LIB = os.path.join(HERE, "libne_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O3", f"-I{os.path.join(ROOT, 'include')}",
@@ -53,39 +56,46 @@ def _compile(nvcc: str, src: str, obj: str, extra: list[str]) -> None:
     os.replace(obj + ".tmp", obj)
 
 
+def _link(nvcc: str, lib: str, objs: list[str], force: bool) -> None:
+    if force or not os.path.exists(lib) or \
+            os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
+
+
 def build(force: bool = False, verbose: bool = False,
           extra_flags: list[str] | None = None) -> str:
-    """Compile every CUDA translation unit and link libne.so; returns its path."""
+    """Compile every CUDA translation unit, link libne.so and the probe's
+    libne_probe.so; returns libne.so's path."""
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     hdr = _headers_mtime()
     extra = list(extra_flags or [])
     jobs = []
-    objs = []
-    for name in SOURCES:
-        src = os.path.join(CSRC, name)
-        if not os.path.exists(src):
-            continue
-        obj = os.path.join(BUILD, name + ".o")
-        objs.append(obj)
-        if force or not os.path.exists(obj) or \
-                os.path.getmtime(obj) < max(os.path.getmtime(src), hdr):
-            jobs.append((src, obj))
+    objs = {LIB: [], PROBE_LIB: []}
+    for lib, names in ((LIB, SOURCES), (PROBE_LIB, PROBE_SOURCES)):
+        for name in names:
+            src = os.path.join(CSRC, name)
+            if not os.path.exists(src):
+                continue
+            obj = os.path.join(BUILD, name + ".o")
+            objs[lib].append(obj)
+            if force or not os.path.exists(obj) or \
+                    os.path.getmtime(obj) < max(os.path.getmtime(src), hdr):
+                jobs.append((src, obj))
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             futs = [ex.submit(_compile, nvcc, s, o, extra) for s, o in jobs]
             for f in futs:
                 f.result()
-    if force or jobs or not os.path.exists(LIB) or \
-            os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+    for lib in (LIB, PROBE_LIB):
+        _link(nvcc, lib, objs[lib], force or bool(jobs))
     if verbose:
-        print(f"built {LIB}")
+        print(f"built {LIB} and {PROBE_LIB}")
     return LIB
 
 

@@ -177,7 +177,11 @@ extern "C" int ne_probe_imad_rate(int kind, int iters, double* instr_per_s,
                                   double* elapsed_ms) {
   if (!instr_per_s || kind < 0 || kind > 6 || iters < 1)
     return NE_ERR_INVALID_ARG;
-  const int sms = sm_count();
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1)
+    return NE_ERR_CUDA;
   const int blocks = sms * 8;
   unsigned long long* sink = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -103,8 +103,6 @@ _SIGS = {
     "ne_self_entangle": ([_vp, _i64, _i32, _i32, _vp, _vp], _i32),
     "ne_permute": ([_vp, _i64, _i32, _i64, _vp, _i32, _vp, _i64, _vp, _vp],
                    _i32),
-    "ne_probe_imad_rate": ([_i32, _i32, ctypes.POINTER(ctypes.c_double),
-                            ctypes.POINTER(ctypes.c_double)], _i32),
     "ne_conv_range": ([_vp, _i64, _i32, _i64, _vp, _i32, _i64, _vp, _i64, _i32,
                        _i64, _i64, _u32, _vp], _i32),
     "ne_gemm": ([_vp, _i64, _i64, _i32, _i64, _i64, _vp, _i64, _i64, _vp,
@@ -628,15 +626,6 @@ def ne_permute(x: torch.Tensor, perm: torch.Tensor, y: torch.Tensor, *,
                             ctypes.c_void_p(bad.data_ptr() if bad is not None else 0),
                             _stream(stream)), "ne_permute")
     return y
-
-
-def ne_probe_imad_rate(kind: int, iters: int = 4096):
-    """(multiply-add instructions per second, launch ms) of probe `kind`."""
-    rate = ctypes.c_double()
-    ms = ctypes.c_double()
-    _check(lib().ne_probe_imad_rate(kind, iters, ctypes.byref(rate),
-                                    ctypes.byref(ms)), "ne_probe_imad_rate")
-    return rate.value, ms.value
 
 
 # ---------------------------------------------------------------------------

@@ -1,4 +1,5 @@
-"""libne.so loads, exports every symbol include/ne.h declares, and its
+"""libne.so loads, exports every symbol include/ne.h and include/ne_debug.h
+declare (the rate probe of include/ne_probe.h is libne_probe.so's), and its
 host-only logic (parameter rule, range checks, argument validation) behaves
 as the paper fixes.  No call here launches a kernel: argument errors are
 returned on the host before any CUDA call."""
@@ -21,9 +22,14 @@ def ne():
     return nemod
 
 
-def declared_symbols():
+PROBE_HEADER = os.path.join(ROOT, "include", "ne_probe.h")
+
+
+def declared_symbols(headers=None):
+    """ne_* functions the headers declare (default: every header but the
+    probe's, whose library is libne_probe.so)."""
     names = set()
-    for h in HEADERS:
+    for h in headers or [h for h in HEADERS if h != PROBE_HEADER]:
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(ne_\w+)\s*\(", text, re.M):
@@ -43,6 +49,15 @@ def test_library_exports_every_declared_symbol(ne):
     L = ctypes.CDLL(ne.LIB_PATH)
     missing = [n for n in declared_symbols() if not hasattr(L, n)]
     assert not missing, missing
+
+
+def test_probe_library_exports_its_symbols(ne):
+    from paper_1509_03838_gb300 import build
+    P = ctypes.CDLL(build.PROBE_LIB)
+    names = declared_symbols([PROBE_HEADER])
+    assert names and all(hasattr(P, n) for n in names)
+    L = ctypes.CDLL(ne.LIB_PATH)
+    assert not any(hasattr(L, n) for n in names)  # not in libne.so
 
 
 def test_binding_signatures_cover_header(ne):
@@ -128,9 +143,10 @@ def test_argument_errors_return_before_launch(ne):
 
 
 def test_probe_kind_and_iteration_checks(ne):
-    """The rate probe (kinds 0-6) rejects an unknown kind or no rounds
-    before it touches a GPU."""
-    L = ne.lib()
+    """The rate probe (kinds 0-6, in libne_probe.so) rejects an unknown kind
+    or no rounds before it touches a GPU."""
+    from probe_lib import probe_lib
+    L = probe_lib()
     rate, ms = ctypes.c_double(0), ctypes.c_double(0)
     for kind, iters in [(-1, 8), (7, 8), (6, 0), (0, -3)]:
         assert L.ne_probe_imad_rate(kind, iters, ctypes.byref(rate),

@@ -191,13 +191,12 @@ def test_protected_tc_extreme_taps(ne, orc):
 def test_tensor_core_rate_probes(ne):
     """The instruction-rate probes the roofline divides by: mma.sync
     m16n8k16 (kind 5) and tcgen05.mma M=128 N=16 K=16 (kind 6) both run to
-    completion with a plausible rate; the device error word stays clear (no
-    bounded wait expired)."""
-    r5, _ = ne.ne_probe_imad_rate(5, 64)
-    r6, ms6 = ne.ne_probe_imad_rate(6, 64)
+    completion with a plausible rate (libne_probe.so)."""
+    from probe_lib import probe_rate
+    r5, _ = probe_rate(5, 64)
+    r6, ms6 = probe_rate(6, 64)
     assert 1e10 < r5 < 1e13
     assert 1e9 < r6 < 1e12 and ms6 > 0
-    assert ne.ne_get_device_error(clear=True) == 0
 
 
 def _child_run(env_extra, select):
