@@ -20,6 +20,7 @@ LIB = os.path.join(HERE, "libne.so")
 
 SOURCES = ["ne_host.cpp", "ne_stream_ops.cu", "ne_conv.cu", "ne_conv_tcr_w32.cu",
            "ne_conv_tcr_w64.cu", "ne_conv_tcr_w32s.cu", "ne_conv_tcr_w64s.cu",
+           "ne_conv_tcr_w32l.cu", "ne_conv_tcr_w64l.cu",
            "ne_batch.cu", "ne_gemm.cu", "ne_pipe.cu", "ne_failstop.cu"]
 # the instruction-rate probe (include/ne_probe.h): a library of its own,
 # used by the benchmark for its roofline denominators

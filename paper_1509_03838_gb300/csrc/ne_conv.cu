@@ -895,18 +895,24 @@ inline bool tcr_enabled() {
 // cost (tensor-memory allocation, barrier and tap set-up in every block,
 // warp-specialised pipeline start) is about 16 us per launch, against about
 // 6 us for the multiply-add kernels; past that the tensor-core forms move
-// the job's bytes at about 3.2 TB/s (protected) or 4.4 TB/s (plain) and the
-// multiply-add kernels do about 6.1e12 multiply-adds per second (half that
-// when products need two instructions, split = true).  Estimated times, in
-// microseconds, measured on GB300; the cheaper estimate wins.
+// the job's bytes at about 3.2 TB/s (protected) or 4.4 TB/s (plain), or,
+// with many taps, issue their products at about one per 25 ns per SM (the
+// slower of the two), and the multiply-add kernels do about 6.1e12
+// multiply-adds per second (half that when products need two
+// instructions, split = true).  Estimated times, in microseconds, measured
+// on GB300; the cheaper estimate wins.  nd: byte digits of the operands.
 std::atomic<int> g_debug_tc_always{0};  // ne_debug_set_dispatch
 inline bool tensor_cores_pay(int streams, int64_t N, int64_t Nout, int K, int wb,
-                             bool prot, bool split) {
+                             bool prot, bool split, int nd) {
   if (g_debug_tc_always.load(std::memory_order_relaxed)) return true;
   const double macs = (double)streams * (double)N * (double)K * (split ? 2.0 : 1.0);
   const double bytes = (double)streams * (double)(N + Nout) * (double)wb;
   const double imad_us = 6.0 + macs / 6.1e6;
-  const double tc_us = 16.0 + bytes / (prot ? 3.2e6 : 4.4e6);
+  const double ks = (double)((32 + 16 * ((K - 1 + 15) / 16)) / 16);
+  const double mmas = (double)streams * (double)((Nout + 4095) / 4096) * ks *
+                      (double)(nd > 0 ? nd : 4) * (prot ? 2.0 : 1.0);
+  const double tc_us = 16.0 + std::max(bytes / (prot ? 3.2e6 : 4.4e6),
+                                       mmas * 0.025 / 152.0);
   return tc_us < imad_us;
 }
 
@@ -925,14 +931,18 @@ std::atomic<int> g_debug_stall_role{0};
 
 // Fill the raw-plane fields of a for inputs in [lo, hi] (known range):
 // returns false if the job is outside these kernels' window.
+// allow_lk: the large-K form (66 <= K <= 1025, its B table in a.btab) may
+// be taken.
 inline bool tcr_plan(ConvArgs& a, bool prot, int w, __int128 lo, __int128 hi,
-                     int64_t max_abs_g, bool vec) {
-  if (!tc_enabled() || !tcr_enabled() || a.K > TR_HMAX + 1 || max_abs_g < 0 ||
-      max_abs_g > TC_MAX_G || (prot && (a.M < 3 || a.M > 6)))
+                     int64_t max_abs_g, bool vec, bool allow_lk) {
+  const bool lk = a.K > TR_HMAX + 1;
+  if (!tc_enabled() || !tcr_enabled() || a.K > (allow_lk ? TR_HMAX_L : TR_HMAX) + 1 ||
+      max_abs_g < 0 || max_abs_g > TC_MAX_G || (prot && (a.M < 3 || a.M > 6)))
     return false;
   const int nd = tcr_digits(lo, hi);
-  if (nd == 0 || (prot && nd > 2)) return false;
+  if (nd == 0 || (prot && nd > 2) || (lk && nd > 3)) return false;
   a.nd = nd;
+  a.lk = lk ? 1 : 0;
   a.hist = 16 * ((a.K - 1 + 15) / 16);
   a.ks = (TR_P + a.hist) / 16;
   // protected, l = 8 q with q <= nd (M = 4 only): the neighbour's levels
@@ -940,7 +950,7 @@ inline bool tcr_plan(ConvArgs& a, bool prot, int w, __int128 lo, __int128 hi,
   // most P products per tap (P = own pairs + neighbour pairs at that
   // level), exact while P K 2^14 <= 2^22
   a.mlev = 0;
-  if (prot && a.M == 4 && a.l % 8 == 0 && a.l / 8 >= 1 && a.l / 8 <= nd) {
+  if (!lk && prot && a.M == 4 && a.l % 8 == 0 && a.l / 8 >= 1 && a.l / 8 <= nd) {
     const int q = a.l / 8;
     int pmax = 0;
     for (int L = 0; L <= nd + q; ++L) {
@@ -977,7 +987,8 @@ int dispatch_tcr(const ConvArgs& a, bool prot, int w, cudaStream_t s) {
 // |g| > 2^15) or another form is forced.
 constexpr int kNotTaken = 1 << 30;
 int protected_tc(const ConvArgs& a, int mode, int64_t max_abs_g, int w,
-                 bool vec, cudaStream_t s, int64_t c_min, int64_t c_max) {
+                 bool vec, cudaStream_t s, int64_t c_min, int64_t c_max,
+                 bool allow_lk) {
   const ProtForm form = forced_form();
   // small jobs: the multiply-add kernels finish before the tensor-core
   // forms are set up (the entangled words need split products beyond 32
@@ -985,13 +996,15 @@ int protected_tc(const ConvArgs& a, int mode, int64_t max_abs_g, int w,
   const __int128 espan = ((__int128)c_max - (__int128)c_min) *
                          (((__int128)1 << a.l) + 1);
   if (form == FORM_AUTO &&
-      !tensor_cores_pay(a.M, a.N, a.Nout, a.K, w / 8, true, espan > 0xFFFFFFFF))
+      !tensor_cores_pay(a.M, a.N, a.Nout, a.K, w / 8, true, espan > 0xFFFFFFFF,
+                        tcr_digits((__int128)c_min, (__int128)c_max)))
     return kNotTaken;
   if (form == FORM_AUTO && a.M >= 3 && a.M <= 6) {
     // raw-plane tcgen05 kernel: products from the digit planes of the raw
     // rows, entangled in the accumulators, recovered in the epilogue
     ConvArgs t = a;
-    if (tcr_plan(t, true, w, (__int128)c_min, (__int128)c_max, max_abs_g, vec)) {
+    if (tcr_plan(t, true, w, (__int128)c_min, (__int128)c_max, max_abs_g, vec,
+                 allow_lk && a.btab != nullptr)) {
       const int st = dispatch_tcr(t, true, w, s);
       if (st != NE_ERR_UNSUPPORTED) return st;
     }
@@ -1089,7 +1102,7 @@ int ne_conv_range(const void* x, int64_t ldx, int M, int64_t N,
                   uint32_t live_mask, void* stream) {
   if (max_abs_g < 0) return NE_ERR_INVALID_ARG;
   if (x_min <= x_max && (w == 32 || w == 64) && M >= 1 && M <= 32 && N > 0 &&
-      K >= 1 && K <= TR_HMAX + 1 && ldx >= N && x && y && g &&
+      K >= 1 && K <= TR_HMAX_L + 1 && ldx >= N && x && y && g &&
       ldy >= N + K - 1) {
     // raw-plane tcgen05 kernel, when the declared ranges allow it
     const int wb = w / 8;
@@ -1109,11 +1122,26 @@ int ne_conv_range(const void* x, int64_t ldx, int M, int64_t N,
     a.live_mask = M == 32 ? live_mask : (live_mask & ((1u << M) - 1u));
     if (a.live_mask == 0) return NE_OK;
     if (tensor_cores_pay(__builtin_popcount(a.live_mask), N, Nout, K, wb, false,
-                         (__int128)x_max - (__int128)x_min > 0xFFFFFFFF) &&
+                         (__int128)x_max - (__int128)x_min > 0xFFFFFFFF,
+                         tcr_digits((__int128)x_min, (__int128)x_max)) &&
         tcr_plan(a, false, w, (__int128)x_min, (__int128)x_max, max_abs_g,
-                 rows_aligned16(x, ldx, wb))) {
-      const int st = dispatch_tcr(a, false, w, (cudaStream_t)stream);
+                 rows_aligned16(x, ldx, wb), true)) {
+      // the large-K form's B table comes from the stream-ordered pool and
+      // returns to it after the launch, in stream order
+      void* tab = nullptr;
+      cudaStream_t s = (cudaStream_t)stream;
+      if (a.lk) {
+        if (cudaMallocAsync(&tab, tr_table_bytes(K), s) != cudaSuccess) {
+          cudaGetLastError();
+          tab = nullptr;
+        }
+        a.btab = tab;
+      }
+      const int st = a.lk && !tab ? NE_ERR_UNSUPPORTED : dispatch_tcr(a, false, w, s);
+      if (tab) cudaFreeAsync(tab, s);
       if (st != NE_ERR_UNSUPPORTED) return st;
+      a.lk = 0;
+      a.btab = nullptr;
     }
   }
   long long bias = 0;
@@ -1207,11 +1235,21 @@ int ne_debug_set_dispatch(int tensor_cores_always) {
   return NE_OK;
 }
 
+// Workspace of ne_protected_conv: the multiply-add form's per-tile arrival
+// words, then (66 <= K <= 1025) the large-K tensor-core form's B table at
+// the next 256-byte boundary.
+inline size_t arrival_ws_bytes(int64_t N, int K) {
+  const int64_t ntiles = (N + K - 1 + CONV_TILE - 1) / CONV_TILE;
+  return (size_t)ntiles * 2 * sizeof(uint32_t);
+}
+inline size_t table_ws_bytes(int K) {
+  return K > TR_HMAX + 1 && K <= TR_HMAX_L + 1 ? tr_table_bytes(K) + 256 : 0;
+}
+
 size_t ne_protected_conv_ws_bytes(int M, int64_t N, int K) {
   (void)M;
   if (N <= 0 || K <= 0) return 0;
-  const int64_t ntiles = (N + K - 1 + CONV_TILE - 1) / CONV_TILE;
-  return (size_t)ntiles * 2 * sizeof(uint32_t);
+  return arrival_ws_bytes(N, K) + table_ws_bytes(K);
 }
 
 int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
@@ -1268,13 +1306,18 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   a.wait_limit = g_debug_wait_limit.load();
   a.stall_role = g_debug_stall_role.load();
   a.ws = (uint32_t*)ws;
+  // the large-K B table after the arrival words, 256-byte aligned
+  const size_t arrival = arrival_ws_bytes(N, K);
+  if (table_ws_bytes(K) > 0)
+    a.btab = reinterpret_cast<void*>(
+        (reinterpret_cast<uintptr_t>(ws) + arrival + 255) & ~(uintptr_t)255);
   // eps = c_m + 2^l c_{m-1} is increasing in both inputs, so it lies in
   // [c_min (2^l + 1), c_max (2^l + 1)]
   const __int128 f = ((__int128)1 << l) + 1;
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
-  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s, c_min, c_max);
+  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s, c_min, c_max, true);
   if (tc != kNotTaken) return tc;
   if (use_cluster(M, K, w, mode, a.ntiles)) {
     if (dispatch_cluster(a, w, mode, vec, s) == NE_OK) return NE_OK;
@@ -1282,7 +1325,7 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
     // and take the arrival-word form
     cudaGetLastError();
   }
-  if (cudaMemsetAsync(ws, 0, need_ws, s) != cudaSuccess) return NE_ERR_CUDA;
+  if (cudaMemsetAsync(ws, 0, arrival, s) != cudaSuccess) return NE_ERR_CUDA;
   return dispatch_conv<true>(a, w, mode, vec, s);
 }
 
@@ -1385,8 +1428,9 @@ extern "C" int ne_protected_conv_noalloc(const void* c, int64_t ldc, int M,
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
-  // the tensor-core forms need no arrival words
-  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s, c_min, c_max);
+  // the tensor-core forms need no arrival words (the large-K form, which
+  // needs a table, is not taken here)
+  const int tc = protected_tc(a, mode, max_abs_g, w, vec, s, c_min, c_max, false);
   if (tc != kNotTaken) return tc;
   // the fixed array covers NE_NOALLOC_MAX_NOUT output samples per stream
   if (Nout > NE_NOALLOC_MAX_NOUT) return NE_ERR_NOMEM;

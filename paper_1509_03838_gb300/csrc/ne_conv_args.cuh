@@ -34,6 +34,9 @@ struct ConvArgs {
                        // in the stream's own levels (l = 8 mlev), 0: apart
   int vec;             // rows of x 16-byte aligned
   unsigned long long corr_mul;  // range-shift correction per unit tap sum
+  int lk;              // the large-K form (66 <= K <= 1025)
+  const void* btab;    // large K: the taps' B table, tr_table_bytes(K)
+                       // bytes, 16-byte aligned (filled by the launch)
   int ytma;            // output rows stored by tensor copies (two tensor
                        // maps passed beside the arguments, rows of even and
                        // of odd index), else by the threads
@@ -50,6 +53,13 @@ struct ConvArgs {
 constexpr int TR_P = 32;
 constexpr int TR_TILE = 128 * TR_P;
 constexpr int TR_HMAX = 64;
+// The large-K form (66 <= K <= 1025): history up to 1024 samples; its B
+// table (tr_table_bytes) lies in global memory.
+constexpr int TR_HMAX_L = 1024;
+inline size_t tr_table_bytes(int K) {
+  const int hist = 16 * ((K - 1 + 15) / 16);
+  return (size_t)((TR_P + hist) / 16) * 2048;
+}
 
 // Launch the raw-plane kernel for a planned job (ConvArgs fields nd, hist,
 // ks, tcols, tslots, vec, corr_mul filled; M, nd within the instantiated
@@ -62,10 +72,15 @@ int tcr_launch_w64(const ConvArgs& a, bool prot, cudaStream_t s);
 // two CUtensorMaps).
 int tcr_launch_w32s(const ConvArgs& a, const void* tm, bool prot, cudaStream_t s);
 int tcr_launch_w64s(const ConvArgs& a, const void* tm, bool prot, cudaStream_t s);
+// The large-K forms (a.lk set, a.btab given).
+int tcr_launch_w32l(const ConvArgs& a, const void* tm, bool prot, cudaStream_t s);
+int tcr_launch_w64l(const ConvArgs& a, const void* tm, bool prot, cudaStream_t s);
 // Host readers of those translation units' device error words.
 unsigned tcr_w32_device_error(bool clear);
 unsigned tcr_w64_device_error(bool clear);
 unsigned tcr_w32s_device_error(bool clear);
 unsigned tcr_w64s_device_error(bool clear);
+unsigned tcr_w32l_device_error(bool clear);
+unsigned tcr_w64l_device_error(bool clear);
 
 }  // namespace ne

@@ -103,6 +103,24 @@ constexpr int TR_WMMA = 23;                     // MMA warp (owns tensor memory)
 constexpr int TR_EPI = 512;                     // epilogue threads
 constexpr uint32_t TR_MAGIC = 0x4B400000u;      // bits of 1.5 * 2^23
 constexpr int TR_TAPS = 96;                     // taps kept (K <= 65)
+// large-K form (66 <= K <= 1025): history up to 1024 samples, the taps'
+// B blocks streamed through a ring, products drained in groups of k-steps
+constexpr int TR_TAPS_L = TR_HMAX_L + 32;       // taps kept (K <= 1025)
+// (the prefix sums run over the taps 32 at a time)
+static_assert(TR_TAPS % 32 == 0 && TR_TAPS_L % 32 == 0, "tap arrays in warps");
+constexpr int TR_NBR = 16;                      // B blocks in the ring
+constexpr int TR_GROUP = 32;                    // k-steps per accumulator group
+
+// Geometry of a form: history, staged samples per row, bytes per chunk
+// column and per digit plane.
+template <bool LK>
+__host__ __device__ constexpr int tr_hmax() { return LK ? TR_HMAX_L : TR_HMAX; }
+template <bool LK>
+__host__ __device__ constexpr int tr_smax() { return TR_TILE + tr_hmax<LK>(); }
+template <bool LK>
+__host__ __device__ constexpr int tr_lbo() { return (128 + tr_hmax<LK>() / TR_P) * 16; }
+template <bool LK>
+__host__ __device__ constexpr int tr_plane() { return 4 * tr_lbo<LK>(); }
 
 // raw-row slots (three while the plane ring leaves room, else two) and
 // digit-plane row slots (four, three with four digits)
@@ -110,6 +128,7 @@ __host__ __device__ constexpr int tr_nraw(int nd) { return nd <= 2 ? 3 : 2; }
 __host__ __device__ constexpr int tr_nrs(int nd) { return nd <= 3 ? 4 : 3; }
 
 struct TrBars {
+  uint64_t b_full[TR_NBR], b_empty[TR_NBR];  // large K: the B ring
   uint64_t raw_full[3], raw_empty[3];
   uint64_t rs_full[4], rs_empty[4];
   uint64_t head_full[2], head_empty[2];  // protected: the tile's first row
@@ -120,27 +139,42 @@ struct TrBars {
   int live_rows[32];  // plain form: the live streams in order
 };
 
-struct TrTaps {
-  int taps[TR_TAPS];
-  long long pref[TR_TAPS];
+template <int NT>
+struct TrTapsT {
+  int taps[NT];
+  long long pref[NT];
   long long total;
 };
+template <bool LK>
+using TrTaps = TrTapsT<LK ? TR_TAPS_L : TR_TAPS>;
 
 // Raw-row slots of a form: the protected form keeps two (its plane ring has
 // two more slots, the head slots below), the plain form three while the
-// plane ring leaves room.
-template <bool PROT>
+// plane ring leaves room; the large-K form two.
+template <bool PROT, bool LK>
 __host__ __device__ constexpr int tr_nraw_form(int nd) {
-  return PROT ? 2 : tr_nraw(nd);
+  return LK ? 2 : (PROT ? 2 : tr_nraw(nd));
 }
-// Dynamic shared memory: plane ring (+ two head slots, protected), raw
-// ring, output tile (1024-byte aligned), B, taps, barriers.
-template <typename W, bool PROT, int ND>
+// Plane-ring slots and head slots of a form (the large-K form's planes are
+// 2.5 times larger: two ring slots, one head slot).
+template <bool PROT, bool LK>
+__host__ __device__ constexpr int tr_nrs_form(int nd) {
+  return LK ? 2 : tr_nrs(nd);
+}
+template <bool PROT, bool LK>
+__host__ __device__ constexpr int tr_nhead() {
+  return PROT ? (LK ? 1 : 2) : 0;
+}
+// Dynamic shared memory: plane ring (+ head slots, protected), raw ring,
+// output tile (1024-byte aligned), B (resident, or the large-K ring), taps,
+// barriers.
+template <typename W, bool PROT, int ND, bool LK>
 __host__ __device__ constexpr size_t tr_smem_bytes() {
-  return (size_t)(tr_nrs(ND) + (PROT ? 2 : 0)) * ND * TR_PLANE +
-         (size_t)tr_nraw_form<PROT>(ND) * TR_SMAX * sizeof(W) +
-         TR_TILE * sizeof(W) + 1024 + TR_BBYTES + sizeof(TrTaps) + sizeof(TrBars) +
-         256;
+  return (size_t)(tr_nrs_form<PROT, LK>(ND) + tr_nhead<PROT, LK>()) * ND *
+             tr_plane<LK>() +
+         (size_t)tr_nraw_form<PROT, LK>(ND) * tr_smax<LK>() * sizeof(W) +
+         TR_TILE * sizeof(W) + 1024 + (LK ? TR_NBR * TR_BS : TR_BBYTES) +
+         sizeof(TrTaps<LK>) + sizeof(TrBars) + 256;
 }
 
 // try_wait with a suspend-time hint: the thread sleeps until the phase
@@ -243,6 +277,23 @@ __device__ __forceinline__ void tr_ld8(uint32_t taddr, uint32_t (&r)[8]) {
       : "r"(taddr));
 }
 
+// Zeros into this warp's 32 lanes x 8 consecutive columns from taddr, and
+// the wait for this thread's tensor-memory stores.
+__device__ __forceinline__ void tr_st8_zero(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};"
+      ::"r"(taddr), "r"(0u)
+      : "memory");
+}
+__device__ __forceinline__ void tr_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// An fp32 accumulator holding an integer of magnitude at most 2^24 (the
+// large-K groups), converted exactly.
+__device__ __forceinline__ int tr_f2i(uint32_t bits) {
+  return __float2int_rn(__uint_as_float(bits));
+}
+
 // Tensor copy of a box of the output (x, y, z) from shared memory, in the
 // issuing thread's bulk group; commit, and the waits for the groups'
 // shared-memory reads or full completion.
@@ -304,28 +355,33 @@ __device__ __forceinline__ void tr_issue_set(uint32_t dc, uint32_t pa,
 // 1 when a row class starts 8 bytes past one (its outputs shifted by 8
 // bytes in the output tile).
 // ---------------------------------------------------------------------------
-template <typename W, bool PROT, int MM, int ND, int Q, int YS>
+template <typename W, bool PROT, int MM, int ND, int Q, int YS, bool LK>
 __global__ void __launch_bounds__(TR_THREADS, 1)
     tcr_conv_kernel(const ConvArgs p, const __grid_constant__ CUtensorMap ytm0,
                     const __grid_constant__ CUtensorMap ytm1) {
   extern __shared__ __align__(128) int4 tr_dyn[];
-  constexpr int NRAW = tr_nraw_form<PROT>(ND);
-  constexpr int TR_NRS = tr_nrs(ND);
-  constexpr int NHEAD = PROT ? 2 : 0;
+  constexpr int NRAW = tr_nraw_form<PROT, LK>(ND);
+  constexpr int TR_NRS = tr_nrs_form<PROT, LK>(ND);
+  constexpr int NHEAD = tr_nhead<PROT, LK>();
+  constexpr int SMAXk = tr_smax<LK>();            // staged samples per raw slot
+  constexpr int LBOk = tr_lbo<LK>();              // bytes per chunk column
+  constexpr int PLANEk = tr_plane<LK>();          // bytes per digit plane
+  constexpr int BBYTESk = LK ? TR_NBR * TR_BS : TR_BBYTES;
+  constexpr int NTAPS = LK ? TR_TAPS_L : TR_TAPS;
   constexpr int NLEV = ND + 1;                    // levels per plane set
   constexpr int NLM = ND + Q + 1;                 // merged levels (Q > 0)
   const int H = p.hist, KS = p.ks;
   const int S = TR_TILE + H;                      // staged samples per row
   const int tcols = p.tcols, tslots = p.tslots;   // tensor-memory slots
   unsigned char* planes = reinterpret_cast<unsigned char*>(tr_dyn);
-  W* raw = reinterpret_cast<W*>(planes + (size_t)(TR_NRS + NHEAD) * ND * TR_PLANE);
+  W* raw = reinterpret_cast<W*>(planes + (size_t)(TR_NRS + NHEAD) * ND * PLANEk);
   // one output row of a tile, swizzled; four quarters of 1024 outputs, one
   // per tensor-memory lane quadrant, in the tensor-copy layout
   W* otile = reinterpret_cast<W*>(
-      (reinterpret_cast<uintptr_t>(raw + NRAW * TR_SMAX) + 1023) & ~(uintptr_t)1023);
+      (reinterpret_cast<uintptr_t>(raw + NRAW * SMAXk) + 1023) & ~(uintptr_t)1023);
   unsigned char* bmat = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(otile + TR_TILE) + 127) & ~(uintptr_t)127);
-  TrTaps& tt = *reinterpret_cast<TrTaps*>(bmat + TR_BBYTES);
+  TrTaps<LK>& tt = *reinterpret_cast<TrTaps<LK>*>(bmat + BBYTESk);
   TrBars& bars = *reinterpret_cast<TrBars*>(
       (reinterpret_cast<uintptr_t>(&tt + 1) + 7) & ~(uintptr_t)7);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -364,9 +420,10 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
   };
   auto slot_of = [&](int i, uint32_t rc0, int j) -> PSlot {
     if (head && j == 0) {
-      const int h = i & 1;
+      // two head slots alternate by tile; one (large K) serves every tile
+      const int h = NHEAD == 2 ? (i & 1) : 0;
       return {TR_NRS + h, &bars.head_full[h], &bars.head_empty[h],
-              (uint32_t)(i >> 1) & 1u};
+              (uint32_t)(NHEAD == 2 ? (i >> 1) : i) & 1u};
     }
     const uint32_t k = rc0 + (uint32_t)(head ? j - 1 : j);
     return {(int)(k % TR_NRS), &bars.rs_full[k % TR_NRS],
@@ -392,6 +449,10 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
       mbar_init(&bars.acc_full[s], 1);    // tcgen05.commit
       mbar_init(&bars.acc_empty[s], 16);  // one arrival per epilogue warp
     }
+    for (int s = 0; s < TR_NBR; ++s) {
+      mbar_init(&bars.b_full[s], 1);      // expect_tx of the block's bytes
+      mbar_init(&bars.b_empty[s], 1);     // tcgen05.commit
+    }
     mbar_init(&bars.drain, 1);
     bars.abort = 0;
     if (!PROT) {
@@ -406,15 +467,18 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
   __syncthreads();
   t5_fence_after();
   if (warp != TR_WLOAD) {
-    for (int t = threadIdx.x; t < TR_TAPS; t += TR_THREADS)
+    // every thread but the loader warp's (which is already copying): the
+    // taps, zero past K
+    const int tid = threadIdx.x < TR_WLOAD * 32 ? threadIdx.x : threadIdx.x - 32;
+    for (int t = tid; t < NTAPS; t += TR_THREADS - 32)
       tt.taps[t] = t < p.K ? __ldg(p.g + t) : 0;
     tr_bar<3, TR_THREADS - 32>();
     // B, K-major without swizzling: element (n, kk) of k-step s at
     // 256 (n / 8) + 16 (n % 8) + 128 (kk / 8) + 2 (kk % 8) of its block; the
     // block of k-step 0 has 256 rows, rows n >= 64 zero (the clearing
     // instruction spans a whole slot)
-    const int tid = threadIdx.x < TR_WLOAD * 32 ? threadIdx.x : threadIdx.x - 32;
-    for (int idx = tid; idx < TR_BBYTES / 2; idx += TR_THREADS - 32) {
+    // (large K: the B blocks are streamed from the table, nothing to build)
+    for (int idx = tid; !LK && idx < TR_BBYTES / 2; idx += TR_THREADS - 32) {
       const int off = 2 * idx;
       const int s = off < TR_B0 ? 0 : 1 + (off - TR_B0) / TR_BS;
       const int o2 = off < TR_B0 ? off : (off - TR_B0) % TR_BS;
@@ -435,7 +499,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
     if (warp == 0) {
       // prefix sums of the taps (K <= 65 < 96) and their total, one warp
       long long run = 0;
-      for (int c0 = 0; c0 < TR_TAPS; c0 += 32) {
+      for (int c0 = 0; c0 < NTAPS; c0 += 32) {
         long long v = tt.taps[c0 + lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -446,6 +510,19 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
         run += __shfl_sync(0xffffffffu, v, 31);
       }
       if (lane == 0) tt.total = run;
+    }
+    if constexpr (LK) {
+      // the products accumulate onto zeros: every slot starts cleared (each
+      // epilogue warp clears the lanes and columns it reads)
+      if (warp < 16) {
+        const uint32_t tl0 = bars.tbase + ((uint32_t)(32 * (warp & 3)) << 16) +
+                             8u * (uint32_t)(warp >> 2);
+        for (int ts = 0; ts < p.tslots; ++ts)
+          for (int L = 0; L < p.tcols / 32; ++L)
+            tr_st8_zero(tl0 + (uint32_t)(ts * p.tcols) + 32u * L);
+        tr_wait_st();
+      }
+      t5_fence_before();
     }
     fence_proxy_async_smem();  // B, written by ordinary stores, is read by MMA
     tr_bar<3, TR_THREADS - 32>();
@@ -491,7 +568,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
             const int m = row_of(j);
             const uint32_t bytes = (uint32_t)((bhi - blo) * sizeof(W));
             mbar_arrive_expect_tx(&bars.raw_full[s], bytes);
-            bulk_copy_g2s(raw + s * TR_SMAX + blo,
+            bulk_copy_g2s(raw + s * SMAXk + blo,
                           x + (int64_t)m * p.ldx + n0 - H + blo, bytes,
                           &bars.raw_full[s]);
             pending |= 1u << s;
@@ -518,7 +595,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
     // pair pi (samples 2 pi, 2 pi + 1 of the window [n0 - H, n0 + 4096)) is
     // chunk pi / 4 at bytes 4 (pi % 4); thread ts takes pi = ts + 192 k,
     // whose slot advances by 12 rows (192 bytes) per step
-    const uint32_t doff = ((ts >> 2) & 3) * TR_LBO + (ts >> 4) * 16 + (ts & 3) * 4;
+    const uint32_t doff = ((ts >> 2) & 3) * LBOk + (ts >> 4) * 16 + (ts & 3) * 4;
     const int npairs = S / 2;
     const int S_ = S;
     uint32_t rc = 0, rc0 = 0;  // raw rows, ring rows before this tile
@@ -543,18 +620,18 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
           break;
         }
         const int m = row_of(j);
-        unsigned char* dst = planes + (size_t)ps.idx * ND * TR_PLANE + doff;
+        unsigned char* dst = planes + (size_t)ps.idx * ND * PLANEk + doff;
         auto put = [&](uint32_t a, uint32_t b) {
           *reinterpret_cast<uint32_t*>(dst) = tr_digit_pair<0>(a, b);
           if constexpr (ND > 1)
-            *reinterpret_cast<uint32_t*>(dst + TR_PLANE) = tr_digit_pair<1>(a, b);
+            *reinterpret_cast<uint32_t*>(dst + PLANEk) = tr_digit_pair<1>(a, b);
           if constexpr (ND > 2)
-            *reinterpret_cast<uint32_t*>(dst + 2 * TR_PLANE) = tr_digit_pair<2>(a, b);
+            *reinterpret_cast<uint32_t*>(dst + 2 * PLANEk) = tr_digit_pair<2>(a, b);
           if constexpr (ND > 3)
-            *reinterpret_cast<uint32_t*>(dst + 3 * TR_PLANE) = tr_digit_pair<3>(a, b);
+            *reinterpret_cast<uint32_t*>(dst + 3 * PLANEk) = tr_digit_pair<3>(a, b);
           dst += TR_NSTG;
         };
-        const W* rs = raw + s * TR_SMAX + 2 * ts;
+        const W* rs = raw + s * SMAXk + 2 * ts;
         auto pair_smem = [&]() {
           if constexpr (sizeof(W) == 8) {
             const longlong2 v = *reinterpret_cast<const longlong2*>(rs);
@@ -595,7 +672,105 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
     }
   } else if (warp == TR_WMMA) {
     // ---- MMA issue (one lane) ---------------------------------------------
-    if (lane == 0 && p.stall_role != 2) {
+    if (LK && lane == 0 && p.stall_role != 2) {
+      // Large K: per stream, groups of at most TR_GROUP k-steps accumulate
+      // onto a cleared slot (every fp32 partial sum an integer of magnitude
+      // at most 2 * 2^14 * 16 * 32 = 2^24); each k-step's B block comes from
+      // the table through a ring of TR_NBR slots, requested up to TR_NBR
+      // blocks ahead by this lane (it waits only on its own products and
+      // on the copies).
+      const uint64_t ad0 = t5_sdesc(smem_addr(planes), LBOk, 128);
+      const uint32_t a_hi = (uint32_t)(ad0 >> 32), a_lo0 = (uint32_t)ad0;
+      const uint64_t bd0 = t5_sdesc(smem_addr(bmat), 128, 256);
+      const uint32_t b_hi = (uint32_t)(bd0 >> 32), b_lo0 = (uint32_t)bd0;
+      const uint32_t id64 = t5_idesc(128, TR_NB);
+      constexpr uint32_t SLOT16 = ND * PLANEk / 16;  // plane-set stride >> 4
+      const unsigned char* btab = static_cast<const unsigned char*>(p.btab);
+      const uint32_t ktot = (uint32_t)my_n * (uint32_t)nstreams * (uint32_t)KS;
+      uint32_t kc = 0, kp = 0;  // B blocks consumed / requested
+      auto b_request = [&]() -> bool {
+        while (kp < ktot && kp < kc + TR_NBR) {
+          const uint32_t sl = kp % TR_NBR;
+          if (!tr_wait(&bars.b_empty[sl], ((kp / TR_NBR) & 1u) ^ 1u, abort, lim))
+            return false;
+          mbar_arrive_expect_tx(&bars.b_full[sl], TR_BS);
+          bulk_copy_g2s(bmat + sl * TR_BS, btab + (size_t)(kp % (uint32_t)KS) * TR_BS,
+                        TR_BS, &bars.b_full[sl]);
+          ++kp;
+        }
+        return true;
+      };
+      uint32_t rc0 = 0, sc = 0;
+      bool ok = true;
+#pragma unroll 1
+      for (int i = 0; i < my_n && ok; ++i, rc0 += (uint32_t)nring) {
+#pragma unroll 1
+        for (int q = 0; q < nstreams && ok; ++q) {
+          const int jo = PROT ? (q + 1 == MM ? 0 : q + 1) : q;
+          const PSlot so = slot_of(i, rc0, jo), sn = slot_of(i, rc0, q);
+          if (!tr_wait(so.full, so.ph, abort, lim) ||
+              (PROT && !tr_wait(sn.full, sn.ph, abort, lim))) {
+            ok = false;
+            break;
+          }
+          const uint32_t pao = a_lo0 + (uint32_t)so.idx * SLOT16;
+          const uint32_t pan = a_lo0 + (uint32_t)sn.idx * SLOT16;
+#pragma unroll 1
+          for (int g0 = 0; g0 < KS && ok; g0 += TR_GROUP, ++sc) {
+            const int ts = (int)(sc % (uint32_t)tslots);
+            if (!tr_wait(&bars.acc_empty[ts], ((sc / tslots) & 1u) ^ 1u, abort, lim)) {
+              ok = false;
+              break;
+            }
+            t5_fence_after();
+            const uint32_t dcol = tb + (uint32_t)(ts * tcols);
+            const uint32_t dn = dcol + 32u * NLEV;
+            const int g1 = g0 + TR_GROUP < KS ? g0 + TR_GROUP : KS;
+#pragma unroll 1
+            for (int st = g0; st < g1; ++st, ++kc) {
+              const uint32_t sl = kc % TR_NBR;
+              if (!b_request() ||
+                  !tr_wait(&bars.b_full[sl], (kc / TR_NBR) & 1u, abort, lim)) {
+                ok = false;
+                break;
+              }
+              t5_fence_after();
+              const uint32_t bl = b_lo0 + ((sl * TR_BS) >> 4);
+              const uint32_t ao =
+                  (uint32_t)((LBOk * 2 * (st & 1) + 16 * (st >> 1)) >> 4);
+#pragma unroll
+              for (int d = 0; d < ND; ++d) {
+                t5_mma_lh<true>(dcol + 32u * d, pao + ao + (uint32_t)d * (PLANEk >> 4),
+                                a_hi, bl, b_hi, id64);
+                if constexpr (PROT)
+                  t5_mma_lh<true>(dn + 32u * d, pan + ao + (uint32_t)d * (PLANEk >> 4),
+                                  a_hi, bl, b_hi, id64);
+              }
+              t5_commit(&bars.b_empty[sl]);
+            }
+            if (!ok) break;
+            t5_commit(&bars.acc_full[ts]);
+          }
+          if (!ok) break;
+          // release the plane slots after their last reader, as below
+          if (PROT) {
+            if (!(head && q == 0)) t5_commit(sn.empty);
+            if (q == nstreams - 1) t5_commit(so.empty);
+          } else {
+            t5_commit(so.empty);
+          }
+        }
+      }
+      // drain: every product issued has completed and every B block
+      // requested has landed before the block exits
+      t5_commit(&bars.drain);
+      for (uint32_t it = 0; it < (1u << 16); ++it)
+        if (tr_try_wait(&bars.drain, 0, TR_POLL_NS)) break;
+      for (uint32_t k = kc; k < kp; ++k)
+        for (uint32_t it = 0; it < (1u << 16); ++it)
+          if (tr_try_wait(&bars.b_full[k % TR_NBR], (k / TR_NBR) & 1u, TR_POLL_NS)) break;
+    }
+    if (!LK && lane == 0 && p.stall_role != 2) {
       const uint64_t bd0 = t5_sdesc(smem_addr(bmat), 128, 256);
       const uint32_t b_hi = (uint32_t)(bd0 >> 32), b_lo = (uint32_t)bd0;
       const uint64_t ad0 = t5_sdesc(smem_addr(planes), TR_LBO, 128);
@@ -866,6 +1041,88 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
       else
         emit_threads(m, n0, v);
     };
+    // One stream's products of this tile: wait for its slot, read it into
+    // out (rd) or drop it, release the slot.  Large K: one slot per group
+    // of k-steps, each group's levels converted exactly (integers of at
+    // most 2^24), summed in 64 bits (modulo 2^64; the word keeps its low w
+    // bits), and the slot cleared before its release (the next group
+    // accumulates onto zeros).
+    auto consume_stream = [&](bool rd, int64_t nb, bool edge, W (&out)[8]) -> bool {
+      if constexpr (!LK) {
+        const int ts = (int)(sc % (uint32_t)tslots);
+        const uint32_t ph = (sc / tslots) & 1u;
+        bool got = true;
+        if (threadIdx.x == 0) got = tr_wait(&bars.acc_full[ts], ph, abort, lim);
+        if (!tr_vote<1, TR_EPI>(got)) return false;
+        t5_fence_after();
+        if (rd) read_slot(ts, nb, edge, out);
+        t5_fence_before();
+        __syncwarp();
+        if (lane == 0) t5_arrive(&bars.acc_empty[ts]);
+        ++sc;
+        return true;
+      } else {
+        constexpr int NLS = PROT ? 2 * NLEV : NLEV;  // levels of a slot
+        unsigned long long acc[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] = 0ull;
+#pragma unroll 1
+        for (int g0 = 0; g0 < KS; g0 += TR_GROUP) {
+          const int ts = (int)(sc % (uint32_t)tslots);
+          const uint32_t ph = (sc / tslots) & 1u;
+          bool got = true;
+          if (threadIdx.x == 0) got = tr_wait(&bars.acc_full[ts], ph, abort, lim);
+          if (!tr_vote<1, TR_EPI>(got)) return false;
+          t5_fence_after();
+          const uint32_t base = tl + (uint32_t)(ts * tcols);
+          if (rd) {
+            uint32_t u[NLEV][8];
+#pragma unroll
+            for (int L = 0; L < NLEV; ++L) tr_ld8(base + 32u * L, u[L]);
+            t5_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              unsigned long long v = 0ull;
+#pragma unroll
+              for (int L = 0; L < NLEV; ++L)
+                v += (unsigned long long)(long long)tr_f2i(u[L][e]) << (8 * L);
+              acc[e] += v;
+            }
+            if constexpr (PROT) {
+              // the neighbour's levels, 2^l above (Eq. 6)
+#pragma unroll
+              for (int L = 0; L < NLEV; ++L) tr_ld8(base + 32u * (NLEV + L), u[L]);
+              t5_wait_ld();
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                unsigned long long v = 0ull;
+#pragma unroll
+                for (int L = 0; L < NLEV; ++L)
+                  v += (unsigned long long)(long long)tr_f2i(u[L][e]) << (8 * L);
+                acc[e] += v << l;
+              }
+            }
+          }
+#pragma unroll
+          for (int L = 0; L < NLS; ++L) tr_st8_zero(base + 32u * L);
+          tr_wait_st();
+          t5_fence_before();
+          __syncwarp();
+          if (lane == 0) t5_arrive(&bars.acc_empty[ts]);
+          ++sc;
+        }
+        if (rd) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const unsigned long long corr =
+                edge ? shift_correction((long long)p.corr_mul, tt.pref, nb + e, p.N, p.K)
+                     : corr_c;
+            out[e] = (W)(acc[e] + corr);
+          }
+        }
+        return true;
+      }
+    };
 #pragma unroll 1
     for (int i = 0; i < my_n; ++i) {
       const int64_t n0 = tile_n0(i);
@@ -877,25 +1134,13 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < MM; ++q) {
           if (q == MM - 1 && skip) break;
-          const int ts = (int)(sc % (uint32_t)tslots);
-          const uint32_t ph = (sc / tslots) & 1u;
-          bool got = true;
-          if (threadIdx.x == 0) got = tr_wait(&bars.acc_full[ts], ph, abort, lim);
-          if (!tr_vote<1, TR_EPI>(got)) {
+          // position q holds stream r + 1 + q (skip) or r + q; the product
+          // of stream r + 1 + qq goes to dl[qq]; stream r's is dropped
+          if (skip ? !consume_stream(true, nb, edge, dl[q < MM - 1 ? q : MM - 2])
+                   : !consume_stream(q >= 1, nb, edge, dl[q >= 1 ? q - 1 : 0])) {
             ok = false;
             break;
           }
-          t5_fence_after();
-          // position q holds stream r + 1 + q (skip) or r + q; the product
-          // of stream r + 1 + qq goes to dl[qq]; stream r's is dropped
-          if (skip)
-            read_slot(ts, nb, edge, dl[q < MM - 1 ? q : MM - 2]);
-          else if (q >= 1)
-            read_slot(ts, nb, edge, dl[q >= 1 ? q - 1 : 0]);
-          t5_fence_before();
-          __syncwarp();
-          if (lane == 0) t5_arrive(&bars.acc_empty[ts]);
-          ++sc;
         }
         if (!ok) break;
         // recovery of all M outputs at these 8 positions (Eq. 16-19): the
@@ -922,21 +1167,11 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
       } else {
 #pragma unroll 1
         for (int q = 0; q < nstreams; ++q) {
-          const int ts = (int)(sc % (uint32_t)tslots);
-          const uint32_t ph = (sc / tslots) & 1u;
-          bool got = true;
-          if (threadIdx.x == 0) got = tr_wait(&bars.acc_full[ts], ph, abort, lim);
-          if (!tr_vote<1, TR_EPI>(got)) {
+          W out[8];
+          if (!consume_stream(true, nb, edge, out)) {
             ok = false;
             break;
           }
-          t5_fence_after();
-          W out[8];
-          read_slot(ts, nb, edge, out);
-          t5_fence_before();
-          __syncwarp();
-          if (lane == 0) t5_arrive(&bars.acc_empty[ts]);
-          ++sc;
           emit_row(row_of(q), n0, out);
         }
         if (!ok) break;
@@ -1015,13 +1250,14 @@ void tr_output_maps(ConvArgs& a, CUtensorMap* tm) {
   a.ytma = 1;
 }
 
-template <typename W, bool PROT, int MM, int ND, int Q, int YS>
+template <typename W, bool PROT, int MM, int ND, int Q, int YS, bool LK>
 int tr_launch_one(const ConvArgs& a, const CUtensorMap* tm, cudaStream_t s) {
   static std::once_flag once;
   static int attr = NE_OK;
-  constexpr size_t smem = tr_smem_bytes<W, PROT, ND>();
+  constexpr size_t smem = tr_smem_bytes<W, PROT, ND, LK>();
+  static_assert(smem <= 232448, "shared memory of a form beyond the limit");
   std::call_once(once, [] {
-    auto k = tcr_conv_kernel<W, PROT, MM, ND, Q, YS>;
+    auto k = tcr_conv_kernel<W, PROT, MM, ND, Q, YS, LK>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       attr = NE_ERR_CUDA;
@@ -1031,44 +1267,93 @@ int tr_launch_one(const ConvArgs& a, const CUtensorMap* tm, cudaStream_t s) {
     return attr;
   }
   const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)sm_count());
-  tcr_conv_kernel<W, PROT, MM, ND, Q, YS>
+  tcr_conv_kernel<W, PROT, MM, ND, Q, YS, LK>
       <<<(unsigned)grid, TR_THREADS, smem, s>>>(a, tm[0], tm[1]);
   return cudaGetLastError() == cudaSuccess ? NE_OK : NE_ERR_CUDA;
 }
 
-template <typename W, bool PROT, int MM, int YS>
+template <typename W, bool PROT, int MM, int YS, bool LK>
 int tr_launch_nd(const ConvArgs& a, const CUtensorMap* tm, cudaStream_t s) {
-  if constexpr (PROT && MM == 4) {
-    // l = 8 or 16 (M = 4 in 32- or 64-bit words): merged levels
-    if (a.mlev == 1)
-      return a.nd == 1 ? tr_launch_one<W, PROT, MM, 1, 1, YS>(a, tm, s)
-                       : tr_launch_one<W, PROT, MM, 2, 1, YS>(a, tm, s);
-    if (a.mlev == 2 && a.nd == 2) return tr_launch_one<W, PROT, MM, 2, 2, YS>(a, tm, s);
+  if constexpr (LK) {
+    // large K: the neighbour's levels apart (Q = 0); up to 2 digits
+    // protected, 3 plain (shared memory)
+    if (a.nd == 1) return tr_launch_one<W, PROT, MM, 1, 0, YS, LK>(a, tm, s);
+    if (a.nd == 2) return tr_launch_one<W, PROT, MM, 2, 0, YS, LK>(a, tm, s);
+    if constexpr (!PROT)
+      if (a.nd == 3) return tr_launch_one<W, PROT, MM, 3, 0, YS, LK>(a, tm, s);
+    return NE_ERR_UNSUPPORTED;
+  } else {
+    if constexpr (PROT && MM == 4) {
+      // l = 8 or 16 (M = 4 in 32- or 64-bit words): merged levels
+      if (a.mlev == 1)
+        return a.nd == 1 ? tr_launch_one<W, PROT, MM, 1, 1, YS, LK>(a, tm, s)
+                         : tr_launch_one<W, PROT, MM, 2, 1, YS, LK>(a, tm, s);
+      if (a.mlev == 2 && a.nd == 2)
+        return tr_launch_one<W, PROT, MM, 2, 2, YS, LK>(a, tm, s);
+    }
+    switch (a.nd) {
+      case 1: return tr_launch_one<W, PROT, MM, 1, 0, YS, LK>(a, tm, s);
+      case 2: return tr_launch_one<W, PROT, MM, 2, 0, YS, LK>(a, tm, s);
+      default: break;
+    }
+    if constexpr (!PROT) {
+      if (a.nd == 3) return tr_launch_one<W, PROT, MM, 3, 0, YS, LK>(a, tm, s);
+      if (a.nd == 4) return tr_launch_one<W, PROT, MM, 4, 0, YS, LK>(a, tm, s);
+    }
+    return NE_ERR_UNSUPPORTED;
   }
-  switch (a.nd) {
-    case 1: return tr_launch_one<W, PROT, MM, 1, 0, YS>(a, tm, s);
-    case 2: return tr_launch_one<W, PROT, MM, 2, 0, YS>(a, tm, s);
-    default: break;
-  }
-  if constexpr (!PROT) {
-    if (a.nd == 3) return tr_launch_one<W, PROT, MM, 3, 0, YS>(a, tm, s);
-    if (a.nd == 4) return tr_launch_one<W, PROT, MM, 4, 0, YS>(a, tm, s);
-  }
-  return NE_ERR_UNSUPPORTED;
 }
 
-// Every form of one word width and output-row alignment (YS); a carries
-// the output maps' fields (tr_output_maps) and tm the two maps.
-template <typename W, int YS>
+// Every form of one word width, output-row alignment (YS) and tap count
+// (LK); a carries the output maps' fields (tr_output_maps) and tm the two
+// maps.
+template <typename W, int YS, bool LK>
 int tr_launch(const ConvArgs& a, const CUtensorMap* tm, bool prot, cudaStream_t s) {
-  if (!prot) return tr_launch_nd<W, false, 0, YS>(a, tm, s);
+  if (!prot) return tr_launch_nd<W, false, 0, YS, LK>(a, tm, s);
   switch (a.M) {
-    case 3: return tr_launch_nd<W, true, 3, YS>(a, tm, s);
-    case 4: return tr_launch_nd<W, true, 4, YS>(a, tm, s);
-    case 5: return tr_launch_nd<W, true, 5, YS>(a, tm, s);
-    case 6: return tr_launch_nd<W, true, 6, YS>(a, tm, s);
+    case 3: return tr_launch_nd<W, true, 3, YS, LK>(a, tm, s);
+    case 4: return tr_launch_nd<W, true, 4, YS, LK>(a, tm, s);
+    case 5: return tr_launch_nd<W, true, 5, YS, LK>(a, tm, s);
+    case 6: return tr_launch_nd<W, true, 6, YS, LK>(a, tm, s);
     default: return NE_ERR_UNSUPPORTED;
   }
+}
+
+// The B blocks of every k-step of the large-K form, in the layout of the
+// resident B: element (n, kk) of k-step s at byte 2048 s + 256 (n / 8) +
+// 16 (n % 8) + 128 (kk / 8) + 2 (kk % 8), the balanced tap digit n / 32 of
+// g[o + H - 16 s - kk] (o = n % 32), zero outside [0, K).  One fp16 per
+// thread.
+__global__ void tr_btab_kernel(const int32_t* __restrict__ g, int K, int H,
+                               int KS, uint16_t* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= KS * (TR_BS / 2)) return;
+  const int s = idx / (TR_BS / 2), o2 = (idx % (TR_BS / 2)) * 2;
+  const int n = (o2 / 256) * 8 + (o2 % 128) / 16;
+  const int kk = ((o2 % 256) / 128) * 8 + (o2 % 16) / 2;
+  const int jg = n / TR_P, o = n % TR_P;
+  const int t = o + H - (16 * s + kk);
+  int v = 0;
+  if (t >= 0 && t < K) {
+    const int gv = g[t];
+    const int g0 = (int)(int8_t)(gv & 0xff);
+    v = jg == 0 ? g0 : (gv - g0) >> 8;
+  }
+  out[idx] = tr_half(v);
+}
+
+// The large-K form: the B table into a.btab (a.ks blocks of TR_BS bytes),
+// then the kernel, both on s.
+template <typename W>
+int tr_launch_large(const ConvArgs& a, const CUtensorMap* tm, bool prot,
+                    cudaStream_t s) {
+  if (!a.btab || (reinterpret_cast<uintptr_t>(a.btab) & 15) != 0)
+    return NE_ERR_UNSUPPORTED;
+  const int n = a.ks * (TR_BS / 2);
+  tr_btab_kernel<<<(n + 255) / 256, 256, 0, s>>>(
+      a.g, a.K, a.hist, a.ks, static_cast<uint16_t*>(const_cast<void*>(a.btab)));
+  if (cudaGetLastError() != cudaSuccess) return NE_ERR_CUDA;
+  return tr_launch<W, 1, true>(a, tm, prot, s);
 }
 
 // Host reader of this translation unit's device error word.

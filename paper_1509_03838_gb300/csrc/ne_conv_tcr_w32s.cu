@@ -6,7 +6,7 @@
 namespace ne {
 
 int tcr_launch_w32s(const ConvArgs& a, const void* tm, bool prot, cudaStream_t s) {
-  return tr_launch<int32_t, 1>(a, static_cast<const CUtensorMap*>(tm), prot, s);
+  return tr_launch<int32_t, 1, false>(a, static_cast<const CUtensorMap*>(tm), prot, s);
 }
 
 unsigned tcr_w32s_device_error(bool clear) { return tr_tu_device_error(clear); }

@@ -57,7 +57,9 @@ int ne_get_device_error(uint32_t* out, int clear) {
                      ne::tcr_w32_device_error(clear != 0) |
                      ne::tcr_w64_device_error(clear != 0) |
                      ne::tcr_w32s_device_error(clear != 0) |
-                     ne::tcr_w64s_device_error(clear != 0);
+                     ne::tcr_w64s_device_error(clear != 0) |
+                     ne::tcr_w32l_device_error(clear != 0) |
+                     ne::tcr_w64l_device_error(clear != 0);
   if (v & 0x80000000u) return NE_ERR_CUDA;
   *out = v;
   return (v & 1u) ? NE_ERR_TIMEOUT : NE_OK;

@@ -200,6 +200,85 @@ def test_tcr_output_row_layouts(ne, orc, case):
         assert (buf[:, :before] == 77).all() and (buf[:, before + Nout:] == 77).all()
 
 
+LARGE_PLAIN = [
+    # w, M, N, K, [lo, hi], max|g|, output row padding   (66 <= K <= 1025)
+    (64, 3, 3 * TILE + 77, 100, (-2**15, 2**15 - 1), 2**15, 0),   # 2 digits
+    (64, 2, 2 * TILE + 5, 1025, (-2**15, 2**15 - 1), 2**15, 1),   # K = 1025, odd ld
+    (32, 4, 5000, 257, (-100, 100), 2**15, 0),                    # 1 digit
+    (64, 2, 3000, 700, (-2**23, 2**23 - 1), 2**15, 0),            # 3 digits
+    (64, 2, 300, 1000, (-2**15, 2**15 - 1), 2**15, 0),            # N < K
+    (64, 1, 9000, 66, (-2**15, 2**15 - 1), 2**15, 2),             # K = 66
+]
+
+
+@pytest.mark.parametrize("case", LARGE_PLAIN)
+def test_tcr_large_k_plain(ne, orc, case):
+    """The large-K form (66 <= K <= 1025): the taps' B blocks streamed from
+    a table, the products drained every 32 k-steps (every fp32 partial sum
+    an integer of at most 2^24), summed in 64 bits; extreme taps and
+    operands at the ends of the declared ranges."""
+    w, M, N, K, (lo, hi), gmax, pad = case
+    gen = synth.rng(N * 5 + K + M)
+    x = synth.uniform_int(gen, (M, N), lo, hi + 1)
+    x[:, 0] = hi
+    x[:, -1] = lo
+    x[:, N // 2] = lo
+    g = synth.uniform_int(gen, (K,), -gmax + 1, gmax)
+    g[0] = gmax
+    g[-1] = -gmax + 1
+    expect = conv_par(orc, x, g, w, strict=False)
+    buf = torch.full((M, N + K - 1 + pad), 5, dtype=dt(w), device="cuda")
+    y = buf[:, :N + K - 1]
+    ne.ne_conv(dev(x, w), torch.from_numpy(g.astype(np.int32)).cuda(),
+               y, x_range=(lo, hi), max_abs_g=gmax)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), expect)
+    if pad:
+        assert (buf[:, N + K - 1:] == 5).all()
+    assert ne.ne_get_device_error(clear=True) == 0
+
+
+LARGE_PROT = [
+    # w, M, N, K, data bits, tap bits, pad d
+    (64, 3, 2 * TILE + 33, 100, 14, 14, 0),   # l = 22
+    (64, 4, 3 * TILE, 1000, 15, 15, 1),       # l = 16, K = 1000, odd ld
+    (64, 5, 5000, 257, 12, 15, 0),            # l = 13
+    (64, 6, 4000, 513, 10, 12, 0),            # l = 11
+    (32, 3, 4096, 66, 6, 7, 0),               # 32-bit words, K = 66
+    (64, 4, 200, 1025, 15, 15, 0),            # N < K, K = 1025
+]
+
+
+@pytest.mark.parametrize("case", LARGE_PROT)
+def test_tcr_large_k_protected_every_failure(ne, orc, case):
+    """The fused protected convolution in the large-K form, every failure
+    mode: each stream's entangled product (own and neighbour planes) drained
+    group by group, then recovered (Eq. 9, Eq. 16-19)."""
+    w, M, N, K, bc, bg, padd = case
+    p = ne.ne_params(M, w)
+    gen = synth.rng(N + 17 * K + M + w)
+    c = synth.uniform_int(gen, (M, N), -(1 << bc), 1 << bc)
+    c[:, 0] = (1 << bc) - 1
+    c[:, -1] = -(1 << bc)
+    g = synth.uniform_int(gen, (K,), -(1 << bg) + 1, 1 << bg)
+    g[0] = (1 << bg) - 1
+    assert K * (1 << bc) * ((1 << bg) - 1) <= p.d_max_exact
+    plain = conv_par(orc, c, g, w)
+    Nout = N + K - 1
+    cd = dev(c, w)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    for fm, r in modes(ne, M):
+        dfull = torch.full((M, Nout + padd), 77, dtype=dt(w), device="cuda")
+        d = dfull[:, :Nout]
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(1 << bc), (1 << bc) - 1),
+                             max_abs_g=(1 << bg) - 1, failed=r, fail_mode=fm)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), plain), (fm, r)
+        if padd:
+            assert (dfull[:, Nout:] == 77).all(), (fm, r)
+    assert ne.ne_get_device_error(clear=True) == 0
+
+
 def test_tcr_protected_full_size_every_output(ne, orc):
     """The benchmark job (M = 4, N = 2^22, K = 64, 16-bit data and taps,
     64-bit words; 1025 tiles, so every block takes 6 or 7 tiles and every
