@@ -911,8 +911,8 @@ inline bool tensor_cores_pay(int streams, int64_t N, int64_t Nout, int K, int wb
   const double ks = (double)((32 + 16 * ((K - 1 + 15) / 16)) / 16);
   const double mmas = (double)streams * (double)((Nout + 4095) / 4096) * ks *
                       (double)(nd > 0 ? nd : 4) * (prot ? 2.0 : 1.0);
-  const double tc_us = 16.0 + std::max(bytes / (prot ? 3.2e6 : 4.4e6),
-                                       mmas * 0.025 / 152.0);
+  const double tc_us = (K > 65 ? 21.0 : 16.0) +
+                       std::max(bytes / (prot ? 3.2e6 : 4.4e6), mmas * 0.025 / 152.0);
   return tc_us < imad_us;
 }
 
@@ -931,13 +931,41 @@ std::atomic<int> g_debug_stall_role{0};
 
 // Fill the raw-plane fields of a for inputs in [lo, hi] (known range):
 // returns false if the job is outside these kernels' window.
+// The pool the plain large-K form takes its B tables from (ne_conv_range
+// has no workspace argument): one per device, created on first use; it
+// keeps up to 16 MiB mapped between calls (a table is at most 132 KiB), so
+// that a call allocates without a driver round trip.
+inline cudaMemPool_t table_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pl = nullptr;
+    if (cudaMemPoolCreate(&pl, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = 16ull << 20;
+    cudaMemPoolSetAttribute(pl, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pl;
+  }
+  return pools[dev];
+}
+
 // allow_lk: the large-K form (66 <= K <= 1025, its B table in a.btab) may
 // be taken.
 inline bool tcr_plan(ConvArgs& a, bool prot, int w, __int128 lo, __int128 hi,
                      int64_t max_abs_g, bool vec, bool allow_lk) {
   const bool lk = a.K > TR_HMAX + 1;
   if (!tc_enabled() || !tcr_enabled() || a.K > (allow_lk ? TR_HMAX_L : TR_HMAX) + 1 ||
-      max_abs_g < 0 || max_abs_g > TC_MAX_G || (prot && (a.M < 3 || a.M > 6)))
+      max_abs_g < 0 || max_abs_g > TC_MAX_G ||
+      (prot && (a.M < 3 || a.M > (lk ? 8 : 6))))
     return false;
   const int nd = tcr_digits(lo, hi);
   if (nd == 0 || (prot && nd > 2) || (lk && nd > 3)) return false;
@@ -999,8 +1027,8 @@ int protected_tc(const ConvArgs& a, int mode, int64_t max_abs_g, int w,
       !tensor_cores_pay(a.M, a.N, a.Nout, a.K, w / 8, true, espan > 0xFFFFFFFF,
                         tcr_digits((__int128)c_min, (__int128)c_max)))
     return kNotTaken;
-  if (form == FORM_AUTO && a.M >= 3 && a.M <= 6) {
-    // raw-plane tcgen05 kernel: products from the digit planes of the raw
+  if (form == FORM_AUTO && a.M >= 3 && a.M <= 8) {
+    // raw-plane tcgen05 kernel (M <= 6; M <= 8 with K > 65): products from the digit planes of the raw
     // rows, entangled in the accumulators, recovered in the epilogue
     ConvArgs t = a;
     if (tcr_plan(t, true, w, (__int128)c_min, (__int128)c_max, max_abs_g, vec,
@@ -1126,12 +1154,14 @@ int ne_conv_range(const void* x, int64_t ldx, int M, int64_t N,
                          tcr_digits((__int128)x_min, (__int128)x_max)) &&
         tcr_plan(a, false, w, (__int128)x_min, (__int128)x_max, max_abs_g,
                  rows_aligned16(x, ldx, wb), true)) {
-      // the large-K form's B table comes from the stream-ordered pool and
-      // returns to it after the launch, in stream order
+      // the large-K form's B table comes from the library's stream-ordered
+      // pool and returns to it after the launch, in stream order
       void* tab = nullptr;
       cudaStream_t s = (cudaStream_t)stream;
       if (a.lk) {
-        if (cudaMallocAsync(&tab, tr_table_bytes(K), s) != cudaSuccess) {
+        cudaMemPool_t pool = table_pool();
+        if (!pool || cudaMallocFromPoolAsync(&tab, tr_table_bytes(K), pool, s) !=
+                         cudaSuccess) {
           cudaGetLastError();
           tab = nullptr;
         }

@@ -117,8 +117,13 @@ template <bool LK>
 __host__ __device__ constexpr int tr_hmax() { return LK ? TR_HMAX_L : TR_HMAX; }
 template <bool LK>
 __host__ __device__ constexpr int tr_smax() { return TR_TILE + tr_hmax<LK>(); }
+// (the large-K planes get two spare rows per chunk column: a column
+// stride 32 bytes past a multiple of 128, as in the small form, keeps the
+// two halves of a k-step's operand on different shared-memory banks)
 template <bool LK>
-__host__ __device__ constexpr int tr_lbo() { return (128 + tr_hmax<LK>() / TR_P) * 16; }
+__host__ __device__ constexpr int tr_lbo() {
+  return (128 + tr_hmax<LK>() / TR_P + (LK ? 2 : 0)) * 16;
+}
 template <bool LK>
 __host__ __device__ constexpr int tr_plane() { return 4 * tr_lbo<LK>(); }
 
@@ -675,10 +680,12 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
     if (LK && lane == 0 && p.stall_role != 2) {
       // Large K: per stream, groups of at most TR_GROUP k-steps accumulate
       // onto a cleared slot (every fp32 partial sum an integer of magnitude
-      // at most 2 * 2^14 * 16 * 32 = 2^24); each k-step's B block comes from
-      // the table through a ring of TR_NBR slots, requested up to TR_NBR
-      // blocks ahead by this lane (it waits only on its own products and
-      // on the copies).
+      // at most 2 * 2^14 * 16 * 32 = 2^24).  The B blocks come from the
+      // table: all of them once, kept in the ring, when there are at most
+      // TR_NBR (K <= 225); else through the ring, requested by this lane
+      // TR_NBR / 2 blocks ahead, so that a slot it refills was last read
+      // half a ring earlier (it waits only on its own products and on the
+      // copies).
       const uint64_t ad0 = t5_sdesc(smem_addr(planes), LBOk, 128);
       const uint32_t a_hi = (uint32_t)(ad0 >> 32), a_lo0 = (uint32_t)ad0;
       const uint64_t bd0 = t5_sdesc(smem_addr(bmat), 128, 256);
@@ -688,8 +695,17 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
       const unsigned char* btab = static_cast<const unsigned char*>(p.btab);
       const uint32_t ktot = (uint32_t)my_n * (uint32_t)nstreams * (uint32_t)KS;
       uint32_t kc = 0, kp = 0;  // B blocks consumed / requested
+      const bool resident = KS <= TR_NBR;
+      bool b_landed = false;  // resident: every block has landed
+      if (resident) {
+        for (int s2 = 0; s2 < KS; ++s2) {
+          mbar_arrive_expect_tx(&bars.b_full[s2], TR_BS);
+          bulk_copy_g2s(bmat + s2 * TR_BS, btab + (size_t)s2 * TR_BS, TR_BS,
+                        &bars.b_full[s2]);
+        }
+      }
       auto b_request = [&]() -> bool {
-        while (kp < ktot && kp < kc + TR_NBR) {
+        while (kp < ktot && kp < kc + TR_NBR / 2) {
           const uint32_t sl = kp % TR_NBR;
           if (!tr_wait(&bars.b_empty[sl], ((kp / TR_NBR) & 1u) ^ 1u, abort, lim))
             return false;
@@ -726,15 +742,49 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
             const uint32_t dcol = tb + (uint32_t)(ts * tcols);
             const uint32_t dn = dcol + 32u * NLEV;
             const int g1 = g0 + TR_GROUP < KS ? g0 + TR_GROUP : KS;
+            if (resident) {
+              // every block at hand: one digit's chain of k-steps after
+              // another (consecutive products into the same columns)
+              if (!b_landed) {
+                for (int s2 = 0; s2 < KS && ok; ++s2)
+                  ok = tr_wait(&bars.b_full[s2], 0u, abort, lim);
+                if (!ok) break;
+                b_landed = true;
+              }
+#pragma unroll
+              for (int d = 0; d < (PROT ? 2 * ND : ND); ++d) {
+                const bool nbr = PROT && d >= ND;
+                const int dd = nbr ? d - ND : d;
+                const uint32_t dc = (nbr ? dn : dcol) + 32u * dd;
+                const uint32_t pa = (nbr ? pan : pao) + (uint32_t)dd * (PLANEk >> 4);
+#pragma unroll 1
+                for (int st = g0; st < g1; ++st)
+                  t5_mma_lh<true>(dc,
+                                  pa + (uint32_t)((LBOk * 2 * (st & 1) + 16 * (st >> 1)) >> 4),
+                                  a_hi, b_lo0 + (uint32_t)((st * TR_BS) >> 4), b_hi, id64);
+              }
+              kc += (uint32_t)(g1 - g0);
+              t5_commit(&bars.acc_full[ts]);
+              continue;
+            }
 #pragma unroll 1
             for (int st = g0; st < g1; ++st, ++kc) {
-              const uint32_t sl = kc % TR_NBR;
-              if (!b_request() ||
-                  !tr_wait(&bars.b_full[sl], (kc / TR_NBR) & 1u, abort, lim)) {
+              // (the copies complete on the mbarrier; no tensor-memory fence
+              // is needed between this wait and the products, and none is
+              // issued per k-step: the issue stays back to back)
+              const uint32_t sl = resident ? (uint32_t)st : kc % TR_NBR;
+              if (resident) {
+                if (!b_landed) {
+                  for (int s2 = 0; s2 < KS && ok; ++s2)
+                    ok = tr_wait(&bars.b_full[s2], 0u, abort, lim);
+                  if (!ok) break;
+                  b_landed = true;
+                }
+              } else if (!b_request() ||
+                         !tr_wait(&bars.b_full[sl], (kc / TR_NBR) & 1u, abort, lim)) {
                 ok = false;
                 break;
               }
-              t5_fence_after();
               const uint32_t bl = b_lo0 + ((sl * TR_BS) >> 4);
               const uint32_t ao =
                   (uint32_t)((LBOk * 2 * (st & 1) + 16 * (st >> 1)) >> 4);
@@ -746,7 +796,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
                   t5_mma_lh<true>(dn + 32u * d, pan + ao + (uint32_t)d * (PLANEk >> 4),
                                   a_hi, bl, b_hi, id64);
               }
-              t5_commit(&bars.b_empty[sl]);
+              if (!resident) t5_commit(&bars.b_empty[sl]);
             }
             if (!ok) break;
             t5_commit(&bars.acc_full[ts]);
@@ -766,9 +816,16 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
       t5_commit(&bars.drain);
       for (uint32_t it = 0; it < (1u << 16); ++it)
         if (tr_try_wait(&bars.drain, 0, TR_POLL_NS)) break;
-      for (uint32_t k = kc; k < kp; ++k)
-        for (uint32_t it = 0; it < (1u << 16); ++it)
-          if (tr_try_wait(&bars.b_full[k % TR_NBR], (k / TR_NBR) & 1u, TR_POLL_NS)) break;
+      if (resident) {
+        for (int s2 = 0; s2 < KS; ++s2)
+          for (uint32_t it = 0; it < (1u << 16); ++it)
+            if (tr_try_wait(&bars.b_full[s2], 0u, TR_POLL_NS)) break;
+      } else {
+        for (uint32_t k = kc; k < kp; ++k)
+          for (uint32_t it = 0; it < (1u << 16); ++it)
+            if (tr_try_wait(&bars.b_full[k % TR_NBR], (k / TR_NBR) & 1u, TR_POLL_NS))
+              break;
+      }
     }
     if (!LK && lane == 0 && p.stall_role != 2) {
       const uint64_t bd0 = t5_sdesc(smem_addr(bmat), 128, 256);
@@ -1315,8 +1372,13 @@ int tr_launch(const ConvArgs& a, const CUtensorMap* tm, bool prot, cudaStream_t 
     case 4: return tr_launch_nd<W, true, 4, YS, LK>(a, tm, s);
     case 5: return tr_launch_nd<W, true, 5, YS, LK>(a, tm, s);
     case 6: return tr_launch_nd<W, true, 6, YS, LK>(a, tm, s);
-    default: return NE_ERR_UNSUPPORTED;
+    default: break;
   }
+  if constexpr (LK) {  // M = 7, 8: the large-K form only
+    if (a.M == 7) return tr_launch_nd<W, true, 7, YS, LK>(a, tm, s);
+    if (a.M == 8) return tr_launch_nd<W, true, 8, YS, LK>(a, tm, s);
+  }
+  return NE_ERR_UNSUPPORTED;
 }
 
 // The B blocks of every k-step of the large-K form, in the layout of the

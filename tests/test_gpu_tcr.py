@@ -246,6 +246,8 @@ LARGE_PROT = [
     (64, 6, 4000, 513, 10, 12, 0),            # l = 11
     (32, 3, 4096, 66, 6, 7, 0),               # 32-bit words, K = 66
     (64, 4, 200, 1025, 15, 15, 0),            # N < K, K = 1025
+    (64, 8, 2 * TILE + 9, 100, 14, 14, 0),    # M = 8, l = 8
+    (64, 7, 3000, 300, 12, 12, 1),            # M = 7, l = 10
 ]
 
 
