@@ -7,6 +7,8 @@
  * partners waiting until their (shortened) limit expires.  Nothing here
  * faults, traps or hangs a GPU.  ne_debug_set_dispatch keeps small jobs on
  * the tensor-core forms so that tests reach those kernels.
+ * ne_debug_index_status and ne_debug_index_selftest read the index checks
+ * of the debug build (libne_debug.so, compiled with NE_INDEX_CHECKS).
  */
 #ifndef NE_DEBUG_H_
 #define NE_DEBUG_H_
@@ -44,6 +46,38 @@ int ne_debug_set_fault(int stall_role, uint32_t wait_polls);
  * for a value other than 0 or 1.
  */
 int ne_debug_set_dispatch(int tensor_cores_always);
+
+/*
+ * ne_debug_index_status -- the index checks of the debug build.  Its
+ * kernels test the derived indices of their key accesses against the extent
+ * each must stay inside: the raw-window bulk copies and the circular gather
+ * of the multiply-add convolution, the raw-row copies, tap-table blocks and
+ * output rows of the tensor-core convolution, and the job and unit numbers
+ * of the batch kernel.  An access whose index falls outside is skipped, not
+ * made, and counted.
+ *   *violations  the number of violations since the last clear (in every
+ *                translation unit of the library);
+ *   *first       0 if none, else one of them as site << 48 | (index mod
+ *                2^48); sites: 1 self-test, 2 multiply-add copy window,
+ *                3 circular gather, 4 tensor-core raw row, 5 tap-table
+ *                block, 6 output row or tile, 7 batch job or unit;
+ *   clear        non-zero: reset the counts after reading them.
+ * Synchronises the device first.  Returns NE_OK; NE_ERR_INVALID_ARG for a
+ * null pointer; NE_ERR_CUDA; NE_ERR_UNSUPPORTED from the default build
+ * (libne.so), which has no checks (both outputs then 0).
+ */
+int ne_debug_index_status(uint64_t* violations, uint64_t* first, int clear);
+
+/*
+ * ne_debug_index_selftest -- debug build only: one GPU thread checks the
+ * index i against the extent n at the self-test site (site 1) and, when it
+ * passes, adds one to a device counter that is copied to *hits (host
+ * memory).  No other memory is accessed, whatever i and n are.  A failing
+ * check is recorded as ne_debug_index_status describes.  Blocks the host.
+ * Returns NE_OK; NE_ERR_INVALID_ARG for a null hits; NE_ERR_CUDA;
+ * NE_ERR_UNSUPPORTED from the default build (*hits then 0).
+ */
+int ne_debug_index_selftest(int64_t i, int64_t n, uint32_t* hits);
 
 #ifdef __cplusplus
 }

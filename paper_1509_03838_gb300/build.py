@@ -3,6 +3,12 @@
 Translation units compile in parallel into ``_build/``; the shared library
 lands next to this file so the binding (``ne.py``) loads it from the package
 directory.  Rebuilds only what is older than its sources or headers.
+
+``build(debug=True)`` makes the debug build instead: the same sources
+compiled with ``-DNE_INDEX_CHECKS`` into ``_build_debug/`` and linked as
+``libne_debug.so``, whose kernels check the indices of their key accesses
+and record violations in a status word (``ne_debug_index_status``).  The
+binding loads it in place of libne.so when ``NE_INDEX_CHECKS=1`` is set.
 """
 from __future__ import annotations
 
@@ -17,6 +23,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libne.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(HERE, "libne_debug.so")
 
 SOURCES = ["ne_host.cpp", "ne_stream_ops.cu", "ne_conv.cu", "ne_conv_tcr_w32.cu",
            "ne_conv_tcr_w64.cu", "ne_conv_tcr_w32s.cu", "ne_conv_tcr_w64s.cu",
@@ -61,7 +69,7 @@ def _link(nvcc: str, lib: str, objs: list[str], force: bool) -> None:
     if force or not os.path.exists(lib) or \
             os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
         tmp = lib + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -69,21 +77,25 @@ def _link(nvcc: str, lib: str, objs: list[str], force: bool) -> None:
 
 
 def build(force: bool = False, verbose: bool = False,
-          extra_flags: list[str] | None = None) -> str:
+          extra_flags: list[str] | None = None, debug: bool = False) -> str:
     """Compile every CUDA translation unit, link libne.so and the probe's
-    libne_probe.so; returns libne.so's path."""
+    libne_probe.so; returns libne.so's path.  debug=True: link the
+    index-checking libne_debug.so alone and return its path."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = BUILD_DEBUG if debug else BUILD
+    os.makedirs(bdir, exist_ok=True)
     hdr = _headers_mtime()
-    extra = list(extra_flags or [])
+    extra = list(extra_flags or []) + (["-DNE_INDEX_CHECKS"] if debug else [])
     jobs = []
-    objs = {LIB: [], PROBE_LIB: []}
-    for lib, names in ((LIB, SOURCES), (PROBE_LIB, PROBE_SOURCES)):
+    libs = ((DEBUG_LIB, SOURCES),) if debug else \
+        ((LIB, SOURCES), (PROBE_LIB, PROBE_SOURCES))
+    objs = {lib: [] for lib, _ in libs}
+    for lib, names in libs:
         for name in names:
             src = os.path.join(CSRC, name)
             if not os.path.exists(src):
                 continue
-            obj = os.path.join(BUILD, name + ".o")
+            obj = os.path.join(bdir, name + ".o")
             objs[lib].append(obj)
             if force or not os.path.exists(obj) or \
                     os.path.getmtime(obj) < max(os.path.getmtime(src), hdr):
@@ -93,12 +105,13 @@ def build(force: bool = False, verbose: bool = False,
             futs = [ex.submit(_compile, nvcc, s, o, extra) for s, o in jobs]
             for f in futs:
                 f.result()
-    for lib in (LIB, PROBE_LIB):
+    for lib, _ in libs:
         _link(nvcc, lib, objs[lib], force or bool(jobs))
     if verbose:
-        print(f"built {LIB} and {PROBE_LIB}")
-    return LIB
+        print("built " + " and ".join(lib for lib, _ in libs))
+    return libs[0][0]
 
 
 if __name__ == "__main__":
-    build(verbose=True)
+    import sys
+    build(verbose=True, debug="--debug" in sys.argv[1:])

@@ -170,15 +170,27 @@ batch_kernel(const BatchArgs a) {
           if (__ldg(a.unit0 + mid) <= u) lo = mid; else hi = mid - 1;
         }
         j = lo;
-        s_jb = a.jobs[j];
-        s_local = u - __ldg(a.unit0 + j);
+        const long long local = u - __ldg(a.unit0 + j);
+        // the job exists and the unit is one of its own
+        if (NE_IN_RANGE(j, a.n_jobs, SITE_BATCH_JOB) &&
+            NE_IN_RANGE(local, __ldg(a.unit0 + j + 1) - __ldg(a.unit0 + j),
+                        SITE_BATCH_JOB)) {
+          s_jb = a.jobs[j];
+          s_local = local;
+        } else {
+          j = -2;  // skip this unit
+        }
       }
       s_job = j;
     }
     __syncthreads();
     const int j = s_job;
     const int64_t local = s_local;
-    if (j < 0) break;
+    if (j == -1) break;
+    if (j < 0) {  // uniform over the block
+      __syncthreads();
+      continue;
+    }
     const JobDev& jb = s_jb;
     if (jb.mode == MODE_I32)
       batch_unit<int32_t, MODE_I32, T>(jb, local, a.arrivals, smem, a.Kp_max,
@@ -406,6 +418,7 @@ int ne_ctx_destroy(ne_ctx* ctx) {
 int ne_ctx_bad_job(const ne_ctx* ctx) { return ctx ? ctx->bad_job : -1; }
 
 int ne_batch_prepare(ne_ctx* ctx, const ne_job* jobs, int n_jobs) {
+  NE_RANGE("ne_batch_prepare");
   if (!ctx || n_jobs < 0 || (n_jobs > 0 && !jobs)) return NE_ERR_INVALID_ARG;
   ctx->bad_job = -1;
   drop_graph(ctx);
@@ -556,12 +569,14 @@ int ne_batch_prepare(ne_ctx* ctx, const ne_job* jobs, int n_jobs) {
 }
 
 int ne_batch_launch(ne_ctx* ctx, void* stream) {
+  NE_RANGE("ne_batch_launch");
   if (!ctx) return NE_ERR_INVALID_ARG;
   return launch_batch(ctx, (cudaStream_t)stream);
 }
 
 int ne_batch_submit(ne_ctx* ctx, const ne_job* jobs, int n_jobs,
                     void* stream) {
+  NE_RANGE("ne_batch_submit");
   const int st = ne_batch_prepare(ctx, jobs, n_jobs);
   if (st != NE_OK) return st;
   return ne_batch_launch(ctx, stream);
@@ -578,6 +593,7 @@ int ne_batch_set_config(ne_ctx* ctx, int threads, int blocks_per_sm) {
 }
 
 int ne_batch_graph_capture(ne_ctx* ctx) {
+  NE_RANGE("ne_batch_graph_capture");
   if (!ctx) return NE_ERR_INVALID_ARG;
   drop_graph(ctx);
   if (!ctx->cap_stream &&
@@ -600,6 +616,7 @@ int ne_batch_graph_capture(ne_ctx* ctx) {
 }
 
 int ne_batch_graph_launch(ne_ctx* ctx, void* stream) {
+  NE_RANGE("ne_batch_graph_launch");
   if (!ctx || !ctx->graph) return NE_ERR_INVALID_ARG;
   return status_from_cuda(cudaGraphLaunch(ctx->graph, (cudaStream_t)stream));
 }
@@ -614,6 +631,7 @@ int ne_batch_set_tune_file(ne_ctx* ctx, const char* path) {
 int ne_batch_autotune(ne_ctx* ctx, const ne_job* jobs, int n_jobs, int reps,
                       void* stream, int* threads_out, int* blocks_out,
                       float* ms_out) {
+  NE_RANGE("ne_batch_autotune");
   if (!ctx || reps < 1) return NE_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;

@@ -107,6 +107,7 @@ __device__ __forceinline__ void stage_circular(const W* __restrict__ row,
   for (int j = threadIdx.x; j < total; j += CONV_THREADS) {
     int64_t gi = (n0 - Kp + j) % N;
     if (gi < 0) gi += N;
+    if (!NE_IN_RANGE(gi, N, SITE_CONV_GATHER)) gi = 0;
     int lo, hi;
     split_word<W, MODE>(wsub<W>(__ldg(row + gi), bias), lo, hi);
     s_lo[j] = lo;
@@ -239,7 +240,13 @@ __device__ __forceinline__ void issue_unit_copy(const ConvArgs& p, int64_t u,
   const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(W));
   const int64_t off = lo - (n0 - p.Kp);
   const W* xb = reinterpret_cast<const W*>(p.x);
-  if (bytes == 0) {
+  // the copied words lie in the row and in the window's staging buffer
+  const bool inside = bytes == 0 ||
+                      (NE_IN_RANGE(lo, p.N, SITE_CONV_COPY) &&
+                       NE_IN_RANGE(lo + cnt - 1, p.N, SITE_CONV_COPY) &&
+                       NE_IN_RANGE(off, CONV_TILE + p.Kp, SITE_CONV_COPY) &&
+                       NE_IN_RANGE(off + cnt - 1, CONV_TILE + p.Kp, SITE_CONV_COPY));
+  if (bytes == 0 || !inside) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
                      smem_addr(bar))
                  : "memory");
@@ -1094,6 +1101,7 @@ extern "C" {
 int ne_conv(const void* x, int64_t ldx, int M, int64_t N, const int32_t* g,
             int K, void* y, int64_t ldy, int w, int64_t x_min, int64_t x_max,
             uint32_t live_mask, void* stream) {
+  NE_RANGE("ne_conv");
   if (M < 1 || M > 32 || N < 0 || K < 1 || K > CONV_MAX_K || ldx < N ||
       (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
@@ -1128,6 +1136,7 @@ int ne_conv_range(const void* x, int64_t ldx, int M, int64_t N,
                   const int32_t* g, int K, int64_t max_abs_g, void* y,
                   int64_t ldy, int w, int64_t x_min, int64_t x_max,
                   uint32_t live_mask, void* stream) {
+  NE_RANGE("ne_conv_range");
   if (max_abs_g < 0) return NE_ERR_INVALID_ARG;
   if (x_min <= x_max && (w == 32 || w == 64) && M >= 1 && M <= 32 && N > 0 &&
       K >= 1 && K <= TR_HMAX_L + 1 && ldx >= N && x && y && g &&
@@ -1210,6 +1219,7 @@ int ne_conv_kind(const void* x, int64_t ldx, int M, int64_t N,
                  const int32_t* g, int K, void* y, int64_t ldy, int w,
                  int64_t x_min, int64_t x_max, uint32_t live_mask, int kind,
                  void* stream) {
+  NE_RANGE("ne_conv_kind");
   if (kind == NE_CONV_LINEAR)
     return ne_conv(x, ldx, M, N, g, K, y, ldy, w, x_min, x_max, live_mask,
                    stream);
@@ -1287,6 +1297,7 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
                       int64_t c_max, int64_t max_abs_g, int failed,
                       int fail_mode, void* d, int64_t ldd, void* ws,
                       size_t ws_bytes, void* stream) {
+  NE_RANGE("ne_protected_conv");
   if (M < 3 || M > 32 || N < 0 || K < 1 || K > CONV_MAX_K || ldc < N ||
       (w != 32 && w != 64) || l <= 0 || l >= w || (M - 1) * l > w ||
       c_min > c_max || max_abs_g < 0)
@@ -1408,6 +1419,7 @@ extern "C" int ne_protected_conv_noalloc(const void* c, int64_t ldc, int M,
                                          int64_t c_max, int64_t max_abs_g,
                                          int failed, int fail_mode, void* d,
                                          int64_t ldd, void* stream) {
+  NE_RANGE("ne_protected_conv_noalloc");
   if (M < 3 || M > 32 || N < 0 || K < 1 || K > CONV_MAX_K || ldc < N ||
       (w != 32 && w != 64) || l <= 0 || l >= w || (M - 1) * l > w ||
       c_min > c_max || max_abs_g < 0)

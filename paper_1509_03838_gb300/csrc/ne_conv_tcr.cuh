@@ -569,8 +569,13 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
           const int s = rc % NRAW;
           const uint32_t ph = (rc / NRAW) & 1u;
           if (!tr_wait(&bars.raw_empty[s], ph ^ 1u, abort, lim)) break;
-          if (bhi > blo) {
-            const int m = row_of(j);
+          const int m = row_of(j);
+          // the copy stays inside row m of x and inside the raw slot
+          if (bhi > blo && NE_IN_RANGE(m, p.M, SITE_TCR_RAW) &&
+              NE_IN_RANGE(n0 - H + blo, p.N, SITE_TCR_RAW) &&
+              NE_IN_RANGE(n0 - H + bhi - 1, p.N, SITE_TCR_RAW) &&
+              NE_IN_RANGE(blo, SMAXk, SITE_TCR_RAW) &&
+              NE_IN_RANGE(bhi - 1, SMAXk, SITE_TCR_RAW)) {
             const uint32_t bytes = (uint32_t)((bhi - blo) * sizeof(W));
             mbar_arrive_expect_tx(&bars.raw_full[s], bytes);
             bulk_copy_g2s(raw + s * SMAXk + blo,
@@ -699,9 +704,14 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
       bool b_landed = false;  // resident: every block has landed
       if (resident) {
         for (int s2 = 0; s2 < KS; ++s2) {
-          mbar_arrive_expect_tx(&bars.b_full[s2], TR_BS);
-          bulk_copy_g2s(bmat + s2 * TR_BS, btab + (size_t)s2 * TR_BS, TR_BS,
-                        &bars.b_full[s2]);
+          // the table holds (TR_P + H) / 16 blocks
+          if (NE_IN_RANGE(s2, (TR_P + H) / 16, SITE_TCR_BTAB)) {
+            mbar_arrive_expect_tx(&bars.b_full[s2], TR_BS);
+            bulk_copy_g2s(bmat + s2 * TR_BS, btab + (size_t)s2 * TR_BS, TR_BS,
+                          &bars.b_full[s2]);
+          } else {
+            t5_arrive(&bars.b_full[s2]);
+          }
         }
       }
       auto b_request = [&]() -> bool {
@@ -709,9 +719,14 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
           const uint32_t sl = kp % TR_NBR;
           if (!tr_wait(&bars.b_empty[sl], ((kp / TR_NBR) & 1u) ^ 1u, abort, lim))
             return false;
-          mbar_arrive_expect_tx(&bars.b_full[sl], TR_BS);
-          bulk_copy_g2s(bmat + sl * TR_BS, btab + (size_t)(kp % (uint32_t)KS) * TR_BS,
-                        TR_BS, &bars.b_full[sl]);
+          const uint32_t blk = kp % (uint32_t)KS;
+          if (NE_IN_RANGE(blk, (TR_P + H) / 16, SITE_TCR_BTAB)) {
+            mbar_arrive_expect_tx(&bars.b_full[sl], TR_BS);
+            bulk_copy_g2s(bmat + sl * TR_BS, btab + (size_t)blk * TR_BS, TR_BS,
+                          &bars.b_full[sl]);
+          } else {
+            t5_arrive(&bars.b_full[sl]);
+          }
           ++kp;
         }
         return true;
@@ -1093,6 +1108,11 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
       tr_bar<4, TR_EPI>();
     };
     auto emit_row = [&](int m, int64_t n0, const W (&v)[8]) {
+      // m and n0 are uniform over the quadrant's warps: a skipped row skips
+      // its named barriers in all of them
+      if (!(NE_IN_RANGE(m, p.M, SITE_TCR_ROW) &&
+            NE_IN_RANGE(n0, p.Nout, SITE_TCR_ROW)))
+        return;
       if (p.ytma)
         emit_tma(m, n0, v);
       else

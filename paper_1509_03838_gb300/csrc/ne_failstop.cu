@@ -91,6 +91,7 @@ int ne_fs_protected_conv(ne_fs* fs, const void* c, int64_t ldc, int M,
                          void* d, int64_t ld_out, double deadline_ms,
                          uint32_t inject_late, uint32_t* late_mask,
                          void* stream) {
+  NE_RANGE("ne_fs_protected_conv");
   const auto t0 = std::chrono::steady_clock::now();
   if (!fs || M < 3 || M > fs->max_M || N < 1 || K < 1 || K > 8192 ||
       ldc < N || lde < N || (w != 32 && w != 64) || l <= 0 || l >= w ||

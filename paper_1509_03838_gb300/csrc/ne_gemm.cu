@@ -417,6 +417,7 @@ int ne_gemm(const void* x, int64_t ldx, int64_t sx, int M, int64_t R,
             int64_t S, const int32_t* g, int64_t ldg, int64_t T, void* y,
             int64_t ldy, int64_t sy, int w, int64_t x_min, int64_t x_max,
             uint32_t live_mask, void* stream) {
+  NE_RANGE("ne_gemm");
   if (M < 1 || M > 32 || R < 0 || S < 0 || T < 0 || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (R == 0 || T == 0) return NE_OK;  // no output
@@ -462,6 +463,7 @@ int ne_protected_gemm(const void* c, int64_t ldc, int64_t sc, int M,
                       int64_t T, int w, int l, int64_t c_min, int64_t c_max,
                       int64_t max_abs_g, int failed, int fail_mode, void* d,
                       int64_t sd, void* ws, size_t ws_bytes, void* stream) {
+  NE_RANGE("ne_protected_gemm");
   if (M < 3 || M > 32 || R < 0 || S < 0 || T < 0 || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (fail_mode != NE_FAIL_NONE && fail_mode != NE_FAIL_SKIP &&
@@ -535,6 +537,7 @@ int ne_protected_gemm(const void* c, int64_t ldc, int64_t sc, int M,
 int ne_outer(const void* x, int64_t ldx, int M, int64_t N, const int32_t* g,
              int64_t P, void* y, int64_t ldy, int64_t sy, int w,
              uint32_t live_mask, void* stream) {
+  NE_RANGE("ne_outer");
   if (M < 1 || M > 32 || N < 0 || P < 0 || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (N == 0 || P == 0) return NE_OK;
@@ -564,6 +567,7 @@ int ne_protected_outer(const void* c, int64_t ldc, int M, int64_t N,
                        int64_t c_min, int64_t c_max, int64_t max_abs_g,
                        int failed, int fail_mode, void* d, int64_t sd,
                        void* stream) {
+  NE_RANGE("ne_protected_outer");
   if (M < 3 || M > 32 || N < 0 || P < 0 || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (fail_mode != NE_FAIL_NONE && fail_mode != NE_FAIL_SKIP &&

@@ -1,12 +1,13 @@
-// Host-only parts of libne: status strings, the parameter rule and the
-// dynamic-range checks.  No CUDA call happens here except the cached SM
-// count query.
+// Host-only parts of libne: status strings, the parameter rule, the
+// dynamic-range checks, the device error word and the debug build's index
+// status.  No kernel runs from here except the index checks' self-test.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <mutex>
 
 #include "../../include/ne.h"
+#include "../../include/ne_debug.h"
 #include "ne_common.cuh"
 #include "ne_conv_args.cuh"
 
@@ -28,6 +29,33 @@ int sm_count() {
   }
   return cached[dev];
 }
+
+#ifdef NE_INDEX_CHECKS
+namespace {
+constexpr int kMaxReaders = 64;
+std::mutex& readers_mu() {
+  static std::mutex mu;
+  return mu;
+}
+IndexStatusReader* readers(int** count) {
+  static IndexStatusReader list[kMaxReaders];
+  static int n = 0;
+  *count = &n;
+  return list;
+}
+
+__global__ void index_selftest_kernel(int64_t i, int64_t n, unsigned* hits) {
+  if (NE_IN_RANGE(i, n, SITE_SELFTEST)) atomicAdd(hits, 1u);
+}
+}  // namespace
+
+void register_index_status(IndexStatusReader reader) {
+  std::lock_guard<std::mutex> lock(readers_mu());
+  int* n = nullptr;
+  IndexStatusReader* list = readers(&n);
+  if (*n < kMaxReaders) list[(*n)++] = reader;
+}
+#endif
 
 }  // namespace ne
 
@@ -63,6 +91,56 @@ int ne_get_device_error(uint32_t* out, int clear) {
   if (v & 0x80000000u) return NE_ERR_CUDA;
   *out = v;
   return (v & 1u) ? NE_ERR_TIMEOUT : NE_OK;
+}
+
+int ne_debug_index_status(uint64_t* violations, uint64_t* first, int clear) {
+  if (!violations || !first) return NE_ERR_INVALID_ARG;
+#ifdef NE_INDEX_CHECKS
+  if (cudaDeviceSynchronize() != cudaSuccess) return NE_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(ne::readers_mu());
+  int* n = nullptr;
+  ne::IndexStatusReader* list = ne::readers(&n);
+  uint64_t count = 0, head = 0;
+  for (int t = 0; t < *n; ++t) {
+    unsigned long long w[2];
+    const int st = list[t](w, clear != 0);
+    if (st != NE_OK) return st;
+    count += w[0];
+    if (head == 0) head = w[1];
+  }
+  *violations = count;
+  *first = head;
+  return NE_OK;
+#else
+  (void)clear;
+  *violations = 0;
+  *first = 0;
+  return NE_ERR_UNSUPPORTED;
+#endif
+}
+
+int ne_debug_index_selftest(int64_t i, int64_t n, uint32_t* hits) {
+  if (!hits) return NE_ERR_INVALID_ARG;
+#ifdef NE_INDEX_CHECKS
+  unsigned* d = nullptr;
+  if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) return NE_ERR_CUDA;
+  int st = NE_OK;
+  if (cudaMemset(d, 0, sizeof(unsigned)) != cudaSuccess) st = NE_ERR_CUDA;
+  if (st == NE_OK) {
+    ne::index_selftest_kernel<<<1, 1>>>(i, n, d);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(hits, d, sizeof(unsigned), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+      st = NE_ERR_CUDA;
+  }
+  cudaFree(d);
+  return st;
+#else
+  (void)i;
+  (void)n;
+  *hits = 0;
+  return NE_ERR_UNSUPPORTED;
+#endif
 }
 
 // Parameter rule (Eq. 12 constraint, Table I objective).  For a fixed l the

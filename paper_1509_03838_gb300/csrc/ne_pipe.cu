@@ -145,6 +145,7 @@ int ne_pipe_protected_conv(ne_pipe* p, const void* c_host, int64_t ldc,
                            int64_t c_min, int64_t c_max, int64_t max_abs_g,
                            int failed, int fail_mode, void* d_host,
                            int64_t ldd, void* stream) {
+  NE_RANGE("ne_pipe_protected_conv");
   if (!p) return NE_ERR_INVALID_ARG;
   if (N < 0 || K < 1 || K > p->K_max || ldc < N) return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;

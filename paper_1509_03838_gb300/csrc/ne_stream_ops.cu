@@ -414,6 +414,7 @@ extern "C" {
 
 int ne_entangle(const void* c, int64_t ldc, void* eps, int64_t lde, int M,
                 int64_t N, int w, int l, void* stream) {
+  NE_RANGE("ne_entangle");
   if (M < 3 || M > 32 || N < 0 || ldc < N || lde < N ||
       (w != 32 && w != 64) || l <= 0 || l >= w)
     return NE_ERR_INVALID_ARG;
@@ -431,6 +432,7 @@ int ne_entangle(const void* c, int64_t ldc, void* eps, int64_t lde, int M,
 
 int ne_recover(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
                int l, int failed, void* d, int64_t ld_out, void* stream) {
+  NE_RANGE("ne_recover");
   if (M < 3 || M > 32 || Nout < 0 || ldd < Nout ||
       ld_out < Nout || (w != 32 && w != 64) || l <= 0 ||
       (M - 1) * l > w || failed < 0 || failed >= M)
@@ -451,12 +453,14 @@ int ne_recover(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
 
 int ne_extract(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
                int l, void* d, int64_t ld_out, void* stream) {
+  NE_RANGE("ne_extract");
   return ne_recover(delta, ldd, M, Nout, w, l, 0, d, ld_out, stream);
 }
 
 int ne_recover_mask(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
                     int l, uint32_t failed_mask, void* d, int64_t ld_out,
                     void* stream) {
+  NE_RANGE("ne_recover_mask");
   if (M < 3 || M > 32) return NE_ERR_INVALID_ARG;
   if (M < 32 && (failed_mask >> M) != 0) return NE_ERR_INVALID_ARG;
   // only a single fail-stop is recoverable (Sec. I)
@@ -469,6 +473,7 @@ int ne_recover_mask(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
 
 int ne_dot(const void* x, int64_t ldx, int M, int64_t N, const void* g,
            int w, void* y, int64_t ldy, uint32_t live_mask, void* stream) {
+  NE_RANGE("ne_dot");
   if (M < 1 || M > 32 || N < 0 || ldx < N || (w != 32 && w != 64) ||
       !y || ldy < 1)
     return NE_ERR_INVALID_ARG;
@@ -497,6 +502,7 @@ int ne_dot(const void* x, int64_t ldx, int M, int64_t N, const void* g,
 int ne_detect(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
               int l, int64_t d_max, void* d, int64_t ld_out, uint32_t* count,
               int64_t* positions, int max_positions, void* stream) {
+  NE_RANGE("ne_detect");
   if (M < 3 || M > 32 || Nout < 0 || ldd < Nout || (w != 32 && w != 64) ||
       l <= 0 || (M - 1) * l > w || d_max < 0 || !count ||
       (d && ld_out < Nout) || max_positions < 0 ||
@@ -543,6 +549,7 @@ int ne_detect(const void* delta, int64_t ldd, int M, int64_t Nout, int w,
 
 int ne_checksum(const void* c, int64_t ldc, int M, int64_t N, int w, void* r,
                 void* stream) {
+  NE_RANGE("ne_checksum");
   if (M < 1 || M > 64 || N < 0 || ldc < N || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;
@@ -564,6 +571,7 @@ int ne_checksum(const void* c, int64_t ldc, int M, int64_t N, int w, void* r,
 
 int ne_checksum_recover(const void* d, int64_t ldd, const void* e, int M,
                         int64_t Nout, int w, int f, void* out, void* stream) {
+  NE_RANGE("ne_checksum_recover");
   if (M < 1 || M > 64 || Nout < 0 || ldd < Nout ||
       (w != 32 && w != 64) || f < 0 || f >= M)
     return NE_ERR_INVALID_ARG;
@@ -582,6 +590,7 @@ int ne_checksum_recover(const void* d, int64_t ldd, const void* e, int M,
 
 int ne_scale(const void* x, int64_t ldx, int M, int64_t N, int64_t sc, int w,
              void* y, int64_t ldy, void* stream) {
+  NE_RANGE("ne_scale");
   if (M < 1 || N < 0 || ldx < N || ldy < N || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;
@@ -603,6 +612,7 @@ int ne_scale(const void* x, int64_t ldx, int M, int64_t N, int64_t sc, int w,
 
 int ne_add(const void* x, int64_t ldx, const void* z, int64_t ldz, int M,
            int64_t N, int w, void* y, int64_t ldy, void* stream) {
+  NE_RANGE("ne_add");
   if (M < 1 || N < 0 || ldx < N || ldz < N || ldy < N ||
       (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
@@ -625,6 +635,7 @@ int ne_add(const void* x, int64_t ldx, const void* z, int64_t ldz, int M,
 
 int ne_self_entangle(const void* g, int64_t N, int w, int l, void* out,
                      void* stream) {
+  NE_RANGE("ne_self_entangle");
   if (N < 0 || (w != 32 && w != 64) || l <= 0 || l >= w)
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;
@@ -641,6 +652,7 @@ int ne_self_entangle(const void* g, int64_t N, int w, int l, void* out,
 int ne_permute(const void* x, int64_t ldx, int M, int64_t N,
                const int64_t* perm, int w, void* y, int64_t ldy,
                int32_t* bad_count, void* stream) {
+  NE_RANGE("ne_permute");
   if (M < 1 || N < 0 || ldx < N || ldy < N || (w != 32 && w != 64))
     return NE_ERR_INVALID_ARG;
   if (N == 0) return NE_OK;

@@ -20,7 +20,11 @@ from dataclasses import dataclass
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libne.so")
+# NE_INDEX_CHECKS=1 selects the debug build (libne_debug.so: kernels that
+# check the indices of their key accesses, read by ne_debug_index_status)
+LIB_PATH = os.path.join(
+    _HERE, "libne_debug.so" if os.environ.get("NE_INDEX_CHECKS") == "1"
+    else "libne.so")
 
 NE_OK = 0
 NE_ERR_INVALID_ARG = 1
@@ -132,6 +136,10 @@ _SIGS = {
                               ctypes.POINTER(_u32), _vp], _i32),
     "ne_debug_set_fault": ([_i32, _u32], _i32),
     "ne_debug_set_dispatch": ([_i32], _i32),
+    "ne_debug_index_status": ([ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.POINTER(ctypes.c_uint64), _i32], _i32),
+    "ne_debug_index_selftest": ([ctypes.c_int64, ctypes.c_int64,
+                                 ctypes.POINTER(_u32)], _i32),
     "ne_protected_outer": ([_vp, _i64, _i32, _i64, _vp, _i64, _i32, _i32, _i64,
                             _i64, _i64, _i32, _i32, _vp, _i64, _vp], _i32),
 }
@@ -430,6 +438,25 @@ def ne_debug_set_dispatch(tensor_cores_always: bool) -> None:
     the default)."""
     _check(lib().ne_debug_set_dispatch(1 if tensor_cores_always else 0),
            "ne_debug_set_dispatch")
+
+
+def ne_debug_index_status(clear: bool = True) -> tuple[int, int]:
+    """(violations, first) of the debug build's index checks
+    (include/ne_debug.h); raises NEError(NE_ERR_UNSUPPORTED) from libne.so,
+    which has no checks."""
+    v, f = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().ne_debug_index_status(ctypes.byref(v), ctypes.byref(f),
+                                       int(clear)), "ne_debug_index_status")
+    return int(v.value), int(f.value)
+
+
+def ne_debug_index_selftest(i: int, n: int) -> int:
+    """Debug build: one GPU thread checks index i against extent n; returns
+    1 if the check passed, else 0 (the violation is then recorded)."""
+    hits = _u32()
+    _check(lib().ne_debug_index_selftest(int(i), int(n), ctypes.byref(hits)),
+           "ne_debug_index_selftest")
+    return int(hits.value)
 
 
 def ne_debug_set_fault(stall_role: int = 0, wait_polls: int = 0) -> None:

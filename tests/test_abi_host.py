@@ -334,3 +334,44 @@ def test_failstop_and_debug_argument_checks(ne):
     for v in (-1, 2):
         assert L.ne_debug_set_dispatch(v) == ne.NE_ERR_INVALID_ARG
     assert L.ne_debug_set_dispatch(0) == ne.NE_OK
+
+
+LAUNCHING_CALLS = [
+    "ne_conv", "ne_conv_range", "ne_conv_kind", "ne_protected_conv",
+    "ne_protected_conv_noalloc", "ne_fs_protected_conv", "ne_gemm",
+    "ne_protected_gemm", "ne_outer", "ne_protected_outer",
+    "ne_pipe_protected_conv", "ne_entangle", "ne_recover", "ne_extract",
+    "ne_recover_mask", "ne_dot", "ne_detect", "ne_checksum",
+    "ne_checksum_recover", "ne_scale", "ne_add", "ne_self_entangle",
+    "ne_permute", "ne_batch_prepare", "ne_batch_launch", "ne_batch_submit",
+    "ne_batch_graph_capture", "ne_batch_graph_launch", "ne_batch_autotune"]
+
+
+def test_every_launching_call_opens_an_nvtx_range():
+    """Each C-ABI call that enqueues GPU work names itself in an NVTX range
+    as its first statement, so a timeline attributes kernels to calls."""
+    csrc = os.path.join(ROOT, "paper_1509_03838_gb300", "csrc")
+    text = "".join(open(os.path.join(csrc, f)).read()
+                   for f in sorted(os.listdir(csrc)) if f.endswith(".cu"))
+    declared = set(declared_symbols())
+    for name in LAUNCHING_CALLS:
+        assert name in declared, name
+        m = re.search(r'^(?:extern "C" )?int ' + name + r'\([^{;]*?\)\s*\{\n'
+                      r'\s*NE_RANGE\("' + name + r'"\);', text, re.M)
+        assert m, name
+
+
+def test_index_checks_absent_from_the_default_build(ne):
+    """libne.so has no index checks: both debug readers say so before any
+    CUDA call, and reject null outputs."""
+    L = ctypes.CDLL(ne.LIB_PATH)
+    v, f, h = ctypes.c_uint64(9), ctypes.c_uint64(9), ctypes.c_uint32(9)
+    assert L.ne_debug_index_status(ctypes.byref(v), ctypes.byref(f), 0) == \
+        ne.NE_ERR_UNSUPPORTED
+    assert (v.value, f.value) == (0, 0)
+    assert L.ne_debug_index_selftest(ctypes.c_int64(0), ctypes.c_int64(1),
+                                     ctypes.byref(h)) == ne.NE_ERR_UNSUPPORTED
+    assert h.value == 0
+    assert L.ne_debug_index_status(None, ctypes.byref(f), 0) == ne.NE_ERR_INVALID_ARG
+    assert L.ne_debug_index_selftest(ctypes.c_int64(0), ctypes.c_int64(1),
+                                     None) == ne.NE_ERR_INVALID_ARG
