@@ -36,14 +36,19 @@ extern "C" {
 int ne_debug_set_fault(int stall_role, uint32_t wait_polls);
 
 /*
- * ne_debug_set_dispatch -- tensor_cores_always = 1: from now on the
- * convolution entry points take their tensor-core forms for every job
- * inside those forms' window, however small; 0 (the default): a job too
- * small to pay for the tensor-core kernels' set-up (an estimate of both
- * forms' time, measured on GB300) runs on the multiply-add kernels.  Lets
- * tests exercise the tensor-core kernels on small inputs.  The results are
- * the same either way.  Host-only; returns NE_OK, or NE_ERR_INVALID_ARG
- * for a value other than 0 or 1.
+ * ne_debug_set_dispatch -- how the convolution entry points choose between
+ * their tensor-core and multiply-add forms, from now on:
+ *   0 (the default): a job too small to pay for the tensor-core kernels'
+ *     set-up (an estimate of both forms' time, measured on GB300) runs on
+ *     the multiply-add kernels;
+ *   1: every job inside the tensor-core forms' window takes them, however
+ *     small;
+ *   2: as 1, and ne_conv_range and ne_protected_conv return
+ *     NE_ERR_UNSUPPORTED for a job the raw-plane tcgen05 kernel (with its
+ *     large-K form and tap pieces) does not take, instead of running
+ *     another form, so that a test knows which kernel produced its outputs.
+ * The results are the same under 0 and 1.  Host-only; returns NE_OK, or
+ * NE_ERR_INVALID_ARG for a value outside 0..2.
  */
 int ne_debug_set_dispatch(int tensor_cores_always);
 

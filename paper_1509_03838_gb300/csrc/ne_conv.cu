@@ -908,7 +908,12 @@ inline bool tcr_enabled() {
 // multiply-adds per second (half that when products need two
 // instructions, split = true).  Estimated times, in microseconds, measured
 // on GB300; the cheaper estimate wins.  nd: byte digits of the operands.
-std::atomic<int> g_debug_tc_always{0};  // ne_debug_set_dispatch
+// ne_debug_set_dispatch: 0 estimate, 1 tensor cores whenever their window
+// allows, 2 the raw-plane kernel required (NE_ERR_UNSUPPORTED otherwise)
+std::atomic<int> g_debug_tc_always{0};
+inline bool raw_plane_required() {
+  return g_debug_tc_always.load(std::memory_order_relaxed) == 2;
+}
 inline bool tensor_cores_pay(int streams, int64_t N, int64_t Nout, int K, int wb,
                              bool prot, bool split, int nd) {
   if (g_debug_tc_always.load(std::memory_order_relaxed)) return true;
@@ -938,10 +943,11 @@ std::atomic<int> g_debug_stall_role{0};
 
 // Fill the raw-plane fields of a for inputs in [lo, hi] (known range):
 // returns false if the job is outside these kernels' window.
-// The pool the plain large-K form takes its B tables from (ne_conv_range
-// has no workspace argument): one per device, created on first use; it
-// keeps up to 16 MiB mapped between calls (a table is at most 132 KiB), so
-// that a call allocates without a driver round trip.
+// The pool the plain large-K form takes its B tables (at most 132 KiB) and
+// the plain tap pieces their scratch from (ne_conv_range has no workspace
+// argument): one per device, created on first use; it keeps up to 256 MiB
+// mapped between calls, so that a call allocates without a driver round
+// trip.
 inline cudaMemPool_t table_pool() {
   static std::mutex mu;
   static cudaMemPool_t pools[64] = {};
@@ -958,7 +964,7 @@ inline cudaMemPool_t table_pool() {
       cudaGetLastError();
       return nullptr;
     }
-    uint64_t keep = 16ull << 20;
+    uint64_t keep = 256ull << 20;
     cudaMemPoolSetAttribute(pl, cudaMemPoolAttrReleaseThreshold, &keep);
     pools[dev] = pl;
   }
@@ -1044,6 +1050,7 @@ int protected_tc(const ConvArgs& a, int mode, int64_t max_abs_g, int w,
       if (st != NE_ERR_UNSUPPORTED) return st;
     }
   }
+  if (raw_plane_required()) return NE_ERR_UNSUPPORTED;
   if (!tc_eligible(mode, a.K, max_abs_g)) return kNotTaken;
   const int M = a.M, wb = w / 8;
   const bool vec_out = rows_aligned16(a.y, a.ldy, wb);
@@ -1076,6 +1083,118 @@ int protected_tc(const ConvArgs& a, int mode, int64_t max_abs_g, int w,
     return ne_recover(a.y, a.ldy, M, a.Nout, w, a.l, a.failed, a.y, a.ldy, s);
   }
   return kNotTaken;
+}
+
+// ---------------------------------------------------------------------------
+// Tap pieces.  A convolution with more taps than the large-K form holds
+// (K > 1025) runs piece by piece: the taps split into P pieces of at most
+// 1024, piece p holding taps [o_p, o_p + K_p), and by the linearity of the
+// operation (Eq. 9)
+//     y[n] = sum_p y_p[n - o_p],   y_p = x * g[o_p, o_p + K_p),
+// each y_p a full convolution of N + K_p - 1 outputs.  Protected, each y_p
+// is a protected convolution of its own, recovered exactly: its outputs are
+// bounded by K_p max|c| max|g|, inside the range checked for the whole K,
+// so the sum of the recovered pieces is the true output.  Piece 0 is
+// written straight into y, whose columns past it are zeroed first; every
+// later piece goes into scratch rows T and is added into y at its offset
+// (ne_add, modulo 2^w).
+// ---------------------------------------------------------------------------
+constexpr int kMaxPieces = 16;
+struct TapPieces {
+  int P = 0;    // pieces (0: the form does not apply)
+  int Kpc = 0;  // taps of every piece but the last (a multiple of 16)
+  int taps(int p, int K) const { return std::min(Kpc, K - p * Kpc); }
+};
+inline TapPieces tap_pieces(int K) {
+  TapPieces t;
+  if (K <= TR_HMAX_L + 1) return t;
+  t.P = (K + TR_HMAX_L - 1) / TR_HMAX_L;
+  t.Kpc = ((K + t.P - 1) / t.P + 15) / 16 * 16;
+  if (t.P > kMaxPieces || (t.P - 1) * t.Kpc >= K) t.P = 0;
+  return t;
+}
+// Scratch of the pieces form: rows of T (leading dimension a multiple of 16
+// words), then the large-K B table, 256-byte aligned.
+inline int64_t pieces_ld(int64_t N, const TapPieces& t) {
+  return (N + t.Kpc - 1 + 15) / 16 * 16;
+}
+inline size_t pieces_scratch_bytes(int rows, int64_t N, int K, int wb) {
+  const TapPieces t = tap_pieces(K);
+  if (t.P == 0 || N <= 0) return 0;
+  return (size_t)rows * (size_t)pieces_ld(N, t) * (size_t)wb + 256 +
+         tr_table_bytes(t.Kpc);
+}
+// The pieces' estimated time against the multiply-add kernels' (as
+// tensor_cores_pay; the large-K form issues its products at about one per
+// 140 ns per SM, measured on GB300, and each later piece adds one pass of
+// 3 reads/writes of its outputs).
+inline bool pieces_pay(int streams, int64_t N, int K, int wb, bool prot,
+                       bool split, int nd, const TapPieces& t) {
+  if (g_debug_tc_always.load(std::memory_order_relaxed)) return true;
+  const double imad_us =
+      6.0 + (double)streams * (double)N * (double)K * (split ? 2.0 : 1.0) / 6.1e6;
+  double tc_us = 0.0;
+  for (int p = 0; p < t.P; ++p) {
+    const int Kp = t.taps(p, K);
+    const int64_t Nout = N + Kp - 1;
+    const double bytes = (double)streams * (double)(N + Nout) * (double)wb;
+    const double ks = (double)((32 + 16 * ((Kp - 1 + 15) / 16)) / 16);
+    const double mmas = (double)streams * (double)((Nout + 4095) / 4096) * ks *
+                        (double)(nd > 0 ? nd : 4) * (prot ? 2.0 : 1.0);
+    tc_us += 21.0 + std::max(bytes / (prot ? 3.2e6 : 4.4e6), mmas * 0.14 / 152.0);
+    if (p > 0) tc_us += 3.0 + 3.0 * (double)streams * (double)Nout * wb / 6.0e6;
+  }
+  return tc_us < imad_us;
+}
+
+// a: the whole job (x, ldx, M, N, Nout, g, K, y, ldy, live_mask; protected:
+// l, failed, fail_mode).  scratch: pieces_scratch_bytes(a.M, a.N, a.K, wb)
+// bytes of device memory, 256-byte aligned, overlapping nothing else.
+// Returns kNotTaken, having launched nothing that matters (the caller's
+// other form then writes every output), when a piece is outside the
+// raw-plane kernel's window.
+int conv_pieces(const ConvArgs& a, bool prot, int w, __int128 lo, __int128 hi,
+                int64_t max_abs_g, bool vec, void* scratch, cudaStream_t s) {
+  const TapPieces t = tap_pieces(a.K);
+  if (t.P == 0 || !scratch) return kNotTaken;
+  const int wb = w / 8;
+  const int64_t ldT = pieces_ld(a.N, t);
+  unsigned char* T = static_cast<unsigned char*>(scratch);
+  void* tab = reinterpret_cast<void*>(
+      (reinterpret_cast<uintptr_t>(T) + (size_t)a.M * (size_t)ldT * wb + 255) &
+      ~(uintptr_t)255);
+  // every piece is planned before anything is launched
+  ConvArgs pa[kMaxPieces];
+  for (int p = 0; p < t.P; ++p) {
+    ConvArgs b = a;
+    b.K = t.taps(p, a.K);
+    b.g = a.g + (size_t)p * (size_t)t.Kpc;
+    b.Nout = a.N + b.K - 1;
+    b.btab = tab;
+    if (p > 0) {
+      b.y = T;
+      b.ldy = ldT;
+    }
+    if (!tcr_plan(b, prot, w, lo, hi, max_abs_g, vec, true)) return kNotTaken;
+    pa[p] = b;
+  }
+  const int64_t n0 = pa[0].Nout;  // the columns of y past piece 0 start at 0
+  if (a.Nout > n0 &&
+      cudaMemset2DAsync(static_cast<char*>(a.y) + (size_t)n0 * wb,
+                        (size_t)a.ldy * wb, 0, (size_t)(a.Nout - n0) * wb,
+                        (size_t)a.M, s) != cudaSuccess)
+    return NE_ERR_CUDA;
+  for (int p = 0; p < t.P; ++p) {
+    int st = dispatch_tcr(pa[p], prot, w, s);
+    if (st == NE_ERR_UNSUPPORTED) return kNotTaken;
+    if (st != NE_OK) return st;
+    if (p > 0) {
+      char* yo = static_cast<char*>(a.y) + (size_t)p * (size_t)t.Kpc * wb;
+      st = ne_add(yo, a.ldy, T, ldT, a.M, pa[p].Nout, w, yo, a.ldy, s);
+      if (st != NE_OK) return st;
+    }
+  }
+  return NE_OK;
 }
 
 }  // namespace
@@ -1183,6 +1302,49 @@ int ne_conv_range(const void* x, int64_t ldx, int M, int64_t N,
       a.btab = nullptr;
     }
   }
+  if (x_min <= x_max && (w == 32 || w == 64) && M >= 1 && M <= 32 && N > 0 &&
+      K > TR_HMAX_L + 1 && K <= CONV_MAX_K && ldx >= N && x && y && g &&
+      ldy >= N + K - 1 && forced_form() == FORM_AUTO &&
+      (M == 32 ? live_mask : (live_mask & ((1u << M) - 1u))) ==
+          (M == 32 ? 0xffffffffu : (1u << M) - 1u)) {
+    // tap pieces on the raw-plane kernel (every stream live), scratch from
+    // the library's pool
+    const int wb = w / 8;
+    const int64_t Nout = N + K - 1;
+    const TapPieces t = tap_pieces(K);
+    if (overlaps(x, rows_bytes(M, ldx, N, wb), y, rows_bytes(M, ldy, Nout, wb)))
+      return NE_ERR_INVALID_ARG;
+    if (t.P > 0 &&
+        pieces_pay(M, N, K, wb, false, (__int128)x_max - (__int128)x_min > 0xFFFFFFFF,
+                   tcr_digits((__int128)x_min, (__int128)x_max), t)) {
+      ConvArgs a{};
+      a.x = x;
+      a.ldx = ldx;
+      a.M = M;
+      a.N = N;
+      a.Nout = Nout;
+      a.g = g;
+      a.K = K;
+      a.y = y;
+      a.ldy = ldy;
+      a.live_mask = M == 32 ? 0xffffffffu : (1u << M) - 1u;
+      cudaStream_t s = (cudaStream_t)stream;
+      cudaMemPool_t pool = table_pool();
+      void* scratch = nullptr;
+      if (pool && cudaMallocFromPoolAsync(&scratch, pieces_scratch_bytes(M, N, K, wb),
+                                          pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        scratch = nullptr;
+      }
+      if (scratch) {
+        const int st = conv_pieces(a, false, w, (__int128)x_min, (__int128)x_max,
+                                   max_abs_g, rows_aligned16(x, ldx, wb), scratch, s);
+        cudaFreeAsync(scratch, s);
+        if (st != kNotTaken) return st;
+      }
+    }
+  }
+  if (raw_plane_required()) return NE_ERR_UNSUPPORTED;
   long long bias = 0;
   const int mode = (w == 32 || w == 64)
                        ? choose_mode(w, x_min <= x_max, (__int128)x_min,
@@ -1269,7 +1431,7 @@ int ne_debug_set_fault(int stall_role, uint32_t wait_polls) {
 }
 
 int ne_debug_set_dispatch(int tensor_cores_always) {
-  if (tensor_cores_always != 0 && tensor_cores_always != 1)
+  if (tensor_cores_always < 0 || tensor_cores_always > 2)
     return NE_ERR_INVALID_ARG;
   g_debug_tc_always.store(tensor_cores_always);
   return NE_OK;
@@ -1286,10 +1448,16 @@ inline size_t table_ws_bytes(int K) {
   return K > TR_HMAX + 1 && K <= TR_HMAX_L + 1 ? tr_table_bytes(K) + 256 : 0;
 }
 
+// The tap pieces' scratch (K > 1025) follows the arrival words, 256-byte
+// aligned; it is sized for 64-bit words.
+inline size_t pieces_ws_bytes(int M, int64_t N, int K) {
+  const size_t b = pieces_scratch_bytes(M, N, K, 8);
+  return b ? b + 256 : 0;
+}
+
 size_t ne_protected_conv_ws_bytes(int M, int64_t N, int K) {
-  (void)M;
-  if (N <= 0 || K <= 0) return 0;
-  return arrival_ws_bytes(N, K) + table_ws_bytes(K);
+  if (N <= 0 || K <= 0 || M <= 0) return 0;
+  return arrival_ws_bytes(N, K) + table_ws_bytes(K) + pieces_ws_bytes(M, N, K);
 }
 
 int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
@@ -1325,7 +1493,9 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const int wb = w / 8;
   if (overlaps(c, rows_bytes(M, ldc, N, wb), d, rows_bytes(M, ldd, Nout, wb)))
     return NE_ERR_INVALID_ARG;
-  const size_t need_ws = ne_protected_conv_ws_bytes(M, N, K);
+  // the arrival words (and a large-K table) are required; the tap pieces'
+  // scratch is used when it is there
+  const size_t need_ws = arrival_ws_bytes(N, K) + table_ws_bytes(K);
   if (!ws || ws_bytes < need_ws) return NE_ERR_NOMEM;
   cudaStream_t s = (cudaStream_t)stream;
   ConvArgs a{};
@@ -1358,6 +1528,22 @@ int ne_protected_conv(const void* c, int64_t ldc, int M, int64_t N,
   const int mode = choose_mode(w, true, (__int128)c_min * f,
                                (__int128)c_max * f, &a.bias);
   const bool vec = rows_aligned16(c, ldc, wb);
+  if (K > TR_HMAX_L + 1 && forced_form() == FORM_AUTO) {
+    // tap pieces on the raw-plane kernel, when the workspace holds their
+    // scratch
+    const TapPieces t = tap_pieces(K);
+    const uintptr_t ws0 = reinterpret_cast<uintptr_t>(ws);
+    const uintptr_t sp = (ws0 + arrival + 255) & ~(uintptr_t)255;
+    const size_t scratch = pieces_scratch_bytes(M, N, K, wb);
+    const __int128 espan = ((__int128)c_max - (__int128)c_min) * f;
+    if (t.P > 0 && scratch > 0 && ws_bytes >= (size_t)(sp - ws0) + scratch &&
+        pieces_pay(M, N, K, wb, true, espan > 0xFFFFFFFF,
+                   tcr_digits((__int128)c_min, (__int128)c_max), t)) {
+      const int st = conv_pieces(a, true, w, (__int128)c_min, (__int128)c_max,
+                                 max_abs_g, vec, reinterpret_cast<void*>(sp), s);
+      if (st != kNotTaken) return st;
+    }
+  }
   const int tc = protected_tc(a, mode, max_abs_g, w, vec, s, c_min, c_max, true);
   if (tc != kNotTaken) return tc;
   if (use_cluster(M, K, w, mode, a.ntiles)) {

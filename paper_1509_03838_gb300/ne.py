@@ -432,11 +432,13 @@ class FailStop:
         return self.last_late
 
 
-def ne_debug_set_dispatch(tensor_cores_always: bool) -> None:
+def ne_debug_set_dispatch(tensor_cores_always) -> None:
     """Test control: take the tensor-core forms for every job in their
-    window (True), or let small jobs run on the multiply-add kernels (False,
-    the default)."""
-    _check(lib().ne_debug_set_dispatch(1 if tensor_cores_always else 0),
+    window (True or 1), or let small jobs run on the multiply-add kernels
+    (False or 0, the default); 2 also makes ne_conv_range and
+    ne_protected_conv fail with NE_ERR_UNSUPPORTED where the raw-plane
+    kernel does not take the job (include/ne_debug.h)."""
+    _check(lib().ne_debug_set_dispatch(int(tensor_cores_always)),
            "ne_debug_set_dispatch")
 
 

@@ -331,7 +331,7 @@ def test_failstop_and_debug_argument_checks(ne):
     for role in (-1, 3):
         assert L.ne_debug_set_fault(role, 0) == ne.NE_ERR_INVALID_ARG
     assert L.ne_debug_set_fault(0, 0) == ne.NE_OK
-    for v in (-1, 2):
+    for v in (-1, 3):
         assert L.ne_debug_set_dispatch(v) == ne.NE_ERR_INVALID_ARG
     assert L.ne_debug_set_dispatch(0) == ne.NE_OK
 
@@ -375,3 +375,14 @@ def test_index_checks_absent_from_the_default_build(ne):
     assert L.ne_debug_index_status(None, ctypes.byref(f), 0) == ne.NE_ERR_INVALID_ARG
     assert L.ne_debug_index_selftest(ctypes.c_int64(0), ctypes.c_int64(1),
                                      None) == ne.NE_ERR_INVALID_ARG
+
+
+def test_protected_workspace_holds_the_tap_pieces(ne):
+    """K > 1025: the workspace adds the tap pieces' scratch rows (M rows of
+    at least N + K_p - 1 words of 8 bytes, K_p = 912 for K = 4500) and
+    their B table; K <= 1025 needs none of it."""
+    base = ne.ne_protected_conv_ws_bytes(3, 1000, 1000)
+    big = ne.ne_protected_conv_ws_bytes(3, 1000, 4500)
+    assert big >= 3 * (1000 + 912 - 1) * 8 + base // 4
+    # K = 1025: arrival words and the large-K table (at most 132 KiB) only
+    assert ne.ne_protected_conv_ws_bytes(3, 1000, 1025) < 140 * 1024

@@ -229,8 +229,9 @@ def test_tcr_large_k_plain(ne, orc, case):
     expect = conv_par(orc, x, g, w, strict=False)
     buf = torch.full((M, N + K - 1 + pad), 5, dtype=dt(w), device="cuda")
     y = buf[:, :N + K - 1]
-    ne.ne_conv(dev(x, w), torch.from_numpy(g.astype(np.int32)).cuda(),
-               y, x_range=(lo, hi), max_abs_g=gmax)
+    with raw_plane_required(ne):
+        ne.ne_conv(dev(x, w), torch.from_numpy(g.astype(np.int32)).cuda(),
+                   y, x_range=(lo, hi), max_abs_g=gmax)
     torch.cuda.synchronize()
     assert np.array_equal(host(y), expect)
     if pad:
@@ -269,16 +270,125 @@ def test_tcr_large_k_protected_every_failure(ne, orc, case):
     Nout = N + K - 1
     cd = dev(c, w)
     gd = torch.from_numpy(g.astype(np.int32)).cuda()
-    for fm, r in modes(ne, M):
-        dfull = torch.full((M, Nout + padd), 77, dtype=dt(w), device="cuda")
-        d = dfull[:, :Nout]
-        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(1 << bc), (1 << bc) - 1),
-                             max_abs_g=(1 << bg) - 1, failed=r, fail_mode=fm)
-        torch.cuda.synchronize()
-        assert np.array_equal(host(d), plain), (fm, r)
-        if padd:
-            assert (dfull[:, Nout:] == 77).all(), (fm, r)
+    with raw_plane_required(ne):
+        for fm, r in modes(ne, M):
+            dfull = torch.full((M, Nout + padd), 77, dtype=dt(w), device="cuda")
+            d = dfull[:, :Nout]
+            ne.ne_protected_conv(cd, gd, d, l=p.l,
+                                 c_range=(-(1 << bc), (1 << bc) - 1),
+                                 max_abs_g=(1 << bg) - 1, failed=r, fail_mode=fm)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(d), plain), (fm, r)
+            if padd:
+                assert (dfull[:, Nout:] == 77).all(), (fm, r)
     assert ne.ne_get_device_error(clear=True) == 0
+
+
+class raw_plane_required:
+    """Within: a job the raw-plane kernel does not take fails with
+    NE_ERR_UNSUPPORTED instead of running another form."""
+
+    def __init__(self, ne):
+        self.ne = ne
+
+    def __enter__(self):
+        self.ne.ne_debug_set_dispatch(2)
+
+    def __exit__(self, *exc):
+        self.ne.ne_debug_set_dispatch(1)
+
+
+PIECES_PLAIN = [
+    # w, M, N, K, [lo, hi], max|g|, output row padding   (K > 1025: tap pieces)
+    (64, 3, 2 * TILE + 77, 1100, (-2**15, 2**15 - 1), 2**15, 0),   # 2 pieces
+    (64, 1, 3000, 4500, (-2**15, 2**15 - 1), 2**15, 1),           # 5 pieces, N < K
+    (32, 2, 5000, 2500, (-2**7, 2**7 - 1), 2**7, 0),              # 32-bit words
+    (64, 2, 7000, 2049, (-2**23, 2**23 - 1), 2**15, 3),           # 3 digits, odd ld
+]
+
+
+@pytest.mark.parametrize("case", PIECES_PLAIN)
+def test_tcr_tap_pieces_plain(ne, orc, case):
+    """K > 1025: the taps split into pieces of at most 1024, each a
+    large-K convolution, added at its offset (Eq. 9 is linear in g); every
+    output against the oracle's convolution with all K taps, nothing written
+    past the rows."""
+    w, M, N, K, (lo, hi), gmax, pad = case
+    gen = synth.rng(N * 3 + K + M + w)
+    x = synth.uniform_int(gen, (M, N), lo, hi + 1)
+    x[:, 0] = hi
+    x[:, -1] = lo
+    g = synth.uniform_int(gen, (K,), -gmax + 1, gmax)
+    g[0] = gmax
+    g[-1] = -gmax + 1
+    expect = conv_par(orc, x, g, w, strict=False)
+    buf = torch.full((M, N + K - 1 + pad), 5, dtype=dt(w), device="cuda")
+    y = buf[:, :N + K - 1]
+    with raw_plane_required(ne):
+        ne.ne_conv(dev(x, w), torch.from_numpy(g.astype(np.int32)).cuda(),
+                   y, x_range=(lo, hi), max_abs_g=gmax)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), expect)
+    if pad:
+        assert (buf[:, N + K - 1:] == 5).all()
+    assert ne.ne_get_device_error(clear=True) == 0
+
+
+PIECES_PROT = [
+    # w, M, N, K, data bits, tap bits, pad d
+    (64, 3, 6000, 4500, 13, 14, 0),          # l = 22, 5 pieces
+    (64, 8, 2 * TILE + 9, 2000, 14, 14, 1),  # M = 8, l = 8, 2 pieces, odd ld
+    (64, 4, 300, 1500, 15, 15, 0),           # N < K
+    (32, 3, 5000, 1500, 4, 5, 0),            # 32-bit words, l = 11
+]
+
+
+@pytest.mark.parametrize("case", PIECES_PROT)
+def test_tcr_tap_pieces_protected_every_failure(ne, orc, case):
+    """K > 1025, protected: every piece a protected convolution recovered
+    exactly (its outputs lie inside the range checked for all K taps), the
+    recovered pieces added at their offsets; every failure mode."""
+    w, M, N, K, bc, bg, padd = case
+    p = ne.ne_params(M, w)
+    gen = synth.rng(N + 19 * K + M + w)
+    c = synth.uniform_int(gen, (M, N), -(1 << bc), 1 << bc)
+    c[:, 0] = (1 << bc) - 1
+    c[:, -1] = -(1 << bc)
+    g = synth.uniform_int(gen, (K,), -(1 << bg) + 1, 1 << bg)
+    g[0] = (1 << bg) - 1
+    assert K * (1 << bc) * ((1 << bg) - 1) <= p.d_max_exact
+    plain = conv_par(orc, c, g, w)
+    Nout = N + K - 1
+    cd = dev(c, w)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    with raw_plane_required(ne):
+        for fm, r in modes(ne, M):
+            dfull = torch.full((M, Nout + padd), 77, dtype=dt(w), device="cuda")
+            d = dfull[:, :Nout]
+            ne.ne_protected_conv(cd, gd, d, l=p.l,
+                                 c_range=(-(1 << bc), (1 << bc) - 1),
+                                 max_abs_g=(1 << bg) - 1, failed=r, fail_mode=fm)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(d), plain), (fm, r)
+            if padd:
+                assert (dfull[:, Nout:] == 77).all(), (fm, r)
+    assert ne.ne_get_device_error(clear=True) == 0
+
+
+def test_raw_plane_required_refuses_other_forms(ne):
+    """Dispatch mode 2 reports a job outside the raw-plane kernel's window
+    (here: |g| above 2^15) instead of running another form, so that the
+    tests above know which kernel wrote their outputs."""
+    x = torch.zeros((3, 5000), dtype=torch.int64, device="cuda")
+    g = torch.ones(200, dtype=torch.int32, device="cuda")
+    y = torch.empty((3, 5199), dtype=torch.int64, device="cuda")
+    with raw_plane_required(ne):
+        with pytest.raises(ne.NEError) as e:
+            ne.ne_conv(x, g, y, x_range=(-5, 5), max_abs_g=1 << 20)
+    assert e.value.status == ne.NE_ERR_UNSUPPORTED
+    ne.ne_conv(x, g, y, x_range=(-5, 5), max_abs_g=1 << 20)  # other forms
+    torch.cuda.synchronize()
+    assert int(y.abs().sum()) == 0
 
 
 def test_tcr_protected_full_size_every_output(ne, orc):
