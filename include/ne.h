@@ -147,15 +147,22 @@ int ne_conv(const void *x, int64_t ldx, int M, int64_t N, const int32_t *g,
 
 /*
  * ne_conv_range -- ne_conv with the taps' range declared as well: every
- * |g[t]| <= max_abs_g.  When the operands fit 32 bits (32-bit words, or
- * 64-bit words whose declared range spans at most 2^32 values), K <= 65 and
- * max_abs_g <= 32768, the convolution runs on the tensor cores, exactly:
- * operand and taps are split into byte digits that fp16 holds exactly,
- * every digit product and every fp32 partial sum is an exact integer
- * below 2^24, and the outputs are assembled in 64-bit integers.  Otherwise
- * it is ne_conv.  Same arguments, layouts and errors as ne_conv, plus
- * NE_ERR_INVALID_ARG for max_abs_g < 0.  A tap beyond max_abs_g gives
- * undefined outputs (no fault).
+ * |g[t]| <= max_abs_g.  When the declared ranges allow it, the convolution
+ * runs on the tensor cores, exactly: the inputs, shifted by the bottom of
+ * their range, are split into 1 to 4 byte digits (3 at most for K > 65)
+ * and the taps into 2 (max_abs_g <= 32768); fp16 holds every digit
+ * exactly, every fp32 partial sum is an integer of at most 2^24 (longer
+ * tap runs are drained into 64-bit sums), and the outputs are assembled in
+ * 64-bit integers, modulo 2^w.  One warp-specialised tcgen05 kernel per
+ * call: K <= 65 with the taps resident in shared memory; 66 <= K <= 1025
+ * with them streamed from a table the call builds in memory from the
+ * library's pool; K > 1025 in pieces of at most 1024 taps, each piece's
+ * outputs added at its offset (scratch rows from the same pool; every
+ * stream live).  Jobs too small to pay for that kernel's set-up, and
+ * ranges outside it, run as ne_conv (or, for K <= 65 and spans of at most
+ * 2^32 values, on the earlier mma.sync kernels).  Same arguments, layouts
+ * and errors as ne_conv, plus NE_ERR_INVALID_ARG for max_abs_g < 0.  A tap
+ * beyond max_abs_g gives undefined outputs (no fault).
  */
 int ne_conv_range(const void *x, int64_t ldx, int M, int64_t N,
                   const int32_t *g, int K, int64_t max_abs_g, void *y,
@@ -266,24 +273,31 @@ int ne_detect(const void *delta, int64_t ldd, int M, int64_t Nout, int w,
  *      [c_min(2^l+1), c_max(2^l+1)].
  *   failed, fail_mode: failure injection (failed in [0, M) or -1 with
  *      NE_FAIL_NONE).
- *   ws: device workspace of ne_protected_conv_ws_bytes() bytes (per-tile
- *      arrival words of the multiply-add form; zeroed by this call on
- *      `stream` when that form runs); ws_bytes its size.
- * Kernels.  When the entangled words fit 32 bits (a span of at most 2^32
- * values, after the range shift), K <= 65 and max_abs_g <= 32768, the
- * products run on the tensor cores, exactly (as in ne_conv_range):
- *   3 <= M <= 4 and 16-byte-aligned rows of c: one warp-specialised tcgen05
- *      kernel; the products stay in tensor memory and the recovery runs in
- *      its epilogue; d is written once;
- *   M <= 8 otherwise: one mma.sync kernel per output tile of all streams,
- *      products in shared memory;
- *   M > 8: an entangling product into d, then the recovery in place.
- * Other jobs run on the integer multiply-add kernels (one 32x32->64
- * multiply-add per tap for a span of at most 2^32 values, see ne_conv): a
- * cluster per tile for short tiles, else per-tile arrival words, where d
- * is also the landing buffer of the entangled tiles and a late M-th stream
- * discards its result.  Waits inside a kernel are bounded; if one expires
- * the outputs are incomplete and ne_get_device_error reports it.
+ *   ws: device workspace of ne_protected_conv_ws_bytes() bytes: per-tile
+ *      arrival words of the multiply-add form (zeroed by this call on
+ *      `stream` when that form runs), the large-K form's tap table, and for
+ *      K > 1025 the tap pieces' scratch rows; ws_bytes its size.  A
+ *      workspace without the pieces' part (NE_ERR_NOMEM below the rest)
+ *      runs such a job on the multiply-add kernels.
+ * Kernels.  When the inputs span at most 2^16 values (two byte digits,
+ * after the shift by c_min), max_abs_g <= 32768 and the job is large enough
+ * to pay for its set-up, one warp-specialised tcgen05 kernel does it all:
+ * it stages the byte-digit planes of the raw rows, forms each stream's
+ * entangled product in tensor memory from its own and its neighbour's
+ * planes, recovers the M outputs of every tile in its epilogue and writes
+ * d once.  Its windows: 3 <= M <= 6 for K <= 65 (taps resident), 3 <= M
+ * <= 8 for 66 <= K <= 1025 (taps streamed from the workspace's table) and
+ * for K > 1025 (pieces of at most 1024 taps, each recovered exactly and
+ * added at its offset in the workspace's scratch).  Otherwise, for K <= 65
+ * and entangled words spanning at most 2^32 values: the earlier tensor-core
+ * kernels (tcgen05 on entangled digits for M <= 4, mma.sync for M <= 8, an
+ * entangling product and an in-place recovery beyond).  Other jobs run on
+ * the integer multiply-add kernels (one 32x32->64 multiply-add per tap for
+ * a span of at most 2^32 values, see ne_conv): a cluster per tile for
+ * short tiles, else per-tile arrival words, where d is also the landing
+ * buffer of the entangled tiles and a late M-th stream discards its
+ * result.  Waits inside a kernel are bounded; if one expires the outputs
+ * are incomplete and ne_get_device_error reports it.
  */
 int ne_protected_conv(const void *c, int64_t ldc, int M, int64_t N,
                       const int32_t *g, int K, int w, int l, int64_t c_min,

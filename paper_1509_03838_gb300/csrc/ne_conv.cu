@@ -986,12 +986,17 @@ inline bool tcr_plan(ConvArgs& a, bool prot, int w, __int128 lo, __int128 hi,
   a.lk = lk ? 1 : 0;
   a.hist = 16 * ((a.K - 1 + 15) / 16);
   a.ks = (TR_P + a.hist) / 16;
-  // protected, l = 8 q with q <= nd (M = 4 only): the neighbour's levels
-  // q .. q + nd share the stream's own columns; a merged level gathers at
-  // most P products per tap (P = own pairs + neighbour pairs at that
-  // level), exact while P K 2^14 <= 2^22
+  // protected, l = 8 q with q <= nd: the neighbour's levels q .. q + nd
+  // share the stream's own columns.  Small form (M = 4 only): a merged
+  // level gathers at most P products per tap (P = own pairs + neighbour
+  // pairs at that level), exact while P K 2^14 <= 2^22.
   a.mlev = 0;
-  if (!lk && prot && a.M == 4 && a.l % 8 == 0 && a.l / 8 >= 1 && a.l / 8 <= nd) {
+  if (lk && prot && (a.M == 4 || a.M == 8) && a.l % 8 == 0 && a.l / 8 >= 1 &&
+      a.l / 8 <= nd && (a.M == 4 || a.l == 8)) {
+    // large K: merged for M = 4 and M = 8; the accumulator groups shrink so
+    // that a merged level stays exact (tr_group)
+    a.mlev = a.l / 8;
+  } else if (!lk && prot && a.M == 4 && a.l % 8 == 0 && a.l / 8 >= 1 && a.l / 8 <= nd) {
     const int q = a.l / 8;
     int pmax = 0;
     for (int L = 0; L <= nd + q; ++L) {

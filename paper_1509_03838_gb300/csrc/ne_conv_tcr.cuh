@@ -109,7 +109,29 @@ constexpr int TR_TAPS_L = TR_HMAX_L + 32;       // taps kept (K <= 1025)
 // (the prefix sums run over the taps 32 at a time)
 static_assert(TR_TAPS % 32 == 0 && TR_TAPS_L % 32 == 0, "tap arrays in warps");
 constexpr int TR_NBR = 16;                      // B blocks in the ring
-constexpr int TR_GROUP = 32;                    // k-steps per accumulator group
+
+// k-steps per accumulator group of the large-K form.  At most P digit pairs
+// (i, j) meet in one level (P = 2 with the neighbour's levels apart; its
+// pairs and the stream's own add up when the levels are merged, Q > 0),
+// each pair adds at most 2^14 per tap and a k-step has 16 taps; every fp32
+// partial sum stays an integer of magnitude at most 2^24 while
+// P * 2^14 * 16 * G <= 2^24, i.e. G <= 64 / P (at most 32).
+template <int ND, int Q>
+constexpr int tr_group() {
+  int pmax = 1;
+  for (int L = 0; L <= ND + Q + 1; ++L) {
+    int pairs = 0;
+    for (int i = 0; i < ND; ++i)
+      for (int j = 0; j < 2; ++j)
+        pairs += (i + j == L ? 1 : 0) + (Q > 0 && Q + i + j == L ? 1 : 0);
+    pmax = pairs > pmax ? pairs : pmax;
+  }
+  return 64 / pmax > 32 ? 32 : 64 / pmax;
+}
+static_assert(tr_group<2, 0>() == 32 && tr_group<3, 0>() == 32 &&
+                  tr_group<2, 1>() == 21 && tr_group<2, 2>() == 32 &&
+                  tr_group<1, 1>() == 32,
+              "accumulator groups");
 
 // Geometry of a form: history, staged samples per row, bytes per chunk
 // column and per digit plane.
@@ -375,6 +397,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
   constexpr int NTAPS = LK ? TR_TAPS_L : TR_TAPS;
   constexpr int NLEV = ND + 1;                    // levels per plane set
   constexpr int NLM = ND + Q + 1;                 // merged levels (Q > 0)
+  constexpr int GROUP = tr_group<ND, Q>();        // large K: k-steps per group
   const int H = p.hist, KS = p.ks;
   const int S = TR_TILE + H;                      // staged samples per row
   const int tcols = p.tcols, tslots = p.tslots;   // tensor-memory slots
@@ -683,9 +706,11 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
   } else if (warp == TR_WMMA) {
     // ---- MMA issue (one lane) ---------------------------------------------
     if (LK && lane == 0 && p.stall_role != 2) {
-      // Large K: per stream, groups of at most TR_GROUP k-steps accumulate
+      // Large K: per stream, groups of at most GROUP k-steps accumulate
       // onto a cleared slot (every fp32 partial sum an integer of magnitude
-      // at most 2 * 2^14 * 16 * 32 = 2^24).  The B blocks come from the
+      // at most 2^24, see tr_group); with merged levels (Q > 0) the
+      // neighbour's products land Q levels up in the stream's own columns.
+      // The B blocks come from the
       // table: all of them once, kept in the ring, when there are at most
       // TR_NBR (K <= 225); else through the ring, requested by this lane
       // TR_NBR / 2 blocks ahead, so that a slot it refills was last read
@@ -747,7 +772,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
           const uint32_t pao = a_lo0 + (uint32_t)so.idx * SLOT16;
           const uint32_t pan = a_lo0 + (uint32_t)sn.idx * SLOT16;
 #pragma unroll 1
-          for (int g0 = 0; g0 < KS && ok; g0 += TR_GROUP, ++sc) {
+          for (int g0 = 0; g0 < KS && ok; g0 += GROUP, ++sc) {
             const int ts = (int)(sc % (uint32_t)tslots);
             if (!tr_wait(&bars.acc_empty[ts], ((sc / tslots) & 1u) ^ 1u, abort, lim)) {
               ok = false;
@@ -755,8 +780,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
             }
             t5_fence_after();
             const uint32_t dcol = tb + (uint32_t)(ts * tcols);
-            const uint32_t dn = dcol + 32u * NLEV;
-            const int g1 = g0 + TR_GROUP < KS ? g0 + TR_GROUP : KS;
+            const uint32_t dn = dcol + 32u * (Q > 0 ? Q : NLEV);
+            const int g1 = g0 + GROUP < KS ? g0 + GROUP : KS;
             if (resident) {
               // every block at hand: one digit's chain of k-steps after
               // another (consecutive products into the same columns)
@@ -1139,12 +1164,15 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
         ++sc;
         return true;
       } else {
-        constexpr int NLS = PROT ? 2 * NLEV : NLEV;  // levels of a slot
+        // levels read as one sum (the own levels; all of them when merged),
+        // and levels of a slot
+        constexpr int NLO = (PROT && Q > 0) ? NLM : NLEV;
+        constexpr int NLS = (PROT && Q == 0) ? 2 * NLEV : NLO;
         unsigned long long acc[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) acc[e] = 0ull;
 #pragma unroll 1
-        for (int g0 = 0; g0 < KS; g0 += TR_GROUP) {
+        for (int g0 = 0; g0 < KS; g0 += GROUP) {
           const int ts = (int)(sc % (uint32_t)tslots);
           const uint32_t ph = (sc / tslots) & 1u;
           bool got = true;
@@ -1153,19 +1181,19 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
           t5_fence_after();
           const uint32_t base = tl + (uint32_t)(ts * tcols);
           if (rd) {
-            uint32_t u[NLEV][8];
+            uint32_t u[NLO][8];
 #pragma unroll
-            for (int L = 0; L < NLEV; ++L) tr_ld8(base + 32u * L, u[L]);
+            for (int L = 0; L < NLO; ++L) tr_ld8(base + 32u * L, u[L]);
             t5_wait_ld();
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               unsigned long long v = 0ull;
 #pragma unroll
-              for (int L = 0; L < NLEV; ++L)
+              for (int L = 0; L < NLO; ++L)
                 v += (unsigned long long)(long long)tr_f2i(u[L][e]) << (8 * L);
               acc[e] += v;
             }
-            if constexpr (PROT) {
+            if constexpr (PROT && Q == 0) {
               // the neighbour's levels, 2^l above (Eq. 6)
 #pragma unroll
               for (int L = 0; L < NLEV; ++L) tr_ld8(base + 32u * (NLEV + L), u[L]);
@@ -1352,8 +1380,18 @@ int tr_launch_one(const ConvArgs& a, const CUtensorMap* tm, cudaStream_t s) {
 template <typename W, bool PROT, int MM, int YS, bool LK>
 int tr_launch_nd(const ConvArgs& a, const CUtensorMap* tm, cudaStream_t s) {
   if constexpr (LK) {
-    // large K: the neighbour's levels apart (Q = 0); up to 2 digits
-    // protected, 3 plain (shared memory)
+    // large K: up to 2 digits protected, 3 plain (shared memory); the
+    // neighbour's levels merged for M = 4 (l = 8, 16) and M = 8 (l = 8),
+    // else apart (Q = 0)
+    if constexpr (PROT && (MM == 4 || MM == 8)) {
+      if (a.mlev == 1)
+        return a.nd == 1 ? tr_launch_one<W, PROT, MM, 1, 1, YS, LK>(a, tm, s)
+                         : tr_launch_one<W, PROT, MM, 2, 1, YS, LK>(a, tm, s);
+      if constexpr (MM == 4)
+        if (a.mlev == 2 && a.nd == 2)
+          return tr_launch_one<W, PROT, MM, 2, 2, YS, LK>(a, tm, s);
+      if (a.mlev != 0) return NE_ERR_UNSUPPORTED;
+    }
     if (a.nd == 1) return tr_launch_one<W, PROT, MM, 1, 0, YS, LK>(a, tm, s);
     if (a.nd == 2) return tr_launch_one<W, PROT, MM, 2, 0, YS, LK>(a, tm, s);
     if constexpr (!PROT)

@@ -247,8 +247,10 @@ LARGE_PROT = [
     (64, 6, 4000, 513, 10, 12, 0),            # l = 11
     (32, 3, 4096, 66, 6, 7, 0),               # 32-bit words, K = 66
     (64, 4, 200, 1025, 15, 15, 0),            # N < K, K = 1025
-    (64, 8, 2 * TILE + 9, 100, 14, 14, 0),    # M = 8, l = 8
+    (64, 8, 2 * TILE + 9, 100, 14, 14, 0),    # M = 8, l = 8: merged at level 1
     (64, 7, 3000, 300, 12, 12, 1),            # M = 7, l = 10
+    (64, 8, 5000, 1000, 14, 14, 0),           # merged, 4 groups of <= 21 k-steps
+    (32, 4, 5000, 300, 5, 6, 0),              # 32-bit words, l = 8, one digit: merged
 ]
 
 
@@ -489,6 +491,31 @@ def test_tcr_extreme_operands_protected(ne, orc):
                              max_abs_g=2**15, failed=r, fail_mode=fm)
         torch.cuda.synchronize()
         assert np.array_equal(host(d), plain), (fm, r)
+
+
+@pytest.mark.parametrize("M,K", [(8, 1000), (4, 700)])
+def test_tcr_large_k_protected_extreme_operands(ne, orc, M, K):
+    """The large-K form with the neighbour's levels merged (M = 8: l = 8,
+    groups of 21 k-steps; M = 4: l = 16, groups of 32): 16-bit data at both
+    ends of the range and extreme taps, every failure mode."""
+    w, N = 64, 2 * TILE + 65
+    p = ne.ne_params(M, w)
+    vals = [-(2**15), 2**15 - 1, -1, 0, 0xFF, -0x100, 0x7F00, -0x7F01]
+    c = _extreme_streams(M, N, vals, 10 + M)
+    gen = synth.rng(11 + M)
+    g = np.asarray(EXTREME_G, dtype=np.int64)[gen.integers(0, len(EXTREME_G), size=K)]
+    g[::3] = -(2**15)
+    assert K * (2**15) * (2**15) <= p.d_max_exact
+    plain = conv_par(orc, c, g, w)
+    cd = dev(c, w)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    with raw_plane_required(ne):
+        for fm, r in modes(ne, M):
+            d = torch.full((M, N + K - 1), 3, dtype=torch.int64, device="cuda")
+            ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(2**15), 2**15 - 1),
+                                 max_abs_g=2**15, failed=r, fail_mode=fm)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(d), plain), (fm, r)
 
 
 def _child_run(env_extra, select):
