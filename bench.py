@@ -265,7 +265,8 @@ def run_reference(args):
 
 def timed(fn, steps, world, stream, per_launch=False):
     """Run fn(i) `steps` times between barriers and synchronisations; return
-    (total ms max over ranks, per-launch ms list)."""
+    (this rank's total ms, per-launch ms list).  Callers take the maximum
+    over ranks (max_over_ranks)."""
     import torch
     ev = []
     barrier(world)
@@ -632,7 +633,8 @@ def run_ne(args):
             else bench_gemm(ne, dev, stream, probe["imad_wide"] / 1e12,
                             probe["wide_plus_imad32"] / 1e12))
     pipeline = None if args.no_pipeline else bench_pipeline(ne, dev, stream)
-    batch = None if args.no_batch else bench_batch(ne, synth, dev, stream)
+    batch = None if args.no_batch else bench_batch(ne, synth, dev, stream,
+                                                   world, rank)
     served = None if args.no_serve else bench_serve(ne, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -981,17 +983,23 @@ def bench_gemm(ne, dev, stream, peak_wide, peak_split, reps=10):
     return rows
 
 
-def bench_batch(ne, synth, dev, stream):
+def bench_batch(ne, synth, dev, stream, world=1, rank=0):
     """4096 independent protected jobs (M in {3..8}, N log-uniform in
     [2^10, 2^18], K in {8..256}, 16-bit data and taps, 64-bit words, one
     failed stream each): one autotuned persistent launch replayed from a
     captured CUDA graph, vs one ne_protected_conv launch per job.  Inputs
     are drawn on the device from a seeded generator (same shapes as the
-    parity test's host-drawn inputs)."""
+    parity test's host-drawn inputs).  On several ranks each runs its share
+    of the jobs (shard.py, balanced by multiply-adds); times are the
+    slowest rank's."""
     import torch
+    from paper_1509_03838_gb300 import shard
     spec = synth.batch_spec(seed=3)
-    n = len(spec)
-    M, N, K = spec.M, spec.N, spec.K
+    mine = np.asarray(shard.my_jobs(shard.job_costs(spec.M, spec.N, spec.K),
+                                    world, rank), dtype=np.int64)
+    n = len(mine)
+    M, N, K = spec.M[mine], spec.N[mine], spec.K[mine]
+    failed = spec.failed[mine]
     cw = int((M * N).sum())
     dw = int((M * (N + K - 1)).sum())
     gw = int(K.sum())
@@ -1012,19 +1020,19 @@ def bench_batch(ne, synth, dev, stream):
         co += m * nn
         go += k
         do += m * (nn + k - 1)
-        f = int(spec.failed[i])
+        f = int(failed[i])
         views.append((c, g, d, f))
         jobs.append(ne.make_job(c, g, d, c_range=(-(1 << 15), (1 << 15) - 1),
                                 max_abs_g=1 << 15, failed=f,
                                 fail_mode=ne.NE_FAIL_DROP))
-    macs = float((M * N * K).sum())
+    macs = float((spec.M * spec.N * spec.K).sum())  # every rank's jobs
     b = ne.Batch()
     threads, bps, _ = b.autotune(jobs, reps=1)
     b.capture_graph()
     b.launch_graph()
     reps = 5
-    t_graph, _ = timed(lambda i: b.launch_graph(), reps, 1, stream)
-    ms_batch = t_graph / reps
+    t_graph, _ = timed(lambda i: b.launch_graph(), reps, world, stream)
+    ms_batch = max_over_ranks(t_graph, world, dev) / reps
     ws = torch.empty(max(ne.ne_protected_conv_ws_bytes(int(M[i]), int(N[i]),
                                                        int(K[i]))
                          for i in range(n)), dtype=torch.uint8, device=dev)
@@ -1036,13 +1044,15 @@ def bench_batch(ne, synth, dev, stream):
                                  max_abs_g=1 << 15, failed=f,
                                  fail_mode=ne.NE_FAIL_DROP, ws=ws)
     per_job(0)
-    t_loop, _ = timed(per_job, 2, 1, stream)
-    ms_loop = t_loop / 2
+    t_loop, _ = timed(per_job, 2, world, stream)
+    ms_loop = max_over_ranks(t_loop, world, dev) / 2
     b.close()
     del cbuf, dbuf, gbuf, views, jobs
     return {"workload": "4096 jobs, M in {3..8}, N log-uniform [2^10,2^18], "
                         "K in {8..256}, 16-bit data/taps, 64-bit words, one "
-                        "failed stream per job",
+                        "failed stream per job" +
+                        (f", sharded over {world} ranks by multiply-adds"
+                         if world > 1 else ""),
             "macs": macs, "ms_graph_launch": ms_batch,
             "gops_batched": 2 * macs / (ms_batch * 1e-3) / 1e9,
             "ms_one_launch_per_job": ms_loop,

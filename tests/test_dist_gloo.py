@@ -47,3 +47,62 @@ def test_two_gloo_ranks_max_timing_and_independent_jobs():
         res = dict(out)
     assert res[0][0] == res[1][0] == 2.0          # max over ranks on both
     assert res[0][1:] != res[1][1:]               # different jobs per rank
+
+
+def _shard_rank_main(rank, world, port, out):
+    """One rank: its share of the 4096-job batch (shard.py), each job
+    planned by the library's host calls, the plans gathered over gloo
+    (host metadata only; no job data crosses ranks)."""
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(world),
+                       "LOCAL_RANK": str(rank), "MASTER_ADDR": "127.0.0.1",
+                       "MASTER_PORT": str(port)})
+    import bench
+    import torch.distributed as dist
+    from paper_1509_03838_gb300 import ne, shard, synth
+    w, r, _ = bench.dist_env()
+    bench.init_dist(w, "gloo")
+    spec = synth.batch_spec(seed=3)
+    mine = shard.my_jobs(shard.job_costs(spec.M, spec.N, spec.K), w, r)
+    plans = []
+    for i in mine:
+        m, n, k = int(spec.M[i]), int(spec.N[i]), int(spec.K[i])
+        p = ne.ne_choose_width(m, k, 1 << 15, 1 << 15)
+        plans.append((i, p.w, p.l, ne.ne_protected_conv_ws_bytes(m, n, k)))
+    got = [None] * w
+    dist.all_gather_object(got, plans)
+    out[rank] = got
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_the_batch_and_plan_it_with_the_library():
+    """Two ranks split the batch with no overlap and nothing left out,
+    balanced by multiply-adds; every rank's plans (word width, l and
+    workspace from libne.so's host calls) agree with one process planning
+    the whole batch, and both ranks gather the same result."""
+    from paper_1509_03838_gb300 import build, ne, shard, synth
+    build.build()
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        procs = [ctx.Process(target=_shard_rank_main, args=(r, 2, port, out))
+                 for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(180)
+            assert p.exitcode == 0
+        res = dict(out)
+    assert res[0] == res[1]
+    parts = res[0]
+    idx = [i for part in parts for i, *_ in part]
+    spec = synth.batch_spec(seed=3)
+    assert sorted(idx) == list(range(len(spec)))      # disjoint and complete
+    costs = shard.job_costs(spec.M, spec.N, spec.K)
+    loads = [sum(int(costs[i]) for i, *_ in part) for part in parts]
+    assert max(loads) <= 1.01 * min(loads)
+    for part in parts:
+        for i, w, l, ws in part:
+            m, n, k = int(spec.M[i]), int(spec.N[i]), int(spec.K[i])
+            p = ne.ne_choose_width(m, k, 1 << 15, 1 << 15)
+            assert (w, l, ws) == (p.w, p.l, ne.ne_protected_conv_ws_bytes(m, n, k))
