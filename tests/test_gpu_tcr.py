@@ -377,6 +377,45 @@ def test_tcr_tap_pieces_protected_every_failure(ne, orc, case):
     assert ne.ne_get_device_error(clear=True) == 0
 
 
+def test_tap_pieces_fall_back_without_their_scratch(ne, orc):
+    """K > 1025 with a workspace that holds the arrival words but not the
+    tap pieces' scratch: the protected call runs the multiply-add form
+    (refused under dispatch mode 2, which requires the raw-plane kernel),
+    with the same outputs; a plain call with a partial live mask likewise
+    leaves the tensor cores and writes only the live rows."""
+    w, M, N, K, bc = 64, 3, 3000, 1500, 12
+    p = ne.ne_params(M, w)
+    gen = synth.rng(77)
+    c = synth.uniform_int(gen, (M, N), -(1 << bc), 1 << bc)
+    g = synth.uniform_int(gen, (K,), -(1 << bc) + 1, 1 << bc)
+    plain = conv_par(orc, c, g, w)
+    cd = dev(c, w)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    full = ne.ne_protected_conv_ws_bytes(M, N, K)
+    small = ne.ne_protected_conv_ws_bytes(M, N, 1000)  # no pieces' part
+    assert small < full
+    ws = torch.empty(small, dtype=torch.uint8, device="cuda")
+    d = torch.full((M, N + K - 1), 9, dtype=torch.int64, device="cuda")
+    with raw_plane_required(ne):
+        with pytest.raises(ne.NEError) as e:
+            ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(1 << bc), (1 << bc) - 1),
+                                 max_abs_g=(1 << bc) - 1, failed=1,
+                                 fail_mode=ne.NE_FAIL_DROP, ws=ws)
+    assert e.value.status == ne.NE_ERR_UNSUPPORTED
+    ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-(1 << bc), (1 << bc) - 1),
+                         max_abs_g=(1 << bc) - 1, failed=1,
+                         fail_mode=ne.NE_FAIL_DROP, ws=ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(d), plain)
+    y = torch.full((M, N + K - 1), -4, dtype=torch.int64, device="cuda")
+    ne.ne_conv(cd, gd, y, x_range=(-(1 << bc), (1 << bc) - 1),
+               max_abs_g=(1 << bc) - 1, live_mask=0b101)
+    torch.cuda.synchronize()
+    got = host(y)
+    assert np.array_equal(got[0], plain[0]) and np.array_equal(got[2], plain[2])
+    assert (got[1] == -4).all()
+
+
 def test_raw_plane_required_refuses_other_forms(ne):
     """Dispatch mode 2 reports a job outside the raw-plane kernel's window
     (here: |g| above 2^15) instead of running another form, so that the
