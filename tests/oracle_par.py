@@ -39,3 +39,30 @@ def conv_par(orc, x, g, w: int, piece: int = 1 << 18, threads: int | None = None
     with cf.ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 4) as ex:
         list(ex.map(lambda t: one(*t), jobs))
     return y
+
+
+def conv_windows(orc, x, g, w: int, windows, threads: int | None = None,
+                 strict: bool = True):
+    """Outputs [a, b) of every row's full linear convolution, for each
+    window (a, b) in `windows`, as the oracle computes them (each from
+    exactly the input window it reads); returns one [rows, b - a] array per
+    window, in order."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.int64))
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.int64))
+    if x.ndim == 1:
+        x = x[None, :]
+    rows, N = x.shape
+    K = g.shape[0]
+    out = [np.empty((rows, b - a), dtype=np.int64) for a, b in windows]
+
+    def one(i, m):
+        a, b = windows[i]
+        start = max(0, a - K + 1)
+        stop = min(N, b)
+        ys = orc.conv(x[m, start:stop], g, w, strict=strict)
+        out[i][m] = ys[a - start:b - start]
+
+    jobs = [(i, m) for i in range(len(windows)) for m in range(rows)]
+    with cf.ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 4) as ex:
+        list(ex.map(lambda t: one(*t), jobs))
+    return out

@@ -15,7 +15,7 @@ The oracle side runs in independent output pieces on all host cores
 import numpy as np
 import pytest
 
-from oracle_par import conv_par
+from oracle_par import conv_par, conv_windows
 from paper_1509_03838_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -430,6 +430,44 @@ def test_raw_plane_required_refuses_other_forms(ne):
     ne.ne_conv(x, g, y, x_range=(-5, 5), max_abs_g=1 << 20)  # other forms
     torch.cuda.synchronize()
     assert int(y.abs().sum()) == 0
+
+
+@pytest.mark.parametrize("M,K", [(3, 100), (3, 1000), (3, 4500), (8, 100),
+                                 (8, 1000), (8, 4500)])
+def test_paper_shapes_full_size_sampled(ne, orc, M, K):
+    """Sec. V's shapes at full size, as the benchmark runs them (N = 10^6,
+    data and taps in [-2^14, 2^14), 64-bit words; K = 4500 in tap pieces):
+    the protected convolution with one stream dropped, and the plain one,
+    on 40 windows of 256 outputs (both ends and seeded positions), every
+    row, against the oracle computed window by window."""
+    w, N = 64, 10**6
+    b = 1 << 14
+    p = ne.ne_params(M, w)
+    gen = synth.rng(1000 + 10 * M + K)
+    c = synth.uniform_int(gen, (M, N), -b, b)
+    g = synth.uniform_int(gen, (K,), -b, b)
+    Nout = N + K - 1
+    starts = [0, Nout - 256] + sorted(gen.integers(0, Nout - 256, size=38).tolist())
+    windows = [(a, a + 256) for a in starts]
+    expect = conv_windows(orc, c, g, w, windows)
+    cd = dev(c, w)
+    gd = torch.from_numpy(g.astype(np.int32)).cuda()
+    d = torch.empty((M, Nout), dtype=torch.int64, device="cuda")
+    r = int(gen.integers(0, M))
+    with raw_plane_required(ne):
+        ne.ne_protected_conv(cd, gd, d, l=p.l, c_range=(-b, b - 1), max_abs_g=b,
+                             failed=r, fail_mode=ne.NE_FAIL_DROP)
+        torch.cuda.synchronize()
+        got = host(d)
+        for (a, e), want in zip(windows, expect):
+            assert np.array_equal(got[:, a:e], want), ("protected", a)
+        y = torch.empty((M, Nout), dtype=torch.int64, device="cuda")
+        ne.ne_conv(cd, gd, y, x_range=(-b, b - 1), max_abs_g=b)
+        torch.cuda.synchronize()
+        got = host(y)
+        for (a, e), want in zip(windows, expect):
+            assert np.array_equal(got[:, a:e], want), ("plain", a)
+    assert ne.ne_get_device_error(clear=True) == 0
 
 
 def test_tcr_protected_full_size_every_output(ne, orc):
