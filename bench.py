@@ -687,7 +687,7 @@ E2E_STREAMS = 4
 # change of those sources.
 TRAFFIC_CAPTURE = {
     "sources_sha256":
-        "348d9e2cc54aa12895da19f5297caa9e1d639a554006aa5d92ed5f5b3af26886",
+        "3ba2aac26419689fcbe489c10badffa95f3d2a6782f5700155aa13826f74e880",
     # tcr_conv_kernel<int64, 1, 4, 2, 2, 0>, second of three captured
     # launches: 134540032 bytes read + 80859392 written (the rest of d is
     # still in L2 when the launch ends), from ncu --set full on the bench job

@@ -387,7 +387,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait for a bulk-copy phase: returns false (and flags the error)
 // if the phase has not completed after `limit` polls.  Every thread of the
-// block must call it; the verdict is made uniform across the block.
+// block must call it; the decision is made uniform across the block.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar,
                                                   uint32_t parity) {
   constexpr uint32_t limit = 1u << 24;
