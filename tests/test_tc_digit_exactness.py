@@ -91,3 +91,58 @@ def test_digits_reassemble_the_operands():
     assert np.array_equal(g0 + 256 * g1, g)
     assert g0.min() >= -128 and g0.max() <= 127
     assert g1.min() >= -128 and g1.max() <= 128
+
+
+# ---------------------------------------------------------------------------
+# The raw-plane kernel's large-K form: balanced byte digits of the shifted
+# operand (each in [-128, 127]) and of the taps (each in [-128, 128]);
+# level L of a slot accumulates the pairs (i, j) with i + j = L, and with
+# the neighbour's levels merged (l = 8 Q) also the neighbour's pairs with
+# Q + i + j = L.  A group of G k-steps (16 taps each) is drained before its
+# sums can leave the integers fp32 holds exactly: P 2^14 16 G <= 2^24 for
+# P pairs per level, so G = min(32, 64 / P).
+# ---------------------------------------------------------------------------
+def pairs_per_level(nd, q):
+    most = 1
+    for L in range(nd + q + 2):
+        n = sum((i + j == L) + (q > 0 and q + i + j == L)
+                for i in range(nd) for j in range(2))
+        most = max(most, n)
+    return most
+
+
+def group_k_steps(nd, q):
+    return min(32, 64 // pairs_per_level(nd, q))
+
+
+FORMS = [(1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (2, 2)]  # (digits, Q) built
+
+
+def test_group_sizes_of_the_built_forms():
+    assert [group_k_steps(nd, q) for nd, q in FORMS] == [32, 32, 32, 32, 21, 32]
+
+
+def _worst_level_sum(pairs, k_steps, order):
+    """The largest odd product, 127 * 127, in every (pair, tap) of a level
+    over k_steps k-steps of 16 taps, summed in fp32 in two orders."""
+    terms = [127 * 127] * (pairs * 16 * k_steps)
+    return int(fp32_sum(terms, order)), sum(terms)
+
+
+@pytest.mark.parametrize("nd,q", FORMS)
+@pytest.mark.parametrize("order", [0, 1])
+def test_group_sums_stay_exact_and_one_more_step_would_not(nd, q, order):
+    P, G = pairs_per_level(nd, q), group_k_steps(nd, q)
+    got, exact = _worst_level_sum(P, G, order)
+    assert got == exact and exact <= 1 << 24
+    if 64 // P <= 32:  # the bound, not the cap, sets G: one step more breaks it
+        got, exact = _worst_level_sum(P, G + 1, order)
+        assert exact > 1 << 24 and got != exact
+
+
+def test_balanced_digits_reach_the_extreme_products():
+    """127 * 127 occurs: operand digits of 127 (x - bias with bytes 0xFF) and
+    tap digits of 127 (g = 127 * 257 = 32639 <= 2^15)."""
+    g = 127 * 257
+    assert tap_digits([g])[0][0] == 127 and tap_digits([g])[1][0] == 127
+    assert g <= 1 << 15
