@@ -687,15 +687,15 @@ E2E_STREAMS = 4
 # change of those sources.
 TRAFFIC_CAPTURE = {
     "sources_sha256":
-        "3ba2aac26419689fcbe489c10badffa95f3d2a6782f5700155aa13826f74e880",
+        "5446d00c79fea58380ed30668ded261d6f47935a103c9874f16d65f6c70579f6",
     # tcr_conv_kernel<int64, 1, 4, 2, 2, 0>, second of three captured
     # launches: 134540032 bytes read + 80859392 written (the rest of d is
     # still in L2 when the launch ends), from ncu --set full on the bench job
     "bytes": 134540032 + 80859392,
 }
-CONV_SOURCES = ["ne_conv.cu", "ne_conv_core.cuh", "ne_conv_args.cuh",
-                "ne_conv_tcr.cuh", "ne_conv_tcr_w64.cu", "ne_tc5.cuh",
-                "ne_common.cuh"]
+# the translation unit the captured kernel is compiled from
+CONV_SOURCES = ["ne_conv_tcr_w64.cu", "ne_conv_tcr.cuh", "ne_conv_args.cuh",
+                "ne_conv_core.cuh", "ne_tc5.cuh", "ne_common.cuh"]
 
 
 def conv_sources_sha() -> str:

@@ -903,11 +903,12 @@ inline bool tcr_enabled() {
 // warp-specialised pipeline start) is about 16 us per launch, against about
 // 6 us for the multiply-add kernels; past that the tensor-core forms move
 // the job's bytes at about 3.2 TB/s (protected) or 4.4 TB/s (plain), or,
-// with many taps, issue their products at about one per 25 ns per SM (the
-// slower of the two), and the multiply-add kernels do about 6.1e12
-// multiply-adds per second (half that when products need two
-// instructions, split = true).  Estimated times, in microseconds, measured
-// on GB300; the cheaper estimate wins.  nd: byte digits of the operands.
+// with many taps, issue their products at about one per 25 ns per SM (one
+// per 140 ns in the large-K form, K > 65; the slower of the two), and the
+// multiply-add kernels do about 6.1e12 multiply-adds per second (half that
+// when products need two instructions, split = true).  Estimated times, in
+// microseconds, measured on GB300; the cheaper estimate wins.  nd: byte
+// digits of the operands.
 // ne_debug_set_dispatch: 0 estimate, 1 tensor cores whenever their window
 // allows, 2 the raw-plane kernel required (NE_ERR_UNSUPPORTED otherwise)
 std::atomic<int> g_debug_tc_always{0};
@@ -924,7 +925,8 @@ inline bool tensor_cores_pay(int streams, int64_t N, int64_t Nout, int K, int wb
   const double mmas = (double)streams * (double)((Nout + 4095) / 4096) * ks *
                       (double)(nd > 0 ? nd : 4) * (prot ? 2.0 : 1.0);
   const double tc_us = (K > 65 ? 21.0 : 16.0) +
-                       std::max(bytes / (prot ? 3.2e6 : 4.4e6), mmas * 0.025 / 152.0);
+                       std::max(bytes / (prot ? 3.2e6 : 4.4e6),
+                                mmas * (K > 65 ? 0.14 : 0.025) / 152.0);
   return tc_us < imad_us;
 }
 
