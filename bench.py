@@ -50,7 +50,7 @@ L2_NOTE = ("inputs larger than L2: c 134 MB + d 134 MB per step vs 129 MB L2 "
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ne", "reference"], default="ne")
     ap.add_argument("--no-cpu-baseline", action="store_true")
