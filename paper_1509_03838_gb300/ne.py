@@ -179,6 +179,9 @@ EXTRA_SIGS: dict = {}
 def lib():
     """The loaded libne.so (raises if it has not been built)."""
     global _lib
+    loaded = _lib
+    if loaded is not None:  # (set once, under the lock below)
+        return loaded
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
@@ -219,19 +222,22 @@ def _word_bits(t: torch.Tensor) -> int:
 
 
 def _rows(t: torch.Tensor, name: str):
-    """(ptr, rows, samples, ld) of a 2-D CUDA tensor with unit inner stride."""
+    """(ptr, rows, samples, ld) of a 2-D CUDA tensor with unit inner stride
+    (a 1-D tensor is one row)."""
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
-    if t.dim() == 1:
-        t2 = t.unsqueeze(0)
-    elif t.dim() == 2:
-        t2 = t
+    shape, stride = t.shape, t.stride()
+    if len(shape) == 1:
+        rows, n, ld, inner = 1, shape[0], max(shape[0], 1), stride[0]
+    elif len(shape) == 2:
+        rows, n = shape
+        inner = stride[1]
+        ld = stride[0] if rows > 1 else max(n, 1)
     else:
         raise ValueError(f"{name} must be 1-D or 2-D")
-    if t2.size(1) > 1 and t2.stride(1) != 1:
+    if n > 1 and inner != 1:
         raise ValueError(f"{name} must have unit stride along samples")
-    ld = t2.stride(0) if t2.size(0) > 1 else max(t2.size(1), 1)
-    return ctypes.c_void_p(t2.data_ptr()), t2.size(0), t2.size(1), ld
+    return ctypes.c_void_p(t.data_ptr()), rows, n, ld
 
 
 def _blocks(t: torch.Tensor, name: str):
