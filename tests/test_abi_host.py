@@ -386,3 +386,19 @@ def test_protected_workspace_holds_the_tap_pieces(ne):
     assert big >= 3 * (1000 + 912 - 1) * 8 + base // 4
     # K = 1025: arrival words and the large-K table (at most 132 KiB) only
     assert ne.ne_protected_conv_ws_bytes(3, 1000, 1025) < 140 * 1024
+
+
+def test_debug_build_compiles_and_exports_every_symbol(ne):
+    """The index-checking build (NE_INDEX_CHECKS) compiles from the same
+    sources and exports the same C ABI; its readers reject null outputs on
+    the host."""
+    from paper_1509_03838_gb300 import build
+    path = build.build(debug=True)
+    assert path == build.DEBUG_LIB and os.path.exists(path)
+    D = ctypes.CDLL(path)
+    missing = [n for n in declared_symbols() if not hasattr(D, n)]
+    assert not missing, missing
+    f = ctypes.c_uint64(0)
+    assert D.ne_debug_index_status(None, ctypes.byref(f), 0) == ne.NE_ERR_INVALID_ARG
+    assert D.ne_debug_index_selftest(ctypes.c_int64(0), ctypes.c_int64(1),
+                                     None) == ne.NE_ERR_INVALID_ARG
